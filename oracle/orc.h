@@ -1,0 +1,77 @@
+/*
+ * orc.h -- plain FP64 CPU oracle for the MUSCL-Hancock step of the
+ * vibrationally excited gas model (Khrapov & Khoperskov 2018).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code,
+ * header or constant with the CUDA path.
+ *
+ * Model (Sec. 2.1): eqs. 1-5 (continuity, momentum, total energy with pump Q
+ * and sink I, vibrational energy relaxing with time tau), eq. 6 (power-law
+ * closures tau, Q, I in rho and T), eq. 7 (p = R rho T).  Units (Sec. 2.3,
+ * normalisation paragraph): rho0 = p0 = R = 1, so T0 = 1; tau0 is kept as a
+ * free parameter and Q0 = I0 = S / tau0 (the definition of S under eq. 8 with
+ * the equilibrium condition Q0 = I0 of eq. 3).
+ *
+ * Conserved state per cell, d = dim:  (rho, rho*v_1 .. rho*v_d, E, E_nu),
+ * nf = d + 3 fields.  Arrays are field-major structure-of-arrays:
+ * U[f * ncell + idx], idx = i + nx * (j + ny * k).  Periodic in every axis.
+ */
+#ifndef ORC_H
+#define ORC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_MINMOD  0
+#define ORC_VANLEER 1
+#define ORC_MC      2
+
+typedef struct {
+  double gamma;     /* adiabatic exponent, eq. 5 */
+  double Ck;        /* C_k = dE_nue / (R dT), under eq. 8 */
+  double S;         /* degree of non-equilibrium S = tau0 Q0 / (R T0), under eq. 8 */
+  double tau0;      /* relaxation time at equilibrium; +inf = frozen limit */
+  double tau_rho, tau_T, Q_rho, Q_T, I_rho, I_T;   /* eq. 6 exponents */
+  double cfl;       /* factor applied to the eq. 16 bound */
+  double c_tau;     /* dt <= c_tau * min tau (explicit source bound) */
+  int limiter;      /* ORC_MINMOD (default), ORC_VANLEER, ORC_MC */
+} orc_params;
+
+/* Pointwise pieces (one cell state u[nf], dim = 1..3). */
+double orc_pressure(const orc_params* P, int dim, const double* u);          /* eq. 5 */
+void   orc_flux(const orc_params* P, int dim, int axis, const double* u, double* F); /* F, G, H of eq. 15 */
+void   orc_source(const orc_params* P, int dim, const double* u, double* Y); /* Y of eq. 15, eq. 6 */
+void   orc_hll(const orc_params* P, int dim, int axis, const double* uL, const double* uR, double* F); /* eq. 13 */
+double orc_limiter(int limiter, double a, double b);                          /* TVD slope limiter */
+int    orc_physical(const orc_params* P, int dim, const double* u);           /* rho > 0, p > 0, finite */
+
+/* One MUSCL-Hancock step (eqs. 13-15, xi = 0) on a periodic grid.
+   n[0..dim-1] = cells per axis, h = cell size, U and Unew are nf*ncell arrays.
+   Returns 0, or -1 if any new state is non-physical (rho <= 0, p <= 0, NaN),
+   or -2 on allocation failure. */
+int orc_step(const orc_params* P, int dim, const long* n, double h, double dt,
+             const double* U, double* Unew);
+
+/* The same step for one cell `idx` only, recomputing its neighbourhood; out[nf].
+   Bitwise identical to orc_step's value at that cell. */
+void orc_step_cell(const orc_params* P, int dim, const long* n, double h, double dt,
+                   const double* U, long idx, double* out);
+
+/* Time step of eq. 16 times cfl, capped by c_tau * min tau. */
+double orc_dt(const orc_params* P, int dim, const long* n, double h, const double* U);
+
+/* Advance U in place until t_end (last step clamped) or max_steps steps.
+   Writes the reached time and the number of steps taken. Returns 0, -1 on a
+   non-physical state (stops there), -2 on allocation failure. */
+int orc_run(const orc_params* P, int dim, const long* n, double h, double* U,
+            double t0, double t_end, long max_steps, double* t_out, long* steps_out);
+
+/* Number of OpenMP threads the array loops use (1 without OpenMP). */
+int orc_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

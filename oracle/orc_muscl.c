@@ -1,0 +1,325 @@
+/*
+ * orc_muscl.c -- plain FP64 CPU oracle of the MUSCL-Hancock step
+ * (Khrapov & Khoperskov 2018, Sec. 2.3, eqs. 13-16).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg, never by the product path.  Built with
+ * -O2 -ffp-contract=off and no fast-math so every operation is a plain IEEE
+ * double operation in source order.
+ *
+ * The step, in the paper's order (eq. 14 with xi = 0, eq. 15, eq. 13):
+ *   1. slopes:   Theta_j h = lim(U_j - U_{j-1}, U_{j+1} - U_j) per conserved
+ *                field and axis (eq. 14 reconstructs U; the limiter is not
+ *                named, minmod by default);
+ *                if an extrapolated state U_j +- Theta_j h / 2 of any axis is
+ *                non-physical, all slopes of that cell are set to zero;
+ *   2. predictor (the half step of the "two-step predictor-corrector"):
+ *                U^{n+1/2}_j = U_j - dt/(2h) sum_axes [F(U_j + Th/2) - F(U_j - Th/2)]
+ *                              + dt/2 Y(U_j);
+ *   3. face states (eq. 14, xi = 0):
+ *                U^L_{j+1/2} = U^{n+1/2}_j + Theta_j h/2,
+ *                U^R_{j+1/2} = U^{n+1/2}_{j+1} - Theta_{j+1} h/2;
+ *                a face with a non-physical state uses U_j, U_{j+1} instead;
+ *   4. HLL flux (eq. 13) with S_L = min(u_L - c_L, u_R - c_R),
+ *                S_R = max(u_L + c_L, u_R + c_R), c = sqrt(gamma p / rho);
+ *   5. corrector (eq. 15):
+ *                U^{n+1}_j = U_j - dt/h sum_axes (F_{j+1/2} - F_{j-1/2})
+ *                            + dt Y(U^{n+1/2}_j).
+ * Source Y (the MUSCL Y vector of Sec. 2.3 with f = 0):
+ *   Y = (0, 0.., rho (Q - I), (rho C_k T - E_nu)/tau + rho Q),
+ * tau, Q, I from eq. 6, T = p / rho (eq. 7, R = 1), p from eq. 5.
+ */
+#include "orc.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define NF_MAX 6
+
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* eq. 5: E = p/(gamma-1) + rho |v|^2 / 2 + E_nu  ->  p */
+double orc_pressure(const orc_params* P, int dim, const double* u) {
+  double rho = u[0];
+  double kin = 0.0;
+  for (int a = 0; a < dim; ++a) kin += u[1 + a] * u[1 + a];
+  kin = 0.5 * kin / rho;
+  return (P->gamma - 1.0) * (u[1 + dim] - kin - u[2 + dim]);
+}
+
+int orc_physical(const orc_params* P, int dim, const double* u) {
+  double p = orc_pressure(P, dim, u);
+  return isfinite(u[0]) && isfinite(p) && u[0] > 0.0 && p > 0.0;
+}
+
+/* Flux along `axis`: F (x), G (y) of eq. 15, and the analogous z flux. */
+void orc_flux(const orc_params* P, int dim, int axis, const double* u, double* F) {
+  double rho = u[0];
+  double va = u[1 + axis] / rho;
+  double p = orc_pressure(P, dim, u);
+  F[0] = u[1 + axis];
+  for (int b = 0; b < dim; ++b) F[1 + b] = u[1 + b] * va + (b == axis ? p : 0.0);
+  F[1 + dim] = va * (u[1 + dim] + p);
+  F[2 + dim] = va * u[2 + dim];
+}
+
+/* Y of eq. 15 with f = 0, closures of eq. 6, T from eq. 7 with R = 1. */
+void orc_source(const orc_params* P, int dim, const double* u, double* Y) {
+  int nf = dim + 3;
+  double rho = u[0];
+  double p = orc_pressure(P, dim, u);
+  double T = p / rho;
+  double Q0 = P->S / P->tau0;   /* S = tau0 Q0 / (R T0) */
+  double I0 = Q0;               /* equilibrium of eq. 3 */
+  double tau = P->tau0 * pow(rho, P->tau_rho) * pow(T, P->tau_T);
+  double Q = Q0 * pow(rho, P->Q_rho) * pow(T, P->Q_T);
+  double I = I0 * pow(rho, P->I_rho) * pow(T, P->I_T);
+  for (int f = 0; f < nf; ++f) Y[f] = 0.0;
+  Y[1 + dim] = rho * (Q - I);
+  Y[2 + dim] = (rho * P->Ck * T - u[2 + dim]) / tau + rho * Q;
+}
+
+/* eq. 13 */
+void orc_hll(const orc_params* P, int dim, int axis, const double* uL, const double* uR, double* F) {
+  int nf = dim + 3;
+  double FL[NF_MAX], FR[NF_MAX];
+  double pL = orc_pressure(P, dim, uL), pR = orc_pressure(P, dim, uR);
+  double vL = uL[1 + axis] / uL[0], vR = uR[1 + axis] / uR[0];
+  double cL = sqrt(P->gamma * pL / uL[0]), cR = sqrt(P->gamma * pR / uR[0]);
+  double SL = fmin(vL - cL, vR - cR);
+  double SR = fmax(vL + cL, vR + cR);
+  orc_flux(P, dim, axis, uL, FL);
+  orc_flux(P, dim, axis, uR, FR);
+  if (0.0 < SL) {
+    for (int f = 0; f < nf; ++f) F[f] = FL[f];
+  } else if (0.0 > SR) {
+    for (int f = 0; f < nf; ++f) F[f] = FR[f];
+  } else {
+    for (int f = 0; f < nf; ++f)
+      F[f] = (SR * FL[f] - SL * FR[f] + SL * SR * (uR[f] - uL[f])) / (SR - SL);
+  }
+}
+
+double orc_limiter(int limiter, double a, double b) {
+  if (a * b <= 0.0) return 0.0;
+  double s = a > 0.0 ? 1.0 : -1.0;
+  switch (limiter) {
+    case ORC_VANLEER:
+      return 2.0 * a * b / (a + b);
+    case ORC_MC: {
+      double m = fmin(2.0 * fabs(a), 2.0 * fabs(b));
+      return s * fmin(m, 0.5 * fabs(a + b));
+    }
+    default:
+      return s * fmin(fabs(a), fabs(b));
+  }
+}
+
+/* ---------------------------------------------------------------- grid */
+
+typedef struct {
+  int dim, nf;
+  long n[3];
+  long ncell;
+} grid_t;
+
+static grid_t make_grid(int dim, const long* n) {
+  grid_t g;
+  g.dim = dim;
+  g.nf = dim + 3;
+  g.n[0] = g.n[1] = g.n[2] = 1;
+  g.ncell = 1;
+  for (int a = 0; a < dim; ++a) { g.n[a] = n[a]; g.ncell *= n[a]; }
+  return g;
+}
+
+/* periodic neighbour of cell idx along axis a at offset s (|s| <= 2) */
+static long neighbour(const grid_t* g, long idx, int a, int s) {
+  long c[3];
+  c[0] = idx % g->n[0];
+  c[1] = (idx / g->n[0]) % g->n[1];
+  c[2] = idx / (g->n[0] * g->n[1]);
+  c[a] = ((c[a] + s) % g->n[a] + g->n[a]) % g->n[a];
+  return c[0] + g->n[0] * (c[1] + g->n[1] * c[2]);
+}
+
+static void gather(const grid_t* g, const double* U, long idx, double* u) {
+  for (int f = 0; f < g->nf; ++f) u[f] = U[(long)f * g->ncell + idx];
+}
+
+/* Steps 1-2 for cell q: slopes dU[a][f] (= Theta h) and the half-step state uh. */
+static void predict(const orc_params* P, const grid_t* g, double h, double dt,
+                    const double* U, long q, double dU[3][NF_MAX], double* uh) {
+  int dim = g->dim, nf = g->nf;
+  double u[NF_MAX], um[NF_MAX], up[NF_MAX];
+  gather(g, U, q, u);
+  int ok = 1;
+  for (int a = 0; a < dim; ++a) {
+    gather(g, U, neighbour(g, q, a, -1), um);
+    gather(g, U, neighbour(g, q, a, +1), up);
+    for (int f = 0; f < nf; ++f) dU[a][f] = orc_limiter(P->limiter, u[f] - um[f], up[f] - u[f]);
+  }
+  for (int a = 0; a < dim && ok; ++a) {
+    for (int f = 0; f < nf; ++f) { um[f] = u[f] - 0.5 * dU[a][f]; up[f] = u[f] + 0.5 * dU[a][f]; }
+    if (!orc_physical(P, dim, um) || !orc_physical(P, dim, up)) ok = 0;
+  }
+  if (!ok)
+    for (int a = 0; a < dim; ++a)
+      for (int f = 0; f < nf; ++f) dU[a][f] = 0.0;
+
+  double Y[NF_MAX], Fm[NF_MAX], Fp[NF_MAX], div[NF_MAX];
+  for (int f = 0; f < nf; ++f) div[f] = 0.0;
+  for (int a = 0; a < dim; ++a) {
+    for (int f = 0; f < nf; ++f) { um[f] = u[f] - 0.5 * dU[a][f]; up[f] = u[f] + 0.5 * dU[a][f]; }
+    orc_flux(P, dim, a, up, Fp);
+    orc_flux(P, dim, a, um, Fm);
+    for (int f = 0; f < nf; ++f) div[f] += Fp[f] - Fm[f];
+  }
+  orc_source(P, dim, u, Y);
+  for (int f = 0; f < nf; ++f) uh[f] = u[f] - dt / (2.0 * h) * div[f] + 0.5 * dt * Y[f];
+}
+
+/* Steps 3-4 for the face between cell l and its +axis neighbour r. */
+static void face_flux(const orc_params* P, const grid_t* g, const double* U, int a,
+                      long l, const double dUl[3][NF_MAX], const double* uhl,
+                      long r, const double dUr[3][NF_MAX], const double* uhr, double* F) {
+  int nf = g->nf, dim = g->dim;
+  double uL[NF_MAX], uR[NF_MAX];
+  for (int f = 0; f < nf; ++f) {
+    uL[f] = uhl[f] + 0.5 * dUl[a][f];
+    uR[f] = uhr[f] - 0.5 * dUr[a][f];
+  }
+  if (!orc_physical(P, dim, uL) || !orc_physical(P, dim, uR)) {
+    gather(g, U, l, uL);
+    gather(g, U, r, uR);
+  }
+  orc_hll(P, dim, a, uL, uR, F);
+}
+
+/* Step 5 for one cell. */
+static void correct(const orc_params* P, const grid_t* g, double h, double dt,
+                    const double* u, const double* uh, double Fp[3][NF_MAX],
+                    double Fm[3][NF_MAX], double* out) {
+  int nf = g->nf, dim = g->dim;
+  double Y[NF_MAX], div[NF_MAX];
+  for (int f = 0; f < nf; ++f) div[f] = 0.0;
+  for (int a = 0; a < dim; ++a)
+    for (int f = 0; f < nf; ++f) div[f] += Fp[a][f] - Fm[a][f];
+  orc_source(P, dim, uh, Y);
+  for (int f = 0; f < nf; ++f) out[f] = u[f] - dt / h * div[f] + dt * Y[f];
+}
+
+int orc_step(const orc_params* P, int dim, const long* n, double h, double dt,
+             const double* U, double* Unew) {
+  grid_t g = make_grid(dim, n);
+  int nf = g.nf;
+  long N = g.ncell;
+  double (*dU)[3][NF_MAX] = malloc(sizeof(double[3][NF_MAX]) * (size_t)N);
+  double (*uh)[NF_MAX] = malloc(sizeof(double[NF_MAX]) * (size_t)N);
+  double (*Fface)[3][NF_MAX] = malloc(sizeof(double[3][NF_MAX]) * (size_t)N);
+  if (!dU || !uh || !Fface) { free(dU); free(uh); free(Fface); return -2; }
+
+#pragma omp parallel for schedule(static)
+  for (long q = 0; q < N; ++q) predict(P, &g, h, dt, U, q, dU[q], uh[q]);
+
+#pragma omp parallel for schedule(static)
+  for (long q = 0; q < N; ++q)
+    for (int a = 0; a < dim; ++a) {
+      long r = neighbour(&g, q, a, +1);
+      face_flux(P, &g, U, a, q, dU[q], uh[q], r, dU[r], uh[r], Fface[q][a]);
+    }
+
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+  for (long q = 0; q < N; ++q) {
+    double u[NF_MAX], out[NF_MAX], Fp[3][NF_MAX], Fm[3][NF_MAX];
+    gather(&g, U, q, u);
+    for (int a = 0; a < dim; ++a) {
+      long l = neighbour(&g, q, a, -1);
+      memcpy(Fp[a], Fface[q][a], sizeof(double) * NF_MAX);
+      memcpy(Fm[a], Fface[l][a], sizeof(double) * NF_MAX);
+    }
+    correct(P, &g, h, dt, u, uh[q], Fp, Fm, out);
+    for (int f = 0; f < nf; ++f) Unew[(long)f * N + q] = out[f];
+    if (!orc_physical(P, dim, out)) bad = 1;
+  }
+  free(dU); free(uh); free(Fface);
+  return bad ? -1 : 0;
+}
+
+void orc_step_cell(const orc_params* P, int dim, const long* n, double h, double dt,
+                   const double* U, long idx, double* out) {
+  grid_t g = make_grid(dim, n);
+  double dUc[3][NF_MAX], uhc[NF_MAX], dUn[3][NF_MAX], uhn[NF_MAX];
+  double Fp[3][NF_MAX], Fm[3][NF_MAX], u[NF_MAX];
+  predict(P, &g, h, dt, U, idx, dUc, uhc);
+  for (int a = 0; a < dim; ++a) {
+    long r = neighbour(&g, idx, a, +1);
+    predict(P, &g, h, dt, U, r, dUn, uhn);
+    face_flux(P, &g, U, a, idx, dUc, uhc, r, dUn, uhn, Fp[a]);
+    long l = neighbour(&g, idx, a, -1);
+    predict(P, &g, h, dt, U, l, dUn, uhn);
+    face_flux(P, &g, U, a, l, dUn, uhn, idx, dUc, uhc, Fm[a]);
+  }
+  gather(&g, U, idx, u);
+  correct(P, &g, h, dt, u, uhc, Fp, Fm, out);
+}
+
+/* eq. 16: dt < min_j min(h / (2|v_j|), h / (|v_j| + c_j)), times cfl;
+   then dt <= c_tau * min_j tau_j (the explicit source needs it when tau is short). */
+double orc_dt(const orc_params* P, int dim, const long* n, double h, const double* U) {
+  grid_t g = make_grid(dim, n);
+  double smax = 0.0, taumin = INFINITY;
+  for (long q = 0; q < g.ncell; ++q) {
+    double u[NF_MAX];
+    gather(&g, U, q, u);
+    double p = orc_pressure(P, dim, u);
+    double v2 = 0.0;
+    for (int a = 0; a < dim; ++a) v2 += (u[1 + a] / u[0]) * (u[1 + a] / u[0]);
+    double v = sqrt(v2);
+    double c = sqrt(P->gamma * p / u[0]);
+    double s = fmax(2.0 * v, v + c);
+    if (s > smax) smax = s;
+    double T = p / u[0];
+    double tau = P->tau0 * pow(u[0], P->tau_rho) * pow(T, P->tau_T);
+    if (tau < taumin) taumin = tau;
+  }
+  double dt = P->cfl * h / smax;
+  if (isfinite(taumin) && P->c_tau * taumin < dt) dt = P->c_tau * taumin;
+  return dt;
+}
+
+int orc_run(const orc_params* P, int dim, const long* n, double h, double* U,
+            double t0, double t_end, long max_steps, double* t_out, long* steps_out) {
+  grid_t g = make_grid(dim, n);
+  size_t bytes = sizeof(double) * (size_t)g.nf * (size_t)g.ncell;
+  double* tmp = malloc(bytes);
+  if (!tmp) return -2;
+  double t = t0;
+  long k = 0;
+  int rc = 0;
+  while (t < t_end && k < max_steps) {
+    double dt = orc_dt(P, dim, n, h, U);
+    int last = 0;
+    if (dt >= t_end - t) { dt = t_end - t; last = 1; }
+    rc = orc_step(P, dim, n, h, dt, U, tmp);
+    memcpy(U, tmp, bytes);
+    t = last ? t_end : t + dt;
+    ++k;
+    if (rc != 0) break;
+  }
+  free(tmp);
+  *t_out = t;
+  *steps_out = k;
+  return rc;
+}
