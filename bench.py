@@ -1,0 +1,288 @@
+"""Benchmark of the fused MUSCL-Hancock step (one JSON line on rank 0).
+
+Workload (default): 1D periodic grid of N = 2^22 cells, h = 1/1024 (L = 4096
+base wavelengths), FP32 state, gamma 1.4, C_k 0.1, tau_rho -1, tau_T -1.5,
+Q/I exponents 0, S 1, tau0 0.08, CFL 0.4, seeded sum of 64 random-phase
+acoustic modes with k_i = 2 pi i / 32 (i = 1..64) and amplitudes 1e-3 / i.
+A "step" is one MUSCL-Hancock time step of the whole grid (one launch of the
+fused kernel).  The state (64 MiB per buffer) fits in L2, so L2 is flushed by a
+256 MiB write before every timed step and each step is timed alone with CUDA
+events on the solver's stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision fp32|fp64|fp32_p64] [--n CELLS]
+
+Under torchrun (N > 1) every rank runs an independent replica (the 1D problem
+is not sharded: "replicas only"); value = all ranks' cell-updates / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload(n_cells: int, gamma: float, Ck: float, S: float):
+    from paper_1805_03442_gb300 import inputs
+    h = 1.0 / 1024
+    L = n_cells * h
+    m0 = max(1, int(round(L / 32.0)))            # k_1 = 2 pi / 32
+    modes = inputs.random_phase_modes(2024, inputs.acoustic_shape(gamma), 64, m0, 1e-3, m_step=m0)
+    U0 = inputs.waves_1d(gamma, n_cells, L, inputs.equilibrium_primitive(Ck, S), modes)
+    return U0, h, L
+
+
+def peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.p = None
+        self.index = index
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.result = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.p is None:
+            return
+        time.sleep(0.2)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if sm:
+            self.result = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                           "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(n_cells: int, budget_s: float = 10.0) -> dict:
+    """The FP64 oracle, as it stands, on the same workload: whole-grid steps
+    until `budget_s` of wall time (at least one)."""
+    from oracle import orc as O
+    P = O.Params(tau0=0.08, S=1.0)
+    U, h, _ = workload(n_cells, P.gamma, P.Ck, P.S)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        dt = O.dt_cfl(P, U, n_cells, h)
+        U, rc = O.step(P, U, n_cells, h, dt)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return {"value": n_cells * steps / el, "unit": METRIC, "cores": O.threads(), "kind": "oracle",
+            "sample": f"{steps} whole-grid FP64 oracle steps of the same N={n_cells} workload "
+                      f"({el:.1f} s wall)"}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch.distributed as dist
+    backend = "nccl"
+    try:
+        import torch
+        if not torch.cuda.is_available():
+            backend = "gloo"
+    except Exception:
+        backend = "gloo"
+    dist.init_process_group(backend)
+    return dist.get_rank(), dist.get_world_size(), dist
+
+
+def run_reference(args):
+    rank, ws, dist = dist_init()
+    if rank != 0:
+        return
+    from oracle import orc as O
+    P = O.Params(tau0=0.08, S=1.0)
+    U, h, _ = workload(args.n, P.gamma, P.Ck, P.S)
+    for _ in range(args.warmup):
+        U, _ = O.step(P, U, args.n, h, O.dt_cfl(P, U, args.n, h))
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        U, _ = O.step(P, U, args.n, h, O.dt_cfl(P, U, args.n, h))
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.n * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"1D periodic MUSCL-Hancock, N={args.n}", "cells": args.n},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": O.threads(), "kind": "oracle",
+                             "sample": f"{args.steps} whole-grid FP64 oracle steps"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, ws, dist = dist_init()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_1805_03442_gb300 import sv
+    from paper_1805_03442_gb300.build import build
+    if rank == 0 or not os.path.exists(sv.LIB_PATH):
+        build()
+    if dist is not None:
+        dist.barrier()
+    prec = {"fp32": sv.FP32, "fp64": sv.FP64, "fp32_p64": sv.FP32_P64}[args.precision]
+    esize = 8 if prec == sv.FP64 else 4
+    P = sv.Params(precision=prec, tau0=0.08, S=1.0)
+    U0, h, L = workload(args.n, P.gamma, P.Ck, P.S)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    solver = sv.Solver(P, (args.n,), (L,), stream=stream)
+    solver.write_state(U0)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        solver.step(1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))
+                ev[i][0].record(stream)
+            solver.step(1)
+            with torch.cuda.stream(stream):
+                ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    times = [a.elapsed_time(b) * 1e-3 for a, b in ev]
+    tot = sum(times)
+    if dist is not None:
+        t = torch.tensor([tot], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    status = solver.status()
+    t_sim, nsteps = solver.time()
+
+    # end to end through the C ABI: pinned host FP64 state in, one step, state out
+    nf = 4
+    host_in = torch.from_numpy(U0.reshape(-1)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    e2e_steps = max(2, min(args.steps, 10))
+    solver.write_state_ptr(host_in.data_ptr())
+    solver.step(1)
+    solver.read_state_ptr(host_out.data_ptr())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.write_state_ptr(host_in.data_ptr())
+        solver.step(1)
+        solver.read_state_ptr(host_out.data_ptr())
+    e2e_t = time.perf_counter() - t0
+    solver.close()
+
+    if rank != 0:
+        return
+    pk = peaks()
+    step_s = tot / args.steps
+    alg_bytes = 2 * nf * esize * args.n            # read + write every conserved field once
+    achieved = alg_bytes / step_s / 1e9
+    value = ws * args.n * args.steps / tot
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp32_p64": "f32"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"1D periodic MUSCL-Hancock step, N={args.n} cells, h=1/1024, "
+                               f"64 random-phase acoustic modes (k^-1, 1e-3), S=1, tau0=0.08, "
+                               f"CFL 0.4", "cells": args.n, "precision": args.precision,
+                   "l2": "flushed by a 256 MiB write before every timed step",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+                     "peak_src": f"{pk['src']} hbm_gbs (burst copy)", "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "alg_bytes_per_launch": alg_bytes},
+        "e2e": {"value": ws * args.n * e2e_steps / e2e_t, "unit": METRIC,
+                "h2d_bytes_per_step": int(host_in.numel() * 8),
+                "d2h_bytes_per_step": int(host_out.numel() * 8)},
+        "gpu_launches": args.steps,
+        "clocks": getattr(clk, "result", None),
+        "status_flags": status, "sim_time": t_sim,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(args.n, budget_s=args.cpu_budget)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_p64"])
+    ap.add_argument("--n", type=int, default=1 << 22)
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

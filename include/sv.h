@@ -1,0 +1,152 @@
+/*
+ * sv.h -- C ABI of libsv.so: a GB300 (sm_103a) solver for the MUSCL-Hancock
+ * finite-volume step of the vibrationally excited gas model of
+ * Khrapov & Khoperskov (2018), "Dynamics of unstable sound waves in a
+ * non-equilibrium medium at the nonlinear stage".
+ *
+ * Problem (Sec. 2.1): eqs. 1-4 -- continuity, momentum, total energy E with
+ * pump Q and heat sink I, vibrational energy E_nu relaxing to its equilibrium
+ * with time tau; eq. 5 (E = p/(gamma-1) + rho|v|^2/2 + E_nu); eq. 6 (tau, Q, I
+ * as power laws of rho and T about the equilibrium); eq. 7 (p = R rho T).
+ * Units (Sec. 2.3, normalisation): rho0 = p0 = R = T0 = 1; tau0 is a free
+ * parameter; Q0 = I0 = S / tau0 (S as defined under eq. 8, Q0 = I0 by the
+ * energy balance of eq. 3 at equilibrium); the equilibrium vibrational energy
+ * is E_nue = C_k rho T (C_k under eq. 8), relaxation term (rho C_k T - E_nu)/tau.
+ *
+ * Method (Sec. 2.3): MUSCL with a two-step predictor-corrector (read as
+ * MUSCL-Hancock), piecewise-linear reconstruction of the conserved variables
+ * with a TVD limiter (eq. 14, xi = 0), HLL interface fluxes (eq. 13), update
+ * with the source Y at the half step (eq. 15), time step from eq. 16.
+ *
+ * Layout.  The state has nf = dim + 3 conserved fields, in this order:
+ *   rho, rho*v_x [, rho*v_y [, rho*v_z]], E, E_nu.
+ * Host buffers are always double, field-major structure-of-arrays:
+ *   buf[f * ncell + idx], idx = i + n[0] * (j + n[1] * k), x fastest.
+ * Periodic boundaries in every axis.  All axes share one cell size
+ * h = L[0] / n[0] (the equal-step grid of Sec. 2.3).
+ *
+ * Errors.  Every call returns an int status, 0 on success, never throws.
+ * Ownership.  Host buffers belong to the caller.  Device memory belongs to
+ * the library unless the caller hands a device block to sv_init.
+ * Threading.  One handle is used by one host thread at a time.  All device
+ * work is enqueued on the CUDA stream given at sv_init; the read calls and
+ * sv_status synchronise that stream.
+ */
+#ifndef SV_H
+#define SV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes */
+#define SV_OK          0
+#define SV_EINVAL     -1   /* bad argument (null pointer, size, parameter) */
+#define SV_ENOMEM     -2   /* device allocation failed / caller block too small */
+#define SV_ECUDA      -3   /* a CUDA runtime call failed */
+#define SV_ENONPHYS   -4   /* a cell reached rho <= 0, p <= 0 or a non-finite value */
+#define SV_EDT        -5   /* the time step collapsed (dt <= 0 or non-finite) */
+#define SV_EMAXSTEPS  -7   /* sv_run_to stopped at max_steps before t_end */
+
+/* ---- status flag bits (sv_status) */
+#define SV_FLAG_NONPHYS 1u
+#define SV_FLAG_DT      2u
+
+/* ---- limiters (the paper asks for "TVD limiters" without naming one) */
+#define SV_MINMOD   0
+#define SV_VANLEER  1
+#define SV_MC       2
+
+/* ---- arithmetic of the step kernels */
+#define SV_FP32     0   /* float state and arithmetic */
+#define SV_FP64     1   /* double state and arithmetic */
+#define SV_FP32_P64 2   /* float state, pressure recovery of eq. 5 in double */
+
+typedef struct {
+  double gamma;                 /* adiabatic exponent (eq. 5) */
+  double Ck;                    /* C_k = dE_nue/(R dT) (under eq. 8) */
+  double S;                     /* degree of non-equilibrium (under eq. 8) */
+  double tau0;                  /* equilibrium relaxation time; +inf: frozen
+                                   limit (Q = I = 0, no relaxation) */
+  double tau_rho, tau_T;        /* eq. 6 exponents of tau */
+  double Q_rho, Q_T;            /* eq. 6 exponents of the pump Q */
+  double I_rho, I_T;            /* eq. 6 exponents of the sink I */
+  double cfl;                   /* factor on the eq. 16 bound, e.g. 0.4 */
+  double c_tau;                 /* dt <= c_tau * min tau (explicit source), e.g. 0.5 */
+  int limiter;                  /* SV_MINMOD, SV_VANLEER, SV_MC */
+  int precision;                /* SV_FP32, SV_FP64, SV_FP32_P64 */
+} sv_params;
+
+typedef struct {
+  int dim;                      /* 1, 2 or 3 */
+  int64_t n[3];                 /* cells per axis (unused axes ignored) */
+  double L[3];                  /* domain length per axis; L[a]/n[a] must agree */
+} sv_grid;
+
+typedef struct sv_solver sv_solver;
+
+/* Bytes of device memory one solver needs for (params, grid): two state
+   buffers, a double staging buffer for host I/O, the control block and the
+   reduction scratch.  Returns SV_EINVAL on a bad grid or parameter. */
+int sv_required_bytes(const sv_params* p, const sv_grid* g, size_t* bytes);
+
+/* Create a solver.  `cuda_stream` is a cudaStream_t (NULL: legacy default
+   stream).  `device_mem` is either NULL (the library allocates and later frees
+   its memory) or a caller-owned device block of `device_bytes` >=
+   sv_required_bytes(), 256-byte aligned, that must outlive the solver.  The
+   state starts at the uniform equilibrium rho = p = 1, v = 0,
+   E_nu = C_k + S, t = 0. */
+int sv_init(const sv_params* p, const sv_grid* g, void* cuda_stream,
+            void* device_mem, size_t device_bytes, sv_solver** out);
+
+/* Upload a state (host double SoA, nf * ncell values) and set the time to t.
+   Clears the status flags and computes the next dt (eq. 16 with the tau cap). */
+int sv_write_state(sv_solver* s, const double* host_soa, double t);
+
+/* Download the current state into host_soa (nf * ncell doubles) and its time. */
+int sv_read_state(sv_solver* s, double* host_soa, double* t);
+
+/* The dt the next step will take: cfl * h / max_j max(2|v_j|, |v_j| + c_j)
+   (eq. 16), capped by c_tau * min_j tau_j and by the pending t_end. */
+int sv_dt_cfl(sv_solver* s, double* dt);
+
+/* Advance exactly nsteps MUSCL-Hancock steps (eqs. 13-15), each with the dt
+   computed on the device from the state it starts from.  Asynchronous on the
+   solver's stream; errors of the steps show up in sv_status. */
+int sv_step(sv_solver* s, int64_t nsteps);
+
+/* Advance until t_end, the last step clamped to land on t_end, or until
+   max_steps steps.  Synchronous.  Returns SV_EMAXSTEPS if stopped early,
+   SV_ENONPHYS / SV_EDT if the run failed (the state of the failing step is
+   kept).  *steps_taken (may be NULL) receives the number of steps. */
+int sv_run_to(sv_solver* s, double t_end, int64_t max_steps, int64_t* steps_taken);
+
+/* Current time and number of steps taken since the last sv_write_state. */
+int sv_time(sv_solver* s, double* t, int64_t* steps);
+
+/* Sums over all cells of each conserved field (nf doubles), accumulated in
+   double with compensated (Neumaier) summation.  Synchronous. */
+int sv_conservation(sv_solver* s, double* sums);
+
+/* Status flags (SV_FLAG_*) accumulated since the last sv_write_state.
+   Synchronous. */
+int sv_status(sv_solver* s, uint32_t* flags);
+
+/* Device pointer of the current state buffer (nf * ncell elements of the
+   solver's precision, field-major), valid until the next step.  For callers
+   that keep data on the device. */
+int sv_state_device(sv_solver* s, void** dev_ptr, int* elem_bytes);
+
+/* Release the solver (waits for its stream). */
+void sv_free(sv_solver* s);
+
+/* Human-readable name of a status code. */
+const char* sv_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

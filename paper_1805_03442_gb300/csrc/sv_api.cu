@@ -1,0 +1,378 @@
+// sv_api.cu -- host runtime behind the C ABI of include/sv.h.
+//
+// One solver = one device block carved into: two state buffers (ping-pong),
+// a double staging buffer for host I/O, the control block (time, dt,
+// reductions, current buffer, flags) and the scratch of the conservation sums.
+// Steps are launched on the caller's stream; runs of steps are replayed from a
+// CUDA graph captured once per solver.  The device decides dt, the clamp to
+// t_end and the buffer flip, so nothing is read back between steps.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "sv.h"
+#include "sv_internal.h"
+#include "sv_model.cuh"
+
+using namespace sv;
+
+struct sv_solver {
+  sv_params p;
+  sv_grid g;
+  int dim = 1, nf = 4, esize = 4;
+  int64_t ncell = 0;
+  double h = 0;
+  KParams kp;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
+  void* mem = nullptr;
+  bool owns_mem = false;
+  void* buf[2] = {nullptr, nullptr};
+  double* staging = nullptr;
+  Ctl* ctl = nullptr;
+  double* partial = nullptr;
+  double* sums_out = nullptr;
+  Ctl* host_ctl = nullptr;             // pinned mirror of the control block
+  double* host_sums = nullptr;
+  int grid = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_len = 0;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kGraphLen = 32;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t state, staging, ctl, partial, sums, total;
+};
+
+int check_inputs(const sv_params* p, const sv_grid* g) {
+  if (!p || !g) return SV_EINVAL;
+  if (g->dim < 1 || g->dim > 3) return SV_EINVAL;
+  for (int a = 0; a < g->dim; ++a)
+    if (g->n[a] < 1 || !(g->L[a] > 0.0)) return SV_EINVAL;
+  const double h = g->L[0] / (double)g->n[0];
+  for (int a = 1; a < g->dim; ++a)
+    if (fabs(g->L[a] / (double)g->n[a] - h) > 1e-12 * h) return SV_EINVAL;
+  if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->c_tau > 0.0) || !(p->tau0 > 0.0))
+    return SV_EINVAL;
+  if (p->limiter < SV_MINMOD || p->limiter > SV_MC) return SV_EINVAL;
+  if (p->precision < SV_FP32 || p->precision > SV_FP32_P64) return SV_EINVAL;
+  return SV_OK;
+}
+
+Layout layout(const sv_params* p, const sv_grid* g) {
+  int64_t ncell = 1;
+  for (int a = 0; a < g->dim; ++a) ncell *= g->n[a];
+  const int nf = g->dim + 3;
+  const size_t es = p->precision == SV_FP64 ? 8 : 4;
+  Layout L;
+  L.state = align_up((size_t)nf * (size_t)ncell * es);
+  L.staging = align_up((size_t)nf * (size_t)ncell * 8);
+  L.ctl = align_up(sizeof(Ctl));
+  L.partial = align_up((size_t)sums_blocks() * (size_t)nf * 2 * 8);
+  L.sums = align_up(8 * 8);
+  L.total = 2 * L.state + L.staging + L.ctl + L.partial + L.sums;
+  return L;
+}
+
+#define SV_TRY(expr)                         \
+  do {                                       \
+    cudaError_t e_ = (expr);                 \
+    if (e_ != cudaSuccess) return SV_ECUDA;  \
+  } while (0)
+
+cudaError_t launch_step(sv_solver* s, cudaStream_t st) {
+  if (s->dim == 1)
+    return step1d_launch(s->p.precision, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell, s->grid, st);
+  return stepnd_launch(s->dim, s->p.precision, s->kp, s->buf[0], s->buf[1], s->ctl, s->g.n,
+                       s->grid, st);
+}
+
+int ensure_graph(sv_solver* s) {
+  if (s->graph) return SV_OK;
+  cudaGraph_t gr = nullptr;
+  SV_TRY(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = cudaSuccess;
+  for (int i = 0; i < kGraphLen && le == cudaSuccess; ++i) le = launch_step(s, s->cap_stream);
+  cudaError_t ee = cudaStreamEndCapture(s->cap_stream, &gr);
+  if (le != cudaSuccess || ee != cudaSuccess) {
+    if (gr) cudaGraphDestroy(gr);
+    return SV_ECUDA;
+  }
+  cudaError_t ie = cudaGraphInstantiate(&s->graph, gr, 0);
+  cudaGraphDestroy(gr);
+  if (ie != cudaSuccess) {
+    s->graph = nullptr;
+    return SV_ECUDA;
+  }
+  s->graph_len = kGraphLen;
+  return SV_OK;
+}
+
+int issue_steps(sv_solver* s, int64_t n) {
+  if (n <= 0) return SV_OK;
+  if (n >= kGraphLen) {
+    int rc = ensure_graph(s);
+    if (rc != SV_OK) return rc;
+    while (n >= s->graph_len) {
+      SV_TRY(cudaGraphLaunch(s->graph, s->stream));
+      n -= s->graph_len;
+    }
+  }
+  for (int64_t i = 0; i < n; ++i) SV_TRY(launch_step(s, s->stream));
+  return SV_OK;
+}
+
+int read_ctl(sv_solver* s) {
+  SV_TRY(cudaMemcpyAsync(s->host_ctl, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
+  SV_TRY(cudaStreamSynchronize(s->stream));
+  return SV_OK;
+}
+
+int flags_to_status(uint32_t f) {
+  if (f & FLAG_NONPHYS) return SV_ENONPHYS;
+  if (f & FLAG_DT) return SV_EDT;
+  return SV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sv_required_bytes(const sv_params* p, const sv_grid* g, size_t* bytes) {
+  int rc = check_inputs(p, g);
+  if (rc != SV_OK) return rc;
+  if (!bytes) return SV_EINVAL;
+  *bytes = layout(p, g).total;
+  return SV_OK;
+}
+
+int sv_init(const sv_params* p, const sv_grid* g, void* cuda_stream, void* device_mem,
+            size_t device_bytes, sv_solver** out) {
+  if (!out) return SV_EINVAL;
+  *out = nullptr;
+  int rc = check_inputs(p, g);
+  if (rc != SV_OK) return rc;
+  const Layout L = layout(p, g);
+  if (device_mem && (device_bytes < L.total || ((uintptr_t)device_mem % kAlign) != 0))
+    return SV_ENOMEM;
+
+  sv_solver* s = new (std::nothrow) sv_solver();
+  if (!s) return SV_ENOMEM;
+  s->p = *p;
+  s->g = *g;
+  s->dim = g->dim;
+  s->nf = g->dim + 3;
+  s->esize = p->precision == SV_FP64 ? 8 : 4;
+  s->ncell = 1;
+  for (int a = 0; a < g->dim; ++a) s->ncell *= g->n[a];
+  s->h = g->L[0] / (double)g->n[0];
+  s->stream = (cudaStream_t)cuda_stream;
+
+  KParams& k = s->kp;
+  k.gamma = p->gamma;
+  k.g1 = p->gamma - 1.0;
+  k.Ck = p->Ck;
+  k.frozen = isinf(p->tau0) ? 1 : 0;
+  k.tau0 = p->tau0;
+  k.inv_tau0 = k.frozen ? 0.0 : 1.0 / p->tau0;
+  k.Q0 = k.frozen ? 0.0 : p->S / p->tau0;   // S = tau0 Q0 / (R T0), R = T0 = 1
+  k.tau_rho = p->tau_rho;
+  k.tau_T = p->tau_T;
+  k.Q_rho = p->Q_rho;
+  k.Q_T = p->Q_T;
+  k.I_rho = p->I_rho;
+  k.I_T = p->I_T;
+  k.qi_zero = (p->Q_rho == 0.0 && p->Q_T == 0.0 && p->I_rho == 0.0 && p->I_T == 0.0) ? 1 : 0;
+  k.h = s->h;
+  k.cfl = p->cfl;
+  k.c_tau = p->c_tau;
+  k.limiter = p->limiter;
+
+  if (device_mem) {
+    s->mem = device_mem;
+  } else {
+    if (cudaMalloc(&s->mem, L.total) != cudaSuccess) {
+      delete s;
+      return SV_ENOMEM;
+    }
+    s->owns_mem = true;
+  }
+  char* m = (char*)s->mem;
+  s->buf[0] = m;
+  s->buf[1] = m + L.state;
+  s->staging = (double*)(m + 2 * L.state);
+  s->ctl = (Ctl*)(m + 2 * L.state + L.staging);
+  s->partial = (double*)(m + 2 * L.state + L.staging + L.ctl);
+  s->sums_out = (double*)(m + 2 * L.state + L.staging + L.ctl + L.partial);
+
+  rc = SV_OK;
+  if (cudaMallocHost((void**)&s->host_ctl, sizeof(Ctl)) != cudaSuccess ||
+      cudaMallocHost((void**)&s->host_sums, 8 * sizeof(double)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    rc = SV_ECUDA;
+  if (rc == SV_OK) {
+    s->grid = s->dim == 1 ? step1d_grid(p->precision) : stepnd_grid(s->dim, p->precision);
+    if (s->grid < 1) rc = SV_ECUDA;
+  }
+  if (rc == SV_OK) {
+    // uniform equilibrium start: rho = p = 1, v = 0, E_nu = C_k + S
+    if (ctl_reset_launch(s->ctl, 0.0, s->stream) != cudaSuccess ||
+        fill_equilibrium_launch(s->p.precision, s->buf[0], s->nf, s->ncell, p->gamma,
+                                p->Ck + p->S, s->stream) != cudaSuccess ||
+        dt_reduce_launch(s->p.precision, s->dim, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell,
+                         s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+      rc = SV_ECUDA;
+  }
+  if (rc != SV_OK) {
+    sv_free(s);
+    return rc;
+  }
+  *out = s;
+  return SV_OK;
+}
+
+int sv_write_state(sv_solver* s, const double* host_soa, double t) {
+  if (!s || !host_soa) return SV_EINVAL;
+  const size_t count = (size_t)s->nf * (size_t)s->ncell;
+  SV_TRY(cudaMemcpyAsync(s->staging, host_soa, count * sizeof(double), cudaMemcpyHostToDevice,
+                         s->stream));
+  SV_TRY(ctl_reset_launch(s->ctl, t, s->stream));
+  SV_TRY(to_state_launch(s->p.precision, s->staging, s->buf[0], s->buf[1], s->ctl, (int64_t)count,
+                         s->stream));
+  SV_TRY(dt_reduce_launch(s->p.precision, s->dim, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell,
+                          s->stream));
+  return SV_OK;
+}
+
+int sv_read_state(sv_solver* s, double* host_soa, double* t) {
+  if (!s || !host_soa) return SV_EINVAL;
+  const size_t count = (size_t)s->nf * (size_t)s->ncell;
+  SV_TRY(from_state_launch(s->p.precision, s->buf[0], s->buf[1], s->ctl, s->staging,
+                           (int64_t)count, s->stream));
+  SV_TRY(cudaMemcpyAsync(host_soa, s->staging, count * sizeof(double), cudaMemcpyDeviceToHost,
+                         s->stream));
+  int rc = read_ctl(s);
+  if (rc != SV_OK) return rc;
+  if (t) *t = s->host_ctl->t;
+  return SV_OK;
+}
+
+int sv_dt_cfl(sv_solver* s, double* dt) {
+  if (!s || !dt) return SV_EINVAL;
+  int rc = read_ctl(s);
+  if (rc != SV_OK) return rc;
+  *dt = s->host_ctl->dt;
+  return SV_OK;
+}
+
+int sv_step(sv_solver* s, int64_t nsteps) {
+  if (!s || nsteps < 0) return SV_EINVAL;
+  return issue_steps(s, nsteps);
+}
+
+int sv_run_to(sv_solver* s, double t_end, int64_t max_steps, int64_t* steps_taken) {
+  if (!s || max_steps < 0 || isnan(t_end)) return SV_EINVAL;
+  SV_TRY(set_target_launch(s->ctl, t_end, s->stream));
+  int rc = read_ctl(s);
+  if (rc != SV_OK) return rc;
+  const int64_t n0 = s->host_ctl->nsteps;
+  int64_t issued = 0;
+  int status = SV_OK;
+  for (;;) {
+    const Ctl& c = *s->host_ctl;
+    const int64_t done = c.nsteps - n0;
+    if (c.flags) { status = flags_to_status(c.flags); break; }
+    if (!(c.t < t_end) || !(c.dt > 0.0)) break;
+    if (done >= max_steps) { status = SV_EMAXSTEPS; break; }
+    // steps still needed at the current dt, bounded by the remaining budget;
+    // launches issued after the run ends return at once on the device.
+    double est = ceil((t_end - c.t) / (c.dt_cfl > 0.0 ? c.dt_cfl : c.dt));
+    if (!(est >= 1.0)) est = 1.0;
+    int64_t n = est > 1e15 ? (int64_t)1e15 : (int64_t)est;
+    n = n > 4096 ? 4096 : n;
+    if (n > max_steps - done) n = max_steps - done;
+    if (n < 1) n = 1;
+    rc = issue_steps(s, n);
+    if (rc != SV_OK) return rc;
+    issued += n;
+    rc = read_ctl(s);
+    if (rc != SV_OK) return rc;
+  }
+  (void)issued;
+  if (steps_taken) *steps_taken = s->host_ctl->nsteps - n0;
+  // clear the target so that later sv_step calls are not clamped
+  SV_TRY(set_target_launch(s->ctl, INFINITY, s->stream));
+  return status;
+}
+
+int sv_time(sv_solver* s, double* t, int64_t* steps) {
+  if (!s) return SV_EINVAL;
+  int rc = read_ctl(s);
+  if (rc != SV_OK) return rc;
+  if (t) *t = s->host_ctl->t;
+  if (steps) *steps = s->host_ctl->nsteps;
+  return SV_OK;
+}
+
+int sv_conservation(sv_solver* s, double* sums) {
+  if (!s || !sums) return SV_EINVAL;
+  SV_TRY(sums_launch(s->p.precision, s->buf[0], s->buf[1], s->ctl, s->nf, s->ncell, s->partial,
+                     sums_blocks(), s->sums_out, s->stream));
+  SV_TRY(cudaMemcpyAsync(s->host_sums, s->sums_out, s->nf * sizeof(double), cudaMemcpyDeviceToHost,
+                         s->stream));
+  SV_TRY(cudaStreamSynchronize(s->stream));
+  memcpy(sums, s->host_sums, s->nf * sizeof(double));
+  return SV_OK;
+}
+
+int sv_status(sv_solver* s, uint32_t* flags) {
+  if (!s || !flags) return SV_EINVAL;
+  int rc = read_ctl(s);
+  if (rc != SV_OK) return rc;
+  *flags = s->host_ctl->flags;
+  return SV_OK;
+}
+
+int sv_state_device(sv_solver* s, void** dev_ptr, int* elem_bytes) {
+  if (!s || !dev_ptr) return SV_EINVAL;
+  int rc = read_ctl(s);
+  if (rc != SV_OK) return rc;
+  *dev_ptr = s->buf[s->host_ctl->cur ? 1 : 0];
+  if (elem_bytes) *elem_bytes = s->esize;
+  return SV_OK;
+}
+
+void sv_free(sv_solver* s) {
+  if (!s) return;
+  if (s->stream || s->mem) cudaStreamSynchronize(s->stream);
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  if (s->owns_mem && s->mem) cudaFree(s->mem);
+  if (s->host_ctl) cudaFreeHost(s->host_ctl);
+  if (s->host_sums) cudaFreeHost(s->host_sums);
+  delete s;
+}
+
+const char* sv_strerror(int code) {
+  switch (code) {
+    case SV_OK: return "ok";
+    case SV_EINVAL: return "invalid argument";
+    case SV_ENOMEM: return "out of device memory or caller block too small";
+    case SV_ECUDA: return "CUDA runtime error";
+    case SV_ENONPHYS: return "non-physical state (rho <= 0, p <= 0 or non-finite)";
+    case SV_EDT: return "time step collapsed";
+    case SV_EMAXSTEPS: return "max_steps reached before t_end";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

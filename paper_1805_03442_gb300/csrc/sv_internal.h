@@ -1,0 +1,41 @@
+// sv_internal.h -- declarations shared by the host runtime and the kernel
+// translation units of libsv.so (not part of the public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sv {
+
+struct KParams;
+struct Ctl;
+
+enum { PREC_FP32 = 0, PREC_FP64 = 1, PREC_FP32_P64 = 2 };
+
+// 1D fused step (sv_step1d.cu)
+int step1d_grid(int precision);
+cudaError_t step1d_launch(int precision, const KParams& kp, void* a, void* b, Ctl* ctl, int64_t N,
+                          int grid, cudaStream_t st);
+
+// 2D / 3D fused steps (sv_stepnd.cu); n[] cells per axis
+int stepnd_grid(int dim, int precision);
+cudaError_t stepnd_launch(int dim, int precision, const KParams& kp, void* a, void* b, Ctl* ctl,
+                          const int64_t* n, int grid, cudaStream_t st);
+
+// Utility kernels (sv_util.cu)
+cudaError_t ctl_reset_launch(Ctl* ctl, double t, cudaStream_t st);
+cudaError_t dt_reduce_launch(int precision, int dim, const KParams& kp, const void* a,
+                             const void* b, Ctl* ctl, int64_t ncell, cudaStream_t st);
+cudaError_t set_target_launch(Ctl* ctl, double t_end, cudaStream_t st);
+cudaError_t to_state_launch(int precision, const double* src, void* a, void* b, Ctl* ctl,
+                            int64_t count, cudaStream_t st);
+cudaError_t from_state_launch(int precision, const void* a, const void* b, const Ctl* ctl,
+                              double* dst, int64_t count, cudaStream_t st);
+cudaError_t sums_launch(int precision, const void* a, const void* b, const Ctl* ctl, int nf,
+                        int64_t ncell, double* partial, int nblocks, double* out,
+                        cudaStream_t st);
+int sums_blocks();
+cudaError_t fill_equilibrium_launch(int precision, void* a, int nf, int64_t ncell, double gamma,
+                                    double ev0, cudaStream_t st);
+
+}  // namespace sv

@@ -1,0 +1,169 @@
+// sv_model.cuh -- device-side physics of the vibrationally excited gas model
+// (Khrapov & Khoperskov 2018) used by every step kernel.
+//
+//   eq. 5   pressure recovery      p = (gamma-1) (E - rho|v|^2/2 - E_nu)
+//   eq. 7   temperature            T = p / rho              (R = 1)
+//   eq. 6   closures               tau = tau0 rho^tau_rho T^tau_T, Q, I alike
+//   MUSCL Y (Sec. 2.3, f = 0)      Y_E    = rho (Q - I)
+//                                  Y_E_nu = (rho C_k T - E_nu) / tau + rho Q
+//   F/G of eq. 15                  (rho v_a, rho v v_a + p e_a, v_a (E + p), v_a E_nu)
+//   eq. 13                         HLL flux with Davis speed estimates
+//
+// Everything is templated on the arithmetic type R (float or double).  The
+// float instantiation uses the SFU approximations (rcp, rsqrt, lg2, ex2); the
+// double instantiation uses IEEE division, sqrt and pow.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+namespace sv {
+
+// Kernel-side parameter block, passed by value.
+struct KParams {
+  double gamma, g1, Ck, Q0, tau0, inv_tau0;
+  double tau_rho, tau_T, Q_rho, Q_T, I_rho, I_T;
+  double h, cfl, c_tau;
+  int limiter;   // 0 minmod, 1 van Leer, 2 MC
+  int frozen;    // 1: no source at all (Q = I = 0, 1/tau = 0)
+  int qi_zero;   // 1: all Q and I exponents are zero (Q = I = Q0)
+};
+
+// Device control block: time, step size and the reductions of one solver.
+struct Ctl {
+  double t;            // current time
+  double dt;           // dt of the next step (0: stopped / reached t_end)
+  double dt_cfl;       // unclamped eq.-16 dt of the current state
+  double t_end;        // target time of the running sv_run_to (+inf otherwise)
+  int64_t nsteps;      // steps taken since the last state upload
+  uint32_t cur;        // which of the two state buffers is current
+  uint32_t last;       // 1: the next step lands exactly on t_end
+  uint32_t flags;      // SV_FLAG_* bits
+  uint32_t ticket;     // blocks finished in the running launch
+  uint64_t smax_key;   // order-preserving key of max signal speed
+  uint64_t tau_key;    // order-preserving key of the tau bound (see finalize)
+  double pad[4];
+};
+
+constexpr uint32_t FLAG_NONPHYS = 1u;
+constexpr uint32_t FLAG_DT = 2u;
+
+// ---------------------------------------------------------------- arithmetic
+
+template <typename R> struct Ar;
+
+template <> struct Ar<float> {
+  static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+  static __device__ __forceinline__ float sqrt_pos(float x) { return x * rsqrtf(x); }
+  static __device__ __forceinline__ float lg2(float x) { return __log2f(x); }
+  static __device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
+};
+
+template <> struct Ar<double> {
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double sqrt_pos(double x) { return sqrt(x); }
+};
+
+// Parameters converted once to the kernel's arithmetic type.
+template <typename R> struct P {
+  R gamma, g1, Ck, Q0, inv_tau0, tau0;
+  R tau_rho, tau_T, Q_rho, Q_T, I_rho, I_T;
+  int limiter, frozen, qi_zero;
+  __device__ __forceinline__ explicit P(const KParams& k)
+      : gamma((R)k.gamma), g1((R)k.g1), Ck((R)k.Ck), Q0((R)k.Q0), inv_tau0((R)k.inv_tau0),
+        tau0((R)k.tau0), tau_rho((R)k.tau_rho), tau_T((R)k.tau_T), Q_rho((R)k.Q_rho),
+        Q_T((R)k.Q_T), I_rho((R)k.I_rho), I_T((R)k.I_T), limiter(k.limiter),
+        frozen(k.frozen), qi_zero(k.qi_zero) {}
+};
+
+// ---------------------------------------------------------------- eq. 5
+
+// Pressure policies of the float kernels: PP = 0 all-float, PP = 1 the
+// subtraction of eq. 5 carried out in double.
+template <typename R, int PP>
+__device__ __forceinline__ R pressure(const P<R>& k, R kin2, R E, R Ev) {
+  // kin2 = rho |v|^2 (twice the kinetic energy density)
+  if (PP == 1) {
+    return (R)((double)k.g1 * ((double)E - 0.5 * (double)kin2 - (double)Ev));
+  }
+  return k.g1 * (E - (R)0.5 * kin2 - Ev);
+}
+
+// ---------------------------------------------------------------- limiter
+
+template <typename R>
+__device__ __forceinline__ R limit(int kind, R a, R b) {
+  R ab = a * b;
+  if (!(ab > (R)0)) return (R)0;
+  if (kind == 1) return (R)2 * ab / (a + b);
+  R m = fmin(fabs(a), fabs(b));
+  if (kind == 2) m = fmin((R)2 * m, (R)0.5 * fabs(a + b));
+  return copysign(m, a);
+}
+
+template <>
+__device__ __forceinline__ float limit<float>(int kind, float a, float b) {
+  float ab = a * b;
+  float m = fminf(fabsf(a), fabsf(b));
+  if (kind == 1) m = __fdividef(2.0f * ab, fabsf(a + b));
+  if (kind == 2) m = fminf(2.0f * m, 0.5f * fabsf(a + b));
+  return ab > 0.0f ? copysignf(m, a) : 0.0f;
+}
+
+// ---------------------------------------------------------------- source Y
+
+// Components E and E_nu of Y (the others vanish with f = 0).
+template <typename R> struct Src;
+
+template <> struct Src<float> {
+  static __device__ __forceinline__ void eval(const P<float>& k, float rho, float T, float Ev,
+                                              float& yE, float& yEv) {
+    float lr = Ar<float>::lg2(rho), lT = Ar<float>::lg2(T);
+    float inv_tau = k.inv_tau0 * Ar<float>::ex2(-fmaf(k.tau_rho, lr, k.tau_T * lT));
+    float Q = k.Q0, I = k.Q0;
+    if (!k.qi_zero) {
+      Q = k.Q0 * Ar<float>::ex2(fmaf(k.Q_rho, lr, k.Q_T * lT));
+      I = k.Q0 * Ar<float>::ex2(fmaf(k.I_rho, lr, k.I_T * lT));
+    }
+    yE = rho * (Q - I);
+    yEv = fmaf(rho * k.Ck, T, -Ev) * inv_tau + rho * Q;
+  }
+};
+
+template <> struct Src<double> {
+  static __device__ __forceinline__ void eval(const P<double>& k, double rho, double T, double Ev,
+                                              double& yE, double& yEv) {
+    double tau = k.tau0 * pow(rho, k.tau_rho) * pow(T, k.tau_T);
+    double Q = k.Q0, I = k.Q0;
+    if (!k.qi_zero) {
+      Q = k.Q0 * pow(rho, k.Q_rho) * pow(T, k.Q_T);
+      I = k.Q0 * pow(rho, k.I_rho) * pow(T, k.I_T);
+    }
+    yE = rho * (Q - I);
+    yEv = (rho * k.Ck * T - Ev) / tau + rho * Q;
+  }
+};
+
+// Order-preserving unsigned keys so that atomicMax/atomicMin order floats.
+__device__ __forceinline__ uint64_t key_of(double x) {
+  uint64_t b = (uint64_t)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__host__ __device__ __forceinline__ double key_to_double(uint64_t k) {
+  uint64_t b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double d;
+  memcpy(&d, &b, sizeof d);
+  return d;
+#endif
+}
+
+}  // namespace sv

@@ -1,0 +1,151 @@
+// sv_reduce.cuh -- the time-step reduction shared by the step kernels.
+//
+// Every step kernel ends by folding, over the cells it wrote, the two
+// quantities that bound the next time step:
+//   s_j  = max(2|v_j|, |v_j| + c_j)           (eq. 16, c the frozen sound speed)
+//   a tau bound per cell (see TauKey below)    (explicit source: dt <= c_tau tau)
+// Warp shuffles, then shared memory, then one atomicMax per block into the
+// solver's control block.  The last block to finish (ticket counter, with a
+// fence before the ticket) turns the maxima into the next dt, advances t and
+// flips the current state buffer: the host never has to read anything to keep
+// stepping, so K steps can be replayed from a CUDA graph.
+#pragma once
+
+#include "sv_model.cuh"
+
+namespace sv {
+
+// The tau bound travels as a double to maximise.
+//   float kernels:  a_j = -(tau_rho log2 rho + tau_T log2 T), tau_j = tau0 2^-a_j
+//   double kernels: a_j = -tau_j (tau_j from pow, as in the closure of eq. 6)
+template <typename R> struct TauKey;
+template <> struct TauKey<float> {
+  static __device__ __forceinline__ double of(const P<float>& k, float rho, float T) {
+    return (double)(-fmaf(k.tau_rho, Ar<float>::lg2(rho), k.tau_T * Ar<float>::lg2(T)));
+  }
+  static __device__ __forceinline__ double tau_min(const KParams& kp, double a) {
+    return kp.tau0 * exp2(-a);
+  }
+};
+template <> struct TauKey<double> {
+  static __device__ __forceinline__ double of(const P<double>& k, double rho, double T) {
+    return -(k.tau0 * pow(rho, k.tau_rho) * pow(T, k.tau_T));
+  }
+  static __device__ __forceinline__ double tau_min(const KParams&, double a) { return -a; }
+};
+
+// Signal speed, tau key and physicality of one updated state (dim-generic).
+// `kin2` = rho |v|^2, `vmag` = |v|.
+template <typename R, int PP>
+__device__ __forceinline__ void cfl_cell(const P<R>& k, R rho, R kin2, R vmag, R E, R Ev,
+                                         double& smax, double& akey, uint32_t& flags) {
+  R p = pressure<R, PP>(k, kin2, E, Ev);
+  R ir = Ar<R>::rcp(rho);
+  bool phys = (rho > (R)0) && (p > (R)0);
+  if (!phys) {
+    flags |= FLAG_NONPHYS;
+    smax = (double)NAN;
+    return;
+  }
+  R c = Ar<R>::sqrt_pos(k.gamma * p * ir);
+  R s = fmax((R)2 * vmag, vmag + c);
+  smax = fmax(smax, (double)s);
+  if (!k.frozen) akey = fmax(akey, TauKey<R>::of(k, rho, p * ir));
+}
+
+// Read a control field written by other blocks in this launch or by the
+// previous launch, bypassing L1.
+template <typename T>
+__device__ __forceinline__ T vload(const T* p) {
+  return *(const volatile T*)p;
+}
+
+// Turn the reduced maxima into the next dt (eq. 16 capped by c_tau tau and by
+// t_end).  `advance` = the kernel just completed a step.
+template <typename R>
+__device__ void finalize(Ctl* ctl, const KParams& kp, bool advance) {
+  __threadfence();
+  const double smax = key_to_double(atomicExch((unsigned long long*)&ctl->smax_key,
+                                               (unsigned long long)key_of(0.0)));
+  const double akey = key_to_double(atomicExch((unsigned long long*)&ctl->tau_key,
+                                               (unsigned long long)key_of(-INFINITY)));
+  uint32_t flags = atomicOr(&ctl->flags, 0u);
+  double dt = kp.cfl * kp.h / smax;
+  if (!kp.frozen) {
+    double taumin = TauKey<R>::tau_min(kp, akey);
+    if (kp.c_tau * taumin < dt) dt = kp.c_tau * taumin;
+  }
+  if (!(dt > 0.0) || !isfinite(dt)) flags |= FLAG_DT;
+  double t = vload(&ctl->t);
+  const double t_end = vload(&ctl->t_end);
+  if (advance) {
+    t = vload(&ctl->last) ? t_end : t + vload(&ctl->dt);
+    ctl->cur = vload(&ctl->cur) ^ 1u;
+    ctl->nsteps = vload(&ctl->nsteps) + 1;
+  }
+  uint32_t last = 0;
+  double dtn = dt;
+  if (flags) {
+    dtn = 0.0;
+  } else if (!(t < t_end)) {
+    dtn = 0.0;
+  } else if (dt >= t_end - t) {
+    dtn = t_end - t;
+    last = 1;
+  }
+  ctl->t = t;
+  ctl->dt_cfl = dt;
+  ctl->dt = dtn;
+  ctl->last = last;
+  ctl->flags = flags;
+  __threadfence();
+  atomicExch(&ctl->ticket, 0u);
+}
+
+// Block-wide fold of (smax, akey, flags) followed by the last-block finalize.
+// Must be called by every thread of the block, after its last store.
+template <typename R, int NT>
+__device__ __forceinline__ void reduce_and_finalize(Ctl* ctl, const KParams& kp, double smax,
+                                                    double akey, uint32_t flags, bool advance) {
+  __shared__ double s_s[NT / 32], s_a[NT / 32];
+  __shared__ uint32_t s_f[NT / 32];
+  __shared__ bool s_last;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    akey = fmax(akey, __shfl_xor_sync(0xffffffffu, akey, o));
+    flags |= __shfl_xor_sync(0xffffffffu, flags, o);
+  }
+  // fmax drops NaN: a non-physical cell already raised its flag.
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    s_s[w] = smax;
+    s_a[w] = akey;
+    s_f[w] = flags;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < NT / 32; ++i) {
+      smax = fmax(smax, s_s[i]);
+      akey = fmax(akey, s_a[i]);
+      flags |= s_f[i];
+    }
+    atomicMax((unsigned long long*)&ctl->smax_key, (unsigned long long)key_of(smax));
+    atomicMax((unsigned long long*)&ctl->tau_key, (unsigned long long)key_of(akey));
+    if (flags) atomicOr(&ctl->flags, flags);
+    __threadfence();
+    const uint32_t ticket = atomicAdd(&ctl->ticket, 1u);
+    s_last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) finalize<R>(ctl, kp, advance);
+}
+
+// Periodic index for |j| within a few periods of [0, N).
+__device__ __forceinline__ int64_t wrap(int64_t j, int64_t N) {
+  if (j >= 0 && j < N) return j;
+  j %= N;
+  return j < 0 ? j + N : j;
+}
+
+}  // namespace sv

@@ -62,13 +62,20 @@ def waves_1d(gamma: float, N: int, L: float, base, modes: list[Mode]) -> np.ndar
     """Conserved (4, N) state: base primitive (rho0, p0, e_nu0) plus sum of modes,
     as point values at cell centres."""
     rho0, p0, ev0 = base
-    x = cell_centres(N, L)
     pert = np.zeros((4, N))
-    for md in modes:
-        k = 2.0 * math.pi * md.m / L
-        ph = np.exp(1j * k * x)
-        for f in range(4):
-            pert[f] += np.real(md.scale * md.shape[f] * ph)
+    if all(0 < md.m < N // 2 for md in modes):
+        # sum of Re(a e^{i 2 pi m (j + 1/2) / N}) by one inverse real FFT per field
+        spec = np.zeros((4, N // 2 + 1), dtype=complex)
+        for md in modes:
+            shift = np.exp(1j * math.pi * md.m / N)          # cell centres at (j + 1/2) h
+            spec[:, md.m] += md.scale * np.asarray(md.shape) * shift * (N / 2.0)
+        pert = np.fft.irfft(spec, n=N, axis=1)
+    else:
+        x = cell_centres(N, L)
+        for md in modes:
+            ph = np.exp(1j * (2.0 * math.pi * md.m / L) * x)
+            for f in range(4):
+                pert[f] += np.real(md.scale * md.shape[f] * ph)
     return prim_to_cons(gamma, rho0 + pert[0], [pert[1]], p0 + pert[2], ev0 + pert[3])
 
 

@@ -1,0 +1,243 @@
+"""ctypes binding of libsv.so (include/sv.h): argument marshalling only.
+
+Every step of the solver runs in the library's CUDA kernels.  PyTorch is used
+for device memory (the solver's device block is a torch uint8 tensor) and for
+the stream the work is enqueued on.  There is no CPU fallback: if libsv.so is
+missing or no CUDA device is present, constructing a Solver raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass, fields
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsv.so")
+
+SV_OK, SV_EINVAL, SV_ENOMEM, SV_ECUDA, SV_ENONPHYS, SV_EDT, SV_EMAXSTEPS = 0, -1, -2, -3, -4, -5, -7
+FLAG_NONPHYS, FLAG_DT = 1, 2
+MINMOD, VANLEER, MC = 0, 1, 2
+FP32, FP64, FP32_P64 = 0, 1, 2
+
+EXPORTS = ("sv_required_bytes", "sv_init", "sv_write_state", "sv_read_state", "sv_dt_cfl",
+           "sv_step", "sv_run_to", "sv_time", "sv_conservation", "sv_status",
+           "sv_state_device", "sv_free", "sv_strerror")
+
+
+class SvError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {code} ({strerror(code)})")
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("gamma", "Ck", "S", "tau0", "tau_rho", "tau_T", "Q_rho", "Q_T", "I_rho", "I_T",
+                 "cfl", "c_tau")] + [("limiter", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("L", ctypes.c_double * 3)]
+
+
+@dataclass
+class Params:
+    """sv_params.  Defaults: gamma 1.4, C_k 0.1, tau_rho -1, tau_T -1.5, Q/I
+    exponents 0 (the 1D runs of the paper), S 1, tau0 0.08, CFL 0.4."""
+    gamma: float = 1.4
+    Ck: float = 0.1
+    S: float = 1.0
+    tau0: float = 0.08
+    tau_rho: float = -1.0
+    tau_T: float = -1.5
+    Q_rho: float = 0.0
+    Q_T: float = 0.0
+    I_rho: float = 0.0
+    I_T: float = 0.0
+    cfl: float = 0.4
+    c_tau: float = 0.5
+    limiter: int = MINMOD
+    precision: int = FP32
+
+    def c(self) -> _Params:
+        return _Params(*[getattr(self, f.name) for f in fields(self)])
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsv.so (built by paper_1805_03442_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run paper_1805_03442_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+    L.sv_required_bytes.argtypes = [ctypes.POINTER(_Params), ctypes.POINTER(_Grid),
+                                    ctypes.POINTER(ctypes.c_size_t)]
+    L.sv_init.argtypes = [ctypes.POINTER(_Params), ctypes.POINTER(_Grid), vp, vp, ctypes.c_size_t,
+                          ctypes.POINTER(vp)]
+    L.sv_write_state.argtypes = [vp, dp, ctypes.c_double]
+    L.sv_read_state.argtypes = [vp, dp, dp]
+    L.sv_dt_cfl.argtypes = [vp, dp]
+    L.sv_step.argtypes = [vp, ctypes.c_int64]
+    L.sv_run_to.argtypes = [vp, ctypes.c_double, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+    L.sv_time.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64)]
+    L.sv_conservation.argtypes = [vp, dp]
+    L.sv_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
+    L.sv_state_device.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int)]
+    L.sv_free.argtypes = [vp]
+    L.sv_free.restype = None
+    L.sv_strerror.argtypes = [ctypes.c_int]
+    L.sv_strerror.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().sv_strerror(code).decode()
+    except RuntimeError:
+        return "?"
+
+
+def _check(rc: int, what: str) -> int:
+    if rc != SV_OK:
+        raise SvError(rc, what)
+    return rc
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def grid(n, L=None) -> _Grid:
+    n = tuple(int(x) for x in (n if hasattr(n, "__len__") else (n,)))
+    if L is None:
+        L = tuple(float(x) / n[0] for x in n)          # h = 1 / n[0]
+    L = tuple(float(x) for x in (L if hasattr(L, "__len__") else (L,)))
+    g = _Grid()
+    g.dim = len(n)
+    for a in range(3):
+        g.n[a] = n[a] if a < len(n) else 1
+        g.L[a] = L[a] if a < len(L) else 1.0
+    return g
+
+
+class Solver:
+    """One periodic grid advanced by the fused MUSCL-Hancock kernels.
+
+    n: cells per axis (tuple of 1-3 ints), L: lengths per axis (equal cell size).
+    memory="torch" backs the solver's device block by a torch uint8 tensor;
+    memory="library" lets libsv allocate it.  stream: a torch.cuda.Stream, or
+    None for torch's current stream."""
+
+    def __init__(self, params: Params, n, L=None, stream=None, memory: str = "torch"):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the solver has no CPU path")
+        self.params = params
+        self.g = grid(n, L)
+        self.dim = self.g.dim
+        self.n = tuple(self.g.n[a] for a in range(self.dim))
+        self.nf = self.dim + 3
+        self.ncell = int(np.prod(self.n))
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        pc = params.c()
+        nbytes = ctypes.c_size_t()
+        _check(lib().sv_required_bytes(ctypes.byref(pc), ctypes.byref(self.g), ctypes.byref(nbytes)),
+               "sv_required_bytes")
+        self.device_bytes = nbytes.value
+        self._mem = None
+        dev_ptr = None
+        if memory == "torch":
+            self._mem = torch.empty(self.device_bytes, dtype=torch.uint8, device="cuda")
+            dev_ptr = self._mem.data_ptr()
+        h = ctypes.c_void_p()
+        _check(lib().sv_init(ctypes.byref(pc), ctypes.byref(self.g),
+                             ctypes.c_void_p(self._stream.cuda_stream), dev_ptr,
+                             self.device_bytes, ctypes.byref(h)), "sv_init")
+        self._h = h
+
+    # ------------------------------------------------------------ lifecycle
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sv_free(self._h)
+            self._h = None
+        self._mem = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------ I/O
+    def write_state(self, U: np.ndarray, t: float = 0.0):
+        U = np.ascontiguousarray(U, dtype=np.float64).reshape(self.nf, self.ncell)
+        _check(lib().sv_write_state(self._h, _dp(U), float(t)), "sv_write_state")
+
+    def write_state_ptr(self, host_ptr: int, t: float = 0.0):
+        """Upload from a host address (e.g. a pinned torch tensor's data_ptr)."""
+        _check(lib().sv_write_state(self._h, ctypes.cast(host_ptr, ctypes.POINTER(ctypes.c_double)),
+                                    float(t)), "sv_write_state")
+
+    def read_state(self) -> tuple[np.ndarray, float]:
+        U = np.empty((self.nf, self.ncell))
+        t = ctypes.c_double()
+        _check(lib().sv_read_state(self._h, _dp(U), ctypes.byref(t)), "sv_read_state")
+        return U, t.value
+
+    def read_state_ptr(self, host_ptr: int) -> float:
+        t = ctypes.c_double()
+        _check(lib().sv_read_state(self._h, ctypes.cast(host_ptr, ctypes.POINTER(ctypes.c_double)),
+                                   ctypes.byref(t)), "sv_read_state")
+        return t.value
+
+    # ------------------------------------------------------------ stepping
+    def dt(self) -> float:
+        d = ctypes.c_double()
+        _check(lib().sv_dt_cfl(self._h, ctypes.byref(d)), "sv_dt_cfl")
+        return d.value
+
+    def step(self, nsteps: int = 1):
+        _check(lib().sv_step(self._h, int(nsteps)), "sv_step")
+
+    def run_to(self, t_end: float, max_steps: int = 1 << 62, check: bool = True) -> tuple[int, int]:
+        k = ctypes.c_int64()
+        rc = lib().sv_run_to(self._h, float(t_end), int(max_steps), ctypes.byref(k))
+        if check and rc not in (SV_OK,):
+            raise SvError(rc, "sv_run_to")
+        return rc, k.value
+
+    def time(self) -> tuple[float, int]:
+        t, k = ctypes.c_double(), ctypes.c_int64()
+        _check(lib().sv_time(self._h, ctypes.byref(t), ctypes.byref(k)), "sv_time")
+        return t.value, k.value
+
+    def conservation(self) -> np.ndarray:
+        out = np.empty(self.nf)
+        _check(lib().sv_conservation(self._h, _dp(out)), "sv_conservation")
+        return out
+
+    def status(self) -> int:
+        f = ctypes.c_uint32()
+        _check(lib().sv_status(self._h, ctypes.byref(f)), "sv_status")
+        return f.value
+
+    def state_device(self):
+        """(device pointer, element bytes) of the current state buffer."""
+        p, e = ctypes.c_void_p(), ctypes.c_int()
+        _check(lib().sv_state_device(self._h, ctypes.byref(p), ctypes.byref(e)), "sv_state_device")
+        return p.value, e.value

@@ -1,0 +1,283 @@
+"""Parity of the fused 1D CUDA step (through the C ABI) with the FP64 oracle.
+
+Tolerances:
+* FP64 kernels: relative L-infinity <= 1e-12 per field (the kernel and the
+  oracle differ only in rounding order: FMA contraction, reciprocal-multiply
+  instead of division, pow implementations -- a few ulp per operation, far
+  below 1e-12 unless an instability amplifies it).
+* FP32 kernels: the state is stored in float (unit roundoff 6e-8) and the
+  approximate SFU reciprocal / sqrt / log2 / exp2 carry up to ~2 ulp each; a
+  step changes each cell by dt/h * flux differences of O(1), so one step's
+  error is O(10 ulp) of the field scale: <= 2e-6 per field after one step.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_util import need_gpu, oracle_params, primitives, rel_linf
+from oracle import dispersion as D
+from oracle import orc as O
+from oracle.riemann import Riemann
+from paper_1805_03442_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sv():
+    return need_gpu()
+
+
+def _one_step(sv, P, U0, N, h, nsteps=1):
+    with sv.Solver(P, (N,), (N * h,)) as s:
+        s.write_state(U0)
+        dts = []
+        for _ in range(nsteps):
+            dts.append(s.dt())
+            s.step(1)
+        U, t = s.read_state()
+        assert s.status() == 0
+    return U, t, dts
+
+
+def _oracle_steps(Po, U0, N, h, nsteps):
+    U = U0.copy()
+    dts = []
+    for _ in range(nsteps):
+        dt = O.dt_cfl(Po, U, N, h)
+        dts.append(dt)
+        U, rc = O.step(Po, U, N, h, dt)
+        assert rc == 0
+    return U, dts
+
+
+@pytest.mark.parametrize("N", [5, 8, 33, 1000, 4099, 70001])
+@pytest.mark.parametrize("params", [dict(tau0=0.3),
+                                    dict(tau0=0.05, S=0.7, Q_rho=0.4, Q_T=-0.3, I_rho=0.2, I_T=0.5),
+                                    dict(tau0=math.inf, S=0.0)])
+def test_fp64_steps_match_oracle(sv, N, params):
+    P = sv.Params(precision=sv.FP64, **params)
+    Po = oracle_params(P)
+    h = 1.0 / N
+    U0 = inputs.random_states(1, N, seed=N, smooth=True)
+    U, t, dts = _one_step(sv, P, U0, N, h, nsteps=3)
+    ref, rdts = _oracle_steps(Po, U0, N, h, 3)
+    assert np.allclose(dts, rdts, rtol=1e-13, atol=0)
+    assert t == pytest.approx(sum(rdts), rel=1e-14)
+    assert rel_linf(U, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("limiter", [sv_l for sv_l in (1, 2)])
+def test_fp64_other_limiters(sv, limiter):
+    N = 257
+    P = sv.Params(precision=sv.FP64, tau0=0.2, limiter=limiter)
+    Po = oracle_params(P)
+    U0 = inputs.random_states(1, N, seed=3, smooth=True)
+    U, _, _ = _one_step(sv, P, U0, N, 1.0 / N, nsteps=2)
+    ref, _ = _oracle_steps(Po, U0, N, 1.0 / N, 2)
+    assert rel_linf(U, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", ["FP32", "FP32_P64"])
+@pytest.mark.parametrize("N", [5, 33, 1000, 4099])
+def test_fp32_one_step(sv, precision, N):
+    P = sv.Params(precision=getattr(sv, precision), tau0=0.3)
+    Po = oracle_params(P)
+    h = 1.0 / N
+    U0 = inputs.random_states(1, N, seed=N + 1, smooth=True)
+    U0 = U0.astype(np.float32).astype(np.float64)       # start from float-representable values
+    U, _, dts = _one_step(sv, P, U0, N, h)
+    ref, rdts = _oracle_steps(Po, U0, N, h, 1)
+    assert dts[0] == pytest.approx(rdts[0], rel=1e-5)
+    # same dt on both sides so that only the step's arithmetic is compared
+    ref, _ = O.step(Po, U0, N, h, dts[0])
+    assert rel_linf(U, ref) <= 2e-6
+
+
+def test_graph_replay_equals_single_launches(sv):
+    N = 3000
+    P = sv.Params(precision=sv.FP32, tau0=0.1)
+    U0 = inputs.random_states(1, N, seed=5, smooth=True)
+    with sv.Solver(P, (N,)) as a, sv.Solver(P, (N,)) as b:
+        a.write_state(U0)
+        b.write_state(U0)
+        a.step(70)                    # two graph replays of 32 + 6 launches
+        for _ in range(70):
+            b.step(1)
+        Ua, ta = a.read_state()
+        Ub, tb = b.read_state()
+    assert ta == tb
+    assert np.array_equal(Ua, Ub)
+
+
+def test_equilibrium_stationary_and_conserved(sv):
+    N = 4096
+    for prec in (sv.FP64, sv.FP32):
+        P = sv.Params(precision=prec, S=0.7, tau0=0.2, Q_rho=0.3, I_T=-0.2)
+        with sv.Solver(P, (N,)) as s:           # starts at the uniform equilibrium
+            U0, _ = s.read_state()
+            s.step(50)
+            U, t = s.read_state()
+            assert t > 0
+        assert np.array_equal(U[:2], U0[:2])     # fluxes cancel exactly
+        tol = 1e-14 if prec == sv.FP64 else 2e-6
+        assert rel_linf(U, U0) <= tol
+
+
+@pytest.mark.parametrize("prec,tol", [("FP64", 1e-13), ("FP32", 1e-6)])
+def test_mass_momentum_conservation(sv, prec, tol):
+    N = 10007
+    P = sv.Params(precision=getattr(sv, prec), tau0=0.1)
+    U0 = inputs.random_states(1, N, seed=9, smooth=True)
+    with sv.Solver(P, (N,)) as s:
+        s.write_state(U0)
+        c0 = s.conservation()
+        s.step(200)
+        c1 = s.conservation()
+        assert s.status() == 0
+    for f in (0, 1):
+        assert abs(c1[f] - c0[f]) <= tol * np.sum(np.abs(U0[f]))
+    assert c0[0] == pytest.approx(math.fsum(U0[0].astype(np.float32 if prec == "FP32" else np.float64)),
+                                  rel=1e-12)
+
+
+def test_run_to_lands_on_t_end_like_the_oracle(sv):
+    N = 512
+    P = sv.Params(precision=sv.FP64, tau0=0.08)
+    Po = oracle_params(P)
+    U0 = inputs.random_states(1, N, seed=12, smooth=True)
+    with sv.Solver(P, (N,)) as s:
+        s.write_state(U0)
+        rc, k = s.run_to(0.0371)
+        U, t = s.read_state()
+    ref, tr, kr, rcr = O.run(Po, U0, N, 1.0 / N, 0.0371)
+    assert rc == 0 and rcr == 0
+    assert t == 0.0371 and tr == 0.0371
+    assert k == kr
+    assert rel_linf(U, ref) <= 1e-12
+
+
+def test_max_steps_and_nonphysical_status(sv):
+    N = 256
+    P = sv.Params(precision=sv.FP32, tau0=0.2)
+    U0 = inputs.random_states(1, N, seed=2, smooth=True)
+    with sv.Solver(P, (N,)) as s:
+        s.write_state(U0)
+        rc, k = s.run_to(10.0, max_steps=7, check=False)
+        assert rc == sv.SV_EMAXSTEPS and k == 7
+        bad = U0.copy()
+        bad[0, 100] = -1.0                      # host-injected negative density
+        s.write_state(bad)
+        rc, _ = s.run_to(1.0, check=False)
+        assert rc in (sv.SV_ENONPHYS, sv.SV_EDT)
+        assert s.status() != 0
+        s.write_state(U0)                        # the solver stays usable
+        rc, _ = s.run_to(0.01, check=False)
+        assert rc == 0 and s.status() == 0
+
+
+def test_fp64_unstable_eigenmode_parity(sv):
+    """Config of the linear-stage run: N = 1024 on one wavelength, tau0 0.08,
+    S = 1, growing eigenmode of amplitude 1e-4.  Pointwise FP64 parity holds
+    while rounding noise stays below the tolerance after amplification
+    (t <= 2 here: growth of noise at most ~e^(2.2 t))."""
+    N = 1024
+    P = sv.Params(precision=sv.FP64, tau0=0.08)
+    Po = oracle_params(P)
+    k = 2 * math.pi
+    w = D.growing_acoustic_root(Po, k)
+    md = D.eigenmode(Po, k, w)
+    U0 = inputs.waves_1d(P.gamma, N, 1.0, inputs.equilibrium_primitive(P.Ck, P.S),
+                         [inputs.Mode(m=1, shape=md["prim"], scale=1e-4)])
+    with sv.Solver(P, (N,)) as s:
+        s.write_state(U0)
+        rc, k_steps = s.run_to(2.0)
+        U, t = s.read_state()
+    ref, tr, kr, _ = O.run(Po, U0, N, 1.0 / N, 2.0)
+    assert k_steps == kr and t == tr
+    assert rel_linf(U, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["FP32", "FP64"])
+def test_growth_rate_matches_eq8(sv, prec):
+    """Linear growth of the fundamental within 2% of Im omega from eq. 8."""
+    N = 1024
+    P = sv.Params(precision=getattr(sv, prec), tau0=0.08)
+    Po = oracle_params(P)
+    k = 2 * math.pi
+    w = D.growing_acoustic_root(Po, k)
+    md = D.eigenmode(Po, k, w)
+    U0 = inputs.waves_1d(P.gamma, N, 1.0, inputs.equilibrium_primitive(P.Ck, P.S),
+                         [inputs.Mode(m=1, shape=md["prim"], scale=1e-4)])
+    x = inputs.cell_centres(N, 1.0)
+    ts, amps = [], []
+    with sv.Solver(P, (N,)) as s:
+        s.write_state(U0)
+        t = 0.0
+        while t < math.log(100.0) / w.imag:
+            s.run_to(t + 0.05)
+            U, t = s.read_state()
+            ts.append(t)
+            amps.append(np.sum(U[1] / U[0] * np.exp(-1j * k * x)) / N)
+    growth = np.polyfit(ts, np.log(np.abs(amps)), 1)[0]
+    freq = -np.polyfit(ts, np.unwrap(np.angle(amps)), 1)[0]
+    assert abs(growth - w.imag) <= 0.02 * w.imag
+    assert abs(freq - w.real) <= 0.01 * w.real
+
+
+@pytest.mark.parametrize("prec", ["FP32", "FP64"])
+def test_frozen_double_tube_vs_exact(sv, prec):
+    """Frozen limit: post-shock plateau density L1 <= 1e-3, shock within one cell."""
+    N, L, t_end = 800, 1.0, 0.1
+    h = L / N
+    P = sv.Params(precision=getattr(sv, prec), tau0=math.inf, S=0.0)
+    outer, inner = (1.0, 0.0, 1.0, 0.3), (0.125, 0.0, 0.1, 0.9)
+    U0 = inputs.double_tube_1d(P.gamma, N, L, outer, inner)
+    with sv.Solver(P, (N,), (L,)) as s:
+        s.write_state(U0)
+        s.run_to(t_end)
+        U, t = s.read_state()
+    assert t == t_end
+    x = inputs.cell_centres(N, L)
+    R = Riemann(P.gamma, *outer[:3], *inner[:3], evL=outer[3], evR=inner[3])
+    ex = R.sample_array((x - 0.25) / t_end)
+    _, _, c, _, sp = R.wave_speeds()
+    xc, xs = 0.25 + c * t_end, 0.25 + sp * t_end
+    plateau = (x > xc + 10 * h) & (x < xs - 3 * h)
+    assert np.mean(np.abs(U[0][plateau] - ex[0][plateau])) <= 1e-3
+    half = 0.5 * (R.star_densities()[1] + inner[0])
+    i = np.where((x > xc) & (x < 0.5) & (U[0] < half))[0][0]
+    xsh = x[i - 1] + (half - U[0][i - 1]) / (U[0][i] - U[0][i - 1]) * h
+    assert abs(xsh - xs) <= h
+    if prec == "FP64":
+        ref, _, _, _ = O.run(oracle_params(P, S=0.0), U0, N, h, t_end)
+        assert rel_linf(U, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("prec,tol", [("FP64", 1e-12), ("FP32", 2e-6)])
+def test_full_size_sampled_parity(sv, prec, tol):
+    """At the benchmark size (N = 2^22, launch configuration of the benchmark),
+    one step checked on sampled cells against the oracle computing them one by one."""
+    N = 1 << 22
+    P = sv.Params(precision=getattr(sv, prec), tau0=0.08)
+    Po = oracle_params(P)
+    h = 1.0 / 1024
+    rng = np.random.default_rng(4)
+    modes = inputs.random_phase_modes(11, inputs.acoustic_shape(P.gamma), 64, 4096 // 32, 1e-3,
+                                      m_step=4096 // 32)
+    U0 = inputs.waves_1d(P.gamma, N, N * h, inputs.equilibrium_primitive(P.Ck, P.S), modes)
+    if prec == "FP32":
+        U0 = U0.astype(np.float32).astype(np.float64)
+    with sv.Solver(P, (N,), (N * h,)) as s:
+        s.write_state(U0)
+        dt = s.dt()
+        s.step(1)
+        U, _ = s.read_state()
+    idx = np.unique(np.concatenate([[0, 1, 2, 31, 32, 33, N - 1, N - 2, N - 33],
+                                    rng.integers(0, N, 200)]))
+    scale = np.max(np.abs(U0), axis=1)
+    for i in idx:
+        ref = O.step_cell(Po, U0, N, h, dt, int(i))
+        err = np.max(np.abs(U[:, i] - ref) / scale)
+        assert err <= tol, (i, err)
