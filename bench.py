@@ -45,6 +45,34 @@ def workload(n_cells: int, gamma: float, Ck: float, S: float):
     return U0, h, L
 
 
+# Workloads: name -> (grid, params, description).  The 1D line is the default.
+WORKLOADS = {
+    "1d": dict(dims=lambda a: (a.n,), params=dict(tau0=0.08, S=1.0, cfl=0.4),
+               desc="1D periodic MUSCL-Hancock step, N={cells} cells, h=1/1024, 64 random-phase "
+                    "acoustic modes (k^-1, 1e-3), S=1, tau0=0.08, CFL 0.4"),
+    "2d": dict(dims=lambda a: (8192, 8192), params=dict(tau0=0.01, S=1.0, cfl=0.4),
+               desc="2D periodic unsplit MUSCL-Hancock step, 8192x8192, plane wave (7,4) at 29.7 deg "
+                    "amplitude 1e-3 + white noise 1e-5, S=1, tau0=0.01, CFL 0.4"),
+    "3d": dict(dims=lambda a: (512, 512, 512), params=dict(tau0=0.08, S=1.0, cfl=0.3),
+               desc="3D periodic unsplit MUSCL-Hancock step, 512^3, isotropic k^-2 random density/"
+                    "velocity perturbations amplitude 1e-3, S=1, tau0=0.08, CFL 0.3"),
+}
+
+
+def make_state(name: str, dims, gamma: float, Ck: float, S: float):
+    """Initial state (nf, ncell) float64, cell size h, lengths L."""
+    from paper_1805_03442_gb300 import inputs
+    base = inputs.equilibrium_primitive(Ck, S)
+    if name == "1d":
+        U0, h, L = workload(dims[0], gamma, Ck, S)
+        return U0, h, (L,)
+    n = dims[0]
+    h = 1.0 / n
+    if name == "2d":
+        return inputs.plane_wave_2d(gamma, dims[0], dims[1], 1.0, base, 7, 4, 1e-3, 1e-5, 3), h, (1.0, 1.0)
+    return inputs.random_field_3d(gamma, n, 1.0, base, 1e-3, seed=5), h, (1.0, 1.0, 1.0)
+
+
 def peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -104,23 +132,31 @@ class Clocks:
                            "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(n_cells: int, budget_s: float = 10.0) -> dict:
+def cpu_baseline(name: str, args, budget_s: float = 10.0) -> dict:
     """The FP64 oracle, as it stands, on the same workload: whole-grid steps
-    until `budget_s` of wall time (at least one)."""
+    until `budget_s` of wall time (at least one).  2D / 3D use a periodic
+    sub-grid of the same generator (2048^2 / 128^3) to stay within budget."""
     from oracle import orc as O
-    P = O.Params(tau0=0.08, S=1.0)
-    U, h, _ = workload(n_cells, P.gamma, P.Ck, P.S)
+    W = WORKLOADS[name]
+    P = O.Params(**W["params"])
+    dims = W["dims"](args)
+    if name == "2d":
+        dims = (2048, 2048)
+    elif name == "3d":
+        dims = (128, 128, 128)
+    U, h, _ = make_state(name, dims, P.gamma, P.Ck, P.S)
+    ncell = int(np.prod(dims))
     steps, t0 = 0, time.perf_counter()
     while True:
-        dt = O.dt_cfl(P, U, n_cells, h)
-        U, rc = O.step(P, U, n_cells, h, dt)
+        dt = O.dt_cfl(P, U, dims, h)
+        U, rc = O.step(P, U, dims, h, dt)
         steps += 1
         el = time.perf_counter() - t0
         if el >= budget_s:
             break
-    return {"value": n_cells * steps / el, "unit": METRIC, "cores": O.threads(), "kind": "oracle",
-            "sample": f"{steps} whole-grid FP64 oracle steps of the same N={n_cells} workload "
-                      f"({el:.1f} s wall)"}
+    return {"value": ncell * steps / el, "unit": METRIC, "cores": O.threads(), "kind": "oracle",
+            "sample": f"{steps} whole-grid FP64 oracle steps of the {name} workload on "
+                      f"{'x'.join(map(str, dims))} cells ({el:.1f} s wall)"}
 
 
 def dist_init():
@@ -144,24 +180,28 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import orc as O
-    P = O.Params(tau0=0.08, S=1.0)
-    U, h, _ = workload(args.n, P.gamma, P.Ck, P.S)
+    W = WORKLOADS[args.workload]
+    P = O.Params(**W["params"])
+    dims = W["dims"](args)
+    U, h, _ = make_state(args.workload, dims, P.gamma, P.Ck, P.S)
+    ncell = int(np.prod(dims))
     for _ in range(args.warmup):
-        U, _ = O.step(P, U, args.n, h, O.dt_cfl(P, U, args.n, h))
+        U, _ = O.step(P, U, dims, h, O.dt_cfl(P, U, dims, h))
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        U, _ = O.step(P, U, args.n, h, O.dt_cfl(P, U, args.n, h))
+        U, _ = O.step(P, U, dims, h, O.dt_cfl(P, U, dims, h))
         times.append(time.perf_counter() - t0)
     tot = sum(times)
-    value = args.n * args.steps / tot
+    value = ncell * args.steps / tot
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"1D periodic MUSCL-Hancock, N={args.n}", "cells": args.n},
+            "config": {"workload": W["desc"].format(cells=ncell), "cells": ncell},
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": O.threads(), "kind": "oracle",
-                             "sample": f"{args.steps} whole-grid FP64 oracle steps"},
+                             "sample": f"{args.steps} whole-grid FP64 oracle steps of the same "
+                                       f"workload"},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -179,11 +219,14 @@ def run_ours(args):
         dist.barrier()
     prec = {"fp32": sv.FP32, "fp64": sv.FP64, "fp32_p64": sv.FP32_P64}[args.precision]
     esize = 8 if prec == sv.FP64 else 4
-    P = sv.Params(precision=prec, tau0=0.08, S=1.0)
-    U0, h, L = workload(args.n, P.gamma, P.Ck, P.S)
+    W = WORKLOADS[args.workload]
+    P = sv.Params(precision=prec, **W["params"])
+    dims = W["dims"](args)
+    ncell = int(np.prod(dims))
+    U0, h, L = make_state(args.workload, dims, P.gamma, P.Ck, P.S)
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    solver = sv.Solver(P, (args.n,), (L,), stream=stream)
+    solver = sv.Solver(P, dims, L, stream=stream)
     solver.write_state(U0)
     torch.cuda.synchronize()
     for _ in range(args.warmup):
@@ -217,7 +260,7 @@ def run_ours(args):
     t_sim, nsteps = solver.time()
 
     # end to end through the C ABI: pinned host FP64 state in, one step, state out
-    nf = 4
+    nf = len(dims) + 3
     host_in = torch.from_numpy(U0.reshape(-1)).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     e2e_steps = max(2, min(args.steps, 10))
@@ -237,25 +280,24 @@ def run_ours(args):
         return
     pk = peaks()
     step_s = tot / args.steps
-    alg_bytes = 2 * nf * esize * args.n            # read + write every conserved field once
+    alg_bytes = 2 * nf * esize * ncell             # read + write every conserved field once
     achieved = alg_bytes / step_s / 1e9
-    value = ws * args.n * args.steps / tot
+    value = ws * ncell * args.steps / tot
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "fp32_p64": "f32"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": f"1D periodic MUSCL-Hancock step, N={args.n} cells, h=1/1024, "
-                               f"64 random-phase acoustic modes (k^-1, 1e-3), S=1, tau0=0.08, "
-                               f"CFL 0.4", "cells": args.n, "precision": args.precision,
+        "config": {"workload": W["desc"].format(cells=ncell), "cells": ncell,
+                   "precision": args.precision,
                    "l2": "flushed by a 256 MiB write before every timed step",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
                      "peak_src": f"{pk['src']} hbm_gbs (burst copy)", "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": None,
                      "alg_bytes_per_launch": alg_bytes},
-        "e2e": {"value": ws * args.n * e2e_steps / e2e_t, "unit": METRIC,
+        "e2e": {"value": ws * ncell * e2e_steps / e2e_t, "unit": METRIC,
                 "h2d_bytes_per_step": int(host_in.numel() * 8),
                 "d2h_bytes_per_step": int(host_out.numel() * 8)},
         "gpu_launches": args.steps,
@@ -263,7 +305,7 @@ def run_ours(args):
         "status_flags": status, "sim_time": t_sim,
     }
     if not args.no_cpu_baseline and ws == 1:
-        line["cpu_baseline"] = cpu_baseline(args.n, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline(args.workload, args, budget_s=args.cpu_budget)
     print(json.dumps(line), flush=True)
 
 
@@ -274,7 +316,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_p64"])
-    ap.add_argument("--n", type=int, default=1 << 22)
+    ap.add_argument("--n", type=int, default=1 << 22, help="cells of the 1d workload")
+    ap.add_argument("--workload", default="1d", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -219,7 +219,7 @@ int sv_init(const sv_params* p, const sv_grid* g, void* cuda_stream, void* devic
       cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     rc = SV_ECUDA;
   if (rc == SV_OK) {
-    s->grid = s->dim == 1 ? step1d_grid(p->precision) : stepnd_grid(s->dim, p->precision);
+    s->grid = s->dim == 1 ? step1d_grid(s->kp, p->precision) : stepnd_grid(s->dim, p->precision, s->kp);
     if (s->grid < 1) rc = SV_ECUDA;
   }
   if (rc == SV_OK) {

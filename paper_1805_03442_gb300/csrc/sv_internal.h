@@ -13,12 +13,12 @@ struct Ctl;
 enum { PREC_FP32 = 0, PREC_FP64 = 1, PREC_FP32_P64 = 2 };
 
 // 1D fused step (sv_step1d.cu)
-int step1d_grid(int precision);
+int step1d_grid(const KParams& kp, int precision);
 cudaError_t step1d_launch(int precision, const KParams& kp, void* a, void* b, Ctl* ctl, int64_t N,
                           int grid, cudaStream_t st);
 
 // 2D / 3D fused steps (sv_stepnd.cu); n[] cells per axis
-int stepnd_grid(int dim, int precision);
+int stepnd_grid(int dim, int precision, const KParams& kp);
 cudaError_t stepnd_launch(int dim, int precision, const KParams& kp, void* a, void* b, Ctl* ctl,
                           const int64_t* n, int grid, cudaStream_t st);
 

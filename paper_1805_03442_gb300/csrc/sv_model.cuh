@@ -19,6 +19,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <type_traits>
+
 namespace sv {
 
 // Kernel-side parameter block, passed by value.
@@ -97,51 +99,59 @@ __device__ __forceinline__ R pressure(const P<R>& k, R kin2, R E, R Ev) {
 
 // ---------------------------------------------------------------- limiter
 
-template <typename R>
-__device__ __forceinline__ R limit(int kind, R a, R b) {
-  R ab = a * b;
-  if (!(ab > (R)0)) return (R)0;
-  if (kind == 1) return (R)2 * ab / (a + b);
-  R m = fmin(fabs(a), fabs(b));
-  if (kind == 2) m = fmin((R)2 * m, (R)0.5 * fabs(a + b));
-  return copysign(m, a);
-}
-
-template <>
-__device__ __forceinline__ float limit<float>(int kind, float a, float b) {
-  float ab = a * b;
-  float m = fminf(fabsf(a), fabsf(b));
-  if (kind == 1) m = __fdividef(2.0f * ab, fabsf(a + b));
-  if (kind == 2) m = fminf(2.0f * m, 0.5f * fabsf(a + b));
-  return ab > 0.0f ? copysignf(m, a) : 0.0f;
+// TVD slope limiters on the two one-sided differences a, b (eq. 14 asks for
+// "limiter functions" without naming one): LIM 0 minmod, 1 van Leer, 2 MC.
+template <int LIM, typename R>
+__device__ __forceinline__ R limit(R a, R b) {
+  const R ab = a * b;
+  R m;
+  if (LIM == 1) {
+    if constexpr (std::is_same<R, float>::value) m = __fdividef(2.0f * ab, fabsf(a + b));
+    else m = (R)2 * ab / fabs(a + b);
+  } else {
+    m = fmin(fabs(a), fabs(b));
+    if (LIM == 2) m = fmin((R)2 * m, (R)0.5 * fabs(a + b));
+  }
+  return ab > (R)0 ? copysign(m, a) : (R)0;
 }
 
 // ---------------------------------------------------------------- source Y
 
 // Components E and E_nu of Y (the others vanish with f = 0).
-template <typename R> struct Src;
+// SRC 0: frozen limit (no source); 1: Q and I exponents all zero (Q = I = Q0,
+// so rho (Q - I) = 0); 2: general closures of eq. 6.
+template <typename R, int SRC> struct Src;
 
-template <> struct Src<float> {
+template <int SRC> struct Src<float, SRC> {
   static __device__ __forceinline__ void eval(const P<float>& k, float rho, float T, float Ev,
                                               float& yE, float& yEv) {
-    float lr = Ar<float>::lg2(rho), lT = Ar<float>::lg2(T);
-    float inv_tau = k.inv_tau0 * Ar<float>::ex2(-fmaf(k.tau_rho, lr, k.tau_T * lT));
-    float Q = k.Q0, I = k.Q0;
-    if (!k.qi_zero) {
-      Q = k.Q0 * Ar<float>::ex2(fmaf(k.Q_rho, lr, k.Q_T * lT));
-      I = k.Q0 * Ar<float>::ex2(fmaf(k.I_rho, lr, k.I_T * lT));
+    if (SRC == 0) {
+      yE = yEv = 0.0f;
+      return;
     }
-    yE = rho * (Q - I);
+    const float lr = Ar<float>::lg2(rho), lT = Ar<float>::lg2(T);
+    const float inv_tau = k.inv_tau0 * Ar<float>::ex2(-fmaf(k.tau_rho, lr, k.tau_T * lT));
+    float Q = k.Q0;
+    yE = 0.0f;
+    if (SRC == 2) {
+      Q = k.Q0 * Ar<float>::ex2(fmaf(k.Q_rho, lr, k.Q_T * lT));
+      const float I = k.Q0 * Ar<float>::ex2(fmaf(k.I_rho, lr, k.I_T * lT));
+      yE = rho * (Q - I);
+    }
     yEv = fmaf(rho * k.Ck, T, -Ev) * inv_tau + rho * Q;
   }
 };
 
-template <> struct Src<double> {
+template <int SRC> struct Src<double, SRC> {
   static __device__ __forceinline__ void eval(const P<double>& k, double rho, double T, double Ev,
                                               double& yE, double& yEv) {
-    double tau = k.tau0 * pow(rho, k.tau_rho) * pow(T, k.tau_T);
+    if (SRC == 0) {
+      yE = yEv = 0.0;
+      return;
+    }
+    const double tau = k.tau0 * pow(rho, k.tau_rho) * pow(T, k.tau_T);
     double Q = k.Q0, I = k.Q0;
-    if (!k.qi_zero) {
+    if (SRC == 2) {
       Q = k.Q0 * pow(rho, k.Q_rho) * pow(T, k.Q_T);
       I = k.Q0 * pow(rho, k.I_rho) * pow(T, k.I_T);
     }

@@ -15,13 +15,13 @@
 
 namespace sv {
 
-// The tau bound travels as a double to maximise.
+// The tau bound is folded as a maximum:
 //   float kernels:  a_j = -(tau_rho log2 rho + tau_T log2 T), tau_j = tau0 2^-a_j
 //   double kernels: a_j = -tau_j (tau_j from pow, as in the closure of eq. 6)
 template <typename R> struct TauKey;
 template <> struct TauKey<float> {
-  static __device__ __forceinline__ double of(const P<float>& k, float rho, float T) {
-    return (double)(-fmaf(k.tau_rho, Ar<float>::lg2(rho), k.tau_T * Ar<float>::lg2(T)));
+  static __device__ __forceinline__ float of(const P<float>& k, float rho, float T) {
+    return -fmaf(k.tau_rho, Ar<float>::lg2(rho), k.tau_T * Ar<float>::lg2(T));
   }
   static __device__ __forceinline__ double tau_min(const KParams& kp, double a) {
     return kp.tau0 * exp2(-a);
@@ -34,23 +34,21 @@ template <> struct TauKey<double> {
   static __device__ __forceinline__ double tau_min(const KParams&, double a) { return -a; }
 };
 
-// Signal speed, tau key and physicality of one updated state (dim-generic).
-// `kin2` = rho |v|^2, `vmag` = |v|.
-template <typename R, int PP>
+// Signal speed, tau key and physicality of one updated state (dim-generic),
+// folded into per-thread maxima of the kernel's own type.
+// `kin2` = rho |v|^2, `vmag` = |v|.  SRC 0 (frozen) has no tau bound.
+template <typename R, int PP, int SRC>
 __device__ __forceinline__ void cfl_cell(const P<R>& k, R rho, R kin2, R vmag, R E, R Ev,
-                                         double& smax, double& akey, uint32_t& flags) {
-  R p = pressure<R, PP>(k, kin2, E, Ev);
-  R ir = Ar<R>::rcp(rho);
-  bool phys = (rho > (R)0) && (p > (R)0);
-  if (!phys) {
+                                         R& smax, R& akey, uint32_t& flags) {
+  const R p = pressure<R, PP>(k, kin2, E, Ev);
+  const R ir = Ar<R>::rcp(rho);
+  if (!((rho > (R)0) && (p > (R)0))) {
     flags |= FLAG_NONPHYS;
-    smax = (double)NAN;
     return;
   }
-  R c = Ar<R>::sqrt_pos(k.gamma * p * ir);
-  R s = fmax((R)2 * vmag, vmag + c);
-  smax = fmax(smax, (double)s);
-  if (!k.frozen) akey = fmax(akey, TauKey<R>::of(k, rho, p * ir));
+  const R c = Ar<R>::sqrt_pos(k.gamma * p * ir);
+  smax = fmax(smax, fmax((R)2 * vmag, vmag + c));
+  if (SRC != 0) akey = fmax(akey, TauKey<R>::of(k, rho, p * ir));
 }
 
 // Read a control field written by other blocks in this launch or by the

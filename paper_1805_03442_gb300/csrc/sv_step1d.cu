@@ -26,9 +26,9 @@ namespace sv {
 
 constexpr int NT1 = 256;
 
+// Offsets are 32-bit: the host rejects grids with nf * ncell >= 2^31.
 template <typename R>
-__device__ __forceinline__ void load_cell(const R* __restrict__ U, int64_t N, int64_t j, R (&u)[4]) {
-  const int64_t i = wrap(j, N);
+__device__ __forceinline__ void load_cell(const R* __restrict__ U, int N, int i, R (&u)[4]) {
 #pragma unroll
   for (int f = 0; f < 4; ++f) u[f] = __ldg(U + f * N + i);
 }
@@ -36,14 +36,14 @@ __device__ __forceinline__ void load_cell(const R* __restrict__ U, int64_t N, in
 // Steps 1-3 for one cell: slopes d (= Theta h), predictor, face states
 // wp = U^{n+1/2} + d/2 (right face), wm = U^{n+1/2} - d/2 (left face), and the
 // source at U^{n+1/2} (E and E_nu components).
-template <typename R, int PP>
+template <typename R, int PP, int LIM, int SRC>
 __device__ __forceinline__ void predict(const P<R>& k, const R (&u)[4], const R (&um)[4],
                                         const R (&up)[4], R dt_2h, R dt_2, R (&wp)[4], R (&wm)[4],
                                         R& yEh, R& yEvh) {
   R d[4], a[4], b[4];
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
-    d[f] = limit<R>(k.limiter, u[f] - um[f], up[f] - u[f]);
+    d[f] = limit<LIM, R>(u[f] - um[f], up[f] - u[f]);
     a[f] = u[f] + (R)0.5 * d[f];
     b[f] = u[f] - (R)0.5 * d[f];
   }
@@ -61,10 +61,10 @@ __device__ __forceinline__ void predict(const P<R>& k, const R (&u)[4], const R 
     for (int f = 0; f < 4; ++f) d[f] = dF[f] = (R)0;
   }
   R yE = 0, yEv = 0;
-  if (!k.frozen) {
+  if (SRC != 0) {
     const R ir = Ar<R>::rcp(u[0]);
     const R p = pressure<R, PP>(k, u[1] * (u[1] * ir), u[2], u[3]);
-    Src<R>::eval(k, u[0], p * ir, u[3], yE, yEv);
+    Src<R, SRC>::eval(k, u[0], p * ir, u[3], yE, yEv);
   }
   R uh[4];
   uh[0] = u[0] - dt_2h * dF[0];
@@ -77,10 +77,10 @@ __device__ __forceinline__ void predict(const P<R>& k, const R (&u)[4], const R 
     wm[f] = uh[f] - (R)0.5 * d[f];
   }
   yEh = yEvh = (R)0;
-  if (!k.frozen) {
+  if (SRC != 0) {
     const R irh = Ar<R>::rcp(uh[0]);
     const R ph = pressure<R, PP>(k, uh[1] * (uh[1] * irh), uh[2], uh[3]);
-    Src<R>::eval(k, uh[0], ph * irh, uh[3], yEh, yEvh);
+    Src<R, SRC>::eval(k, uh[0], ph * irh, uh[3], yEh, yEvh);
   }
 }
 
@@ -116,10 +116,10 @@ __device__ __forceinline__ R shfl(R v, int src) {
   return __shfl_sync(0xffffffffu, v, src);
 }
 
-template <typename R, int PP, int MINB>
+template <typename R, int PP, int LIM, int SRC, int MINB>
 __global__ void __launch_bounds__(NT1, MINB)
 step1d_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl* __restrict__ ctl,
-              int64_t N) {
+              int N) {
   const double dtd = vload(&ctl->dt);
   if (!(dtd > 0.0)) return;                       // stopped, or t_end reached
   const uint32_t cur = vload(&ctl->cur);
@@ -130,26 +130,30 @@ step1d_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
   const R dt = (R)dtd, dtdx = (R)(dtd / kp.h), dt_2h = (R)(dtd / (2.0 * kp.h)), dt_2 = (R)(0.5 * dtd);
 
   const int lane = threadIdx.x & 31;
-  const int64_t nwarps = (int64_t)gridDim.x * (NT1 / 32);
-  const int64_t warp = (int64_t)blockIdx.x * (NT1 / 32) + (threadIdx.x >> 5);
-  const int64_t nchunk = (N + 31) / 32;
-  const int64_t c0 = warp * nchunk / nwarps, c1 = (warp + 1) * nchunk / nwarps;
+  const int nwarps = gridDim.x * (NT1 / 32);
+  const int warp = blockIdx.x * (NT1 / 32) + (threadIdx.x >> 5);
+  const int nchunk = (N + 31) / 32;
+  const int c0 = (int)((int64_t)warp * nchunk / nwarps);
+  const int c1 = (int)((int64_t)(warp + 1) * nchunk / nwarps);
 
-  double smax = 0.0, akey = -INFINITY;
+  R smax = 0, akey = -INFINITY;
   uint32_t flags = 0;
 
   if (c1 > c0) {
+    // cells c0*32-64 .. (c1+2)*32-1 are read; no index wrap needed inside [0, N)
+    const bool nowrap = c0 >= 2 && (c1 + 2) * 32 <= N;
+    auto idx = [&](int j) { return nowrap ? j : (int)wrap(j, N); };
     const int src_m = (lane + 31) & 31, src_p = (lane + 1) & 31;
     R Uprev[4], Uc[4], Un[4], Un2[4];
     R Wp_prev[4] = {0, 0, 0, 0}, F_prev[4] = {0, 0, 0, 0}, yE_prev = 0, yEv_prev = 0;
-    const int64_t base = c0 * 32 + lane;
-    load_cell(Uin, N, base - 64, Uprev);
-    load_cell(Uin, N, base - 32, Uc);
-    load_cell(Uin, N, base, Un);
-    load_cell(Uin, N, base + 32, Un2);
+    const int base = c0 * 32 + lane;
+    load_cell(Uin, N, idx(base - 64), Uprev);
+    load_cell(Uin, N, idx(base - 32), Uc);
+    load_cell(Uin, N, idx(base), Un);
+    load_cell(Uin, N, idx(base + 32), Un2);
     // chunk index kk runs from c0-1 (warm-up) to c1 (trailing faces)
-    for (int64_t kk = c0 - 1; kk <= c1; ++kk) {
-      const int64_t j = kk * 32 + lane;
+    for (int kk = c0 - 1; kk <= c1; ++kk) {
+      const int j = kk * 32 + lane;
       R Um[4], Up[4];
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
@@ -157,7 +161,7 @@ step1d_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
         Up[f] = shfl(lane == 0 ? Un[f] : Uc[f], src_p);
       }
       R Wp[4], Wm[4], yEh, yEvh;
-      predict<R, PP>(k, Uc, Um, Up, dt_2h, dt_2, Wp, Wm, yEh, yEvh);
+      predict<R, PP, LIM, SRC>(k, Uc, Um, Up, dt_2h, dt_2, Wp, Wm, yEh, yEvh);
       R F[4] = {0, 0, 0, 0};
       if (kk >= c0) {
         R WL[4];
@@ -170,7 +174,7 @@ step1d_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
         R FR[4];
 #pragma unroll
         for (int f = 0; f < 4; ++f) FR[f] = shfl(lane == 0 ? F[f] : F_prev[f], src_p);
-        const int64_t jo = j - 32;
+        const int jo = j - 32;
         if (jo < N) {
           R un[4];
           un[0] = Uprev[0] - dtdx * (FR[0] - F_prev[0]);
@@ -180,7 +184,7 @@ step1d_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
 #pragma unroll
           for (int f = 0; f < 4; ++f) Uout[f * N + jo] = un[f];
           const R v = un[1] * Ar<R>::rcp(un[0]);
-          cfl_cell<R, PP>(k, un[0], un[1] * v, fabs(v), un[2], un[3], smax, akey, flags);
+          cfl_cell<R, PP, SRC>(k, un[0], un[1] * v, fabs(v), un[2], un[3], smax, akey, flags);
         }
       }
       // rotate the window
@@ -194,45 +198,62 @@ step1d_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
       }
       yE_prev = yEh;
       yEv_prev = yEvh;
-      if (kk + 3 <= c1 + 1) load_cell(Uin, N, j + 96, Un2);
+      if (kk + 3 <= c1 + 1) load_cell(Uin, N, idx(j + 96), Un2);
     }
   }
-  reduce_and_finalize<R, NT1>(ctl, kp, smax, akey, flags, true);
+  reduce_and_finalize<R, NT1>(ctl, kp, (double)smax, (double)akey, flags, true);
 }
 
-// Grid size: a persistent grid of (resident blocks per SM) x (SMs).
-template <typename R, int PP, int MINB>
-static int grid_for() {
+// Kernel variants: arithmetic (float / double / float with double pressure),
+// limiter and source kind are compile-time; one of them is chosen per solver.
+template <typename R, int PP, int LIM, int SRC>
+struct K1 {
+  static constexpr int MINB = sizeof(R) == 8 ? 1 : 2;
+  static constexpr auto fn = step1d_kernel<R, PP, LIM, SRC, MINB>;
+};
+
+template <int LIM, int SRC>
+static void* pick_prec(int precision) {
+  switch (precision) {
+    case PREC_FP64: return (void*)K1<double, 0, LIM, SRC>::fn;
+    case PREC_FP32_P64: return (void*)K1<float, 1, LIM, SRC>::fn;
+    default: return (void*)K1<float, 0, LIM, SRC>::fn;
+  }
+}
+
+template <int LIM>
+static void* pick_src(int precision, int src) {
+  switch (src) {
+    case 0: return pick_prec<LIM, 0>(precision);
+    case 1: return pick_prec<LIM, 1>(precision);
+    default: return pick_prec<LIM, 2>(precision);
+  }
+}
+
+static void* pick(const KParams& kp, int precision) {
+  const int src = kp.frozen ? 0 : (kp.qi_zero ? 1 : 2);
+  switch (kp.limiter) {
+    case 1: return pick_src<1>(precision, src);
+    case 2: return pick_src<2>(precision, src);
+    default: return pick_src<0>(precision, src);
+  }
+}
+
+int step1d_grid(const KParams& kp, int precision) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step1d_kernel<R, PP, MINB>, NT1, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pick(kp, precision), NT1, 0);
   if (per < 1) per = 1;
   return sms * per;
 }
 
-template <typename R, int PP, int MINB>
-static cudaError_t launch(const KParams& kp, void* a, void* b, Ctl* ctl, int64_t N, int grid,
-                          cudaStream_t st) {
-  step1d_kernel<R, PP, MINB><<<grid, NT1, 0, st>>>(kp, (R*)a, (R*)b, ctl, N);
-  return cudaGetLastError();
-}
-
-int step1d_grid(int precision) {
-  switch (precision) {
-    case PREC_FP64: return grid_for<double, 0, 1>();
-    case PREC_FP32_P64: return grid_for<float, 1, 2>();
-    default: return grid_for<float, 0, 2>();
-  }
-}
-
 cudaError_t step1d_launch(int precision, const KParams& kp, void* a, void* b, Ctl* ctl, int64_t N,
                           int grid, cudaStream_t st) {
-  switch (precision) {
-    case PREC_FP64: return launch<double, 0, 1>(kp, a, b, ctl, N, grid, st);
-    case PREC_FP32_P64: return launch<float, 1, 2>(kp, a, b, ctl, N, grid, st);
-    default: return launch<float, 0, 2>(kp, a, b, ctl, N, grid, st);
-  }
+  if (N >= (1LL << 31) / 4) return cudaErrorInvalidValue;
+  int n32 = (int)N;
+  void* args[] = {(void*)&kp, &a, &b, &ctl, &n32};
+  return cudaLaunchKernel(pick(kp, precision), dim3(grid), dim3(NT1), args, 0, st);
 }
 
 }  // namespace sv

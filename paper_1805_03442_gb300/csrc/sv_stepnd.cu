@@ -1,15 +1,391 @@
-// sv_stepnd.cu -- fused 2D/3D unsplit MUSCL-Hancock steps (placeholder until
-// the multi-dimensional kernels land).
+// sv_stepnd.cu -- fused 2D / 3D unsplit MUSCL-Hancock steps (Sec. 2.3:
+// eq. 15 with both flux differences F and G -- and the analogous z flux in
+// 3D -- in one update; eq. 14 face states per axis with xi = 0; eq. 13 HLL per
+// axis; source Y at the half step; eq. 16 reduction).
+//
+// Work decomposition ("marching planes").  Each block owns a transverse tile
+// (TX threads along x in 2D; TX x TY threads over x-y in 3D) and a segment of
+// planes along the outermost axis (y in 2D, z in 3D).  Thread (tx, ty) owns
+// the column of cells at one transverse position; the outer ring of threads is
+// a one-cell halo whose predictors feed the tile's faces but which update
+// nothing.  Per plane q the block
+//   a. publishes plane q's states in shared memory (the halo threads also load
+//      the second ring, needed by their slopes),
+//   b. computes slopes (all axes; the marching-axis slope from the planes
+//      q-1, q, q+1 held in registers), the positivity guard and the half-step
+//      predictor of plane q -- once per cell,
+//   c. publishes the +face states of the transverse axes and computes each
+//      cell's left transverse faces (HLL, once per face),
+//   d. publishes those fluxes and forms the transverse flux divergence,
+//   e. computes the marching-axis face between planes q-1 and q,
+//   f. updates plane q-1 (all its faces are now known) and folds its
+//      signal speed / tau bound for the next dt.
+// Three barriers per plane; loads are coalesced along x.
 #include "sv_internal.h"
-#include "sv_model.cuh"
+#include "sv_reduce.cuh"
 
 namespace sv {
 
-int stepnd_grid(int, int) { return 1; }
+template <typename R, int PP, int DIM, int SRC>
+struct Nd {
+  static constexpr int NF = DIM + 3;
+  using V = R[NF];
 
-cudaError_t stepnd_launch(int, int, const KParams&, void*, void*, Ctl*, const int64_t*, int,
-                          cudaStream_t) {
-  return cudaErrorNotSupported;
+  static __device__ __forceinline__ void prim(const P<R>& k, const V& u, R& ir, R (&v)[DIM], R& p) {
+    ir = Ar<R>::rcp(u[0]);
+    R kin2 = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      v[a] = u[1 + a] * ir;
+      kin2 += u[1 + a] * v[a];
+    }
+    p = pressure<R, PP>(k, kin2, u[1 + DIM], u[2 + DIM]);
+  }
+
+  template <int A>
+  static __device__ __forceinline__ void flux(const V& u, const R (&v)[DIM], R p, V& F) {
+    F[0] = u[1 + A];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) F[1 + b] = u[1 + b] * v[A] + (b == A ? p : (R)0);
+    F[1 + DIM] = v[A] * (u[1 + DIM] + p);
+    F[2 + DIM] = v[A] * u[2 + DIM];
+  }
+
+  // F(u + d/2) - F(u - d/2) along axis A; returns false if a state is non-physical
+  template <int A>
+  static __device__ __forceinline__ bool dflux(const P<R>& k, const V& u, const V& d, V& dF) {
+    V a, b;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      a[f] = u[f] + (R)0.5 * d[f];
+      b[f] = u[f] - (R)0.5 * d[f];
+    }
+    R ira, irb, pa, pb, va[DIM], vb[DIM];
+    prim(k, a, ira, va, pa);
+    prim(k, b, irb, vb, pb);
+    V Fa, Fb;
+    flux<A>(a, va, pa, Fa);
+    flux<A>(b, vb, pb, Fb);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) dF[f] = Fa[f] - Fb[f];
+    return (a[0] > (R)0) && (pa > (R)0) && (b[0] > (R)0) && (pb > (R)0);
+  }
+
+  static __device__ __forceinline__ void source(const P<R>& k, const V& u, R& yE, R& yEv) {
+    yE = yEv = (R)0;
+    if (SRC == 0) return;
+    R ir, p, v[DIM];
+    prim(k, u, ir, v, p);
+    Src<R, SRC>::eval(k, u[0], p * ir, u[2 + DIM], yE, yEv);
+  }
+
+  // eq. 13 along axis A
+  template <int A>
+  static __device__ __forceinline__ void hll(const P<R>& k, const V& l, const V& r, const V& fl,
+                                             const V& fr, V& F) {
+    V L, Rr;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) { L[f] = l[f]; Rr[f] = r[f]; }
+    R irL, pL, vL[DIM], irR, pR, vR[DIM];
+    prim(k, L, irL, vL, pL);
+    prim(k, Rr, irR, vR, pR);
+    if (!((L[0] > (R)0) && (pL > (R)0) && (Rr[0] > (R)0) && (pR > (R)0))) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) { L[f] = fl[f]; Rr[f] = fr[f]; }
+      prim(k, L, irL, vL, pL);
+      prim(k, Rr, irR, vR, pR);
+    }
+    const R cL = Ar<R>::sqrt_pos(k.gamma * pL * irL);
+    const R cR = Ar<R>::sqrt_pos(k.gamma * pR * irR);
+    const R sl = fmin(fmin(vL[A] - cL, vR[A] - cR), (R)0);
+    const R sr = fmax(fmax(vL[A] + cL, vR[A] + cR), (R)0);
+    V FL, FR;
+    flux<A>(L, vL, pL, FL);
+    flux<A>(Rr, vR, pR, FR);
+    const R inv = Ar<R>::rcp(sr - sl), slsr = sl * sr;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) F[f] = (sr * FL[f] - sl * FR[f] + slsr * (Rr[f] - L[f])) * inv;
+  }
+};
+
+template <typename R>
+__device__ __forceinline__ void ld(const R* __restrict__ U, int64_t ncell, int64_t idx, R* u, int nf) {
+  for (int f = 0; f < nf; ++f) u[f] = __ldg(U + f * ncell + idx);
+}
+
+// DIM 2: TY must be 1; marching axis y.  DIM 3: marching axis z.
+template <typename R, int PP, int LIM, int SRC, int DIM, int TX, int TY, int MINB>
+__global__ void __launch_bounds__(TX * TY, MINB)
+stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl* __restrict__ ctl,
+              int64_t nx, int64_t ny, int64_t nz, int tiles_x, int tiles_y, int nseg) {
+  using C = Nd<R, PP, DIM, SRC>;
+  constexpr int NF = DIM + 3;
+  constexpr int NT = TX * TY;
+  constexpr int SY = DIM == 3 ? TY + 2 : 1;     // rows of the shared state plane
+  constexpr int AM = DIM - 1;                   // marching axis
+  // dynamic shared memory: sU[NF][SY][TX+2], sW[DIM-1][NF][TY][TX], sF[DIM-1][NF][TY][TX]
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R (*sU)[SY][TX + 2] = reinterpret_cast<R (*)[SY][TX + 2]>(smem_raw);
+  R (*sW)[NF][TY][TX] = reinterpret_cast<R (*)[NF][TY][TX]>(smem_raw + sizeof(R) * NF * SY * (TX + 2));
+  R (*sF)[NF][TY][TX] = reinterpret_cast<R (*)[NF][TY][TX]>(
+      smem_raw + sizeof(R) * (NF * SY * (TX + 2) + (DIM - 1) * NF * TY * TX));
+
+  const double dtd = vload(&ctl->dt);
+  if (!(dtd > 0.0)) return;
+  const uint32_t cur = vload(&ctl->cur);
+  const R* __restrict__ Uin = cur ? bufB : bufA;
+  R* __restrict__ Uout = cur ? bufA : bufB;
+  const P<R> k(kp);
+  const R dt = (R)dtd, dtdx = (R)(dtd / kp.h), dt_2h = (R)(dtd / (2.0 * kp.h)), dt_2 = (R)(0.5 * dtd);
+
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int seg = blockIdx.x % nseg;
+  const int tile = blockIdx.x / nseg;
+  const int tile_x = tile % tiles_x, tile_y = tile / tiles_x;
+  const int64_t gx = (int64_t)tile_x * (TX - 2) - 1 + tx;
+  const int64_t gy = DIM == 3 ? (int64_t)tile_y * (TY - 2) - 1 + ty : 0;
+  const int64_t M = DIM == 3 ? nz : ny;                     // planes
+  const int64_t plane = DIM == 3 ? nx * ny : nx;            // cells per plane
+  const int64_t ncell = plane * M;
+  const int64_t q0 = seg * M / nseg, q1 = (seg + 1) * M / nseg;
+  const bool interior = tx >= 1 && tx <= TX - 2 && gx < nx &&
+                        (DIM == 2 || (ty >= 1 && ty <= TY - 2 && gy < ny));
+  const int64_t wx = wrap(gx, nx), wy = DIM == 3 ? wrap(gy, ny) : 0;
+  const int64_t col = DIM == 3 ? wy * nx + wx : wx;          // index within a plane
+  // second-ring positions loaded by the halo threads
+  const bool ringx = (tx == 0) || (tx == TX - 1);
+  const int64_t col_rx = (DIM == 3 ? wy * nx : 0) + wrap(gx + (tx == 0 ? -1 : 1), nx);
+  const bool ringy = DIM == 3 && ((ty == 0) || (ty == TY - 1));
+  const int64_t col_ry = DIM == 3 ? wrap(gy + (ty == 0 ? -1 : 1), ny) * nx + wx : 0;
+  const int oy = DIM == 3 ? ty + 1 : 0;
+
+  R smax = 0, akey = -INFINITY;
+  uint32_t flags = 0;
+
+  R Um1[NF], Uq[NF], Up1[NF], Up2[NF], Rx[NF], Ry[NF];
+  R Wm_prev[NF], D_prev[NF], H_prev[NF], yE_prev = 0, yEv_prev = 0;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) Wm_prev[f] = D_prev[f] = H_prev[f] = Rx[f] = Ry[f] = (R)0;
+  auto pidx = [&](int64_t q) { return wrap(q, M) * plane; };
+  ld(Uin, ncell, pidx(q0 - 2) + col, Um1, NF);
+  ld(Uin, ncell, pidx(q0 - 1) + col, Uq, NF);
+  ld(Uin, ncell, pidx(q0) + col, Up1, NF);
+  ld(Uin, ncell, pidx(q0 + 1) + col, Up2, NF);
+  if (ringx) ld(Uin, ncell, pidx(q0 - 1) + col_rx, Rx, NF);
+  if (ringy) ld(Uin, ncell, pidx(q0 - 1) + col_ry, Ry, NF);
+
+  for (int64_t q = q0 - 1; q <= q1; ++q) {
+    // a. publish plane q
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      sU[f][oy][tx + 1] = Uq[f];
+      if (ringx) sU[f][oy][tx == 0 ? 0 : TX + 1] = Rx[f];
+      if (DIM == 3 && ringy) sU[f][ty == 0 ? 0 : SY - 1][tx + 1] = Ry[f];
+    }
+    if (q + 1 <= q1) {
+      if (ringx) ld(Uin, ncell, pidx(q + 1) + col_rx, Rx, NF);
+      if (ringy) ld(Uin, ncell, pidx(q + 1) + col_ry, Ry, NF);
+    }
+    __syncthreads();
+
+    // b. slopes and predictor of plane q
+    R d[DIM][NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      d[0][f] = limit<LIM, R>(Uq[f] - sU[f][oy][tx], sU[f][oy][tx + 2] - Uq[f]);
+      if (DIM == 3) d[1][f] = limit<LIM, R>(Uq[f] - sU[f][oy - 1][tx + 1], sU[f][oy + 1][tx + 1] - Uq[f]);
+      d[AM][f] = limit<LIM, R>(Uq[f] - Um1[f], Up1[f] - Uq[f]);
+    }
+    R div[NF], dF[NF];
+    bool ok = C::template dflux<0>(k, Uq, d[0], div);
+    ok = C::template dflux<1>(k, Uq, d[1], dF) && ok;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) div[f] += dF[f];
+    if (DIM == 3) {
+      ok = C::template dflux<DIM == 3 ? 2 : 1>(k, Uq, d[AM], dF) && ok;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) div[f] += dF[f];
+    }
+    if (!ok) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        div[f] = (R)0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) d[a][f] = (R)0;
+      }
+    }
+    R yE, yEv;
+    C::source(k, Uq, yE, yEv);
+    R uh[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) uh[f] = Uq[f] - dt_2h * div[f];
+    uh[1 + DIM] += dt_2 * yE;
+    uh[2 + DIM] += dt_2 * yEv;
+    R yEh, yEvh;
+    C::source(k, uh, yEh, yEvh);
+
+    // c. transverse faces: publish +states, take the left neighbour's
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      sW[0][f][ty][tx] = uh[f] + (R)0.5 * d[0][f];
+      if (DIM == 3) sW[DIM == 3 ? 1 : 0][f][ty][tx] = uh[f] + (R)0.5 * d[1][f];
+    }
+    __syncthreads();
+    R Fx[NF], Fy[NF];
+    {
+      R l[NF], r[NF], fl[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        l[f] = sW[0][f][ty][tx > 0 ? tx - 1 : tx];
+        r[f] = uh[f] - (R)0.5 * d[0][f];
+        fl[f] = sU[f][oy][tx];
+      }
+      C::template hll<0>(k, l, r, fl, Uq, Fx);
+      if (DIM == 3) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          l[f] = sW[DIM == 3 ? 1 : 0][f][ty > 0 ? ty - 1 : ty][tx];
+          r[f] = uh[f] - (R)0.5 * d[1][f];
+          fl[f] = sU[f][oy > 0 ? oy - 1 : oy][tx + 1];
+        }
+        C::template hll<1>(k, l, r, fl, Uq, Fy);
+      }
+    }
+    // d. transverse flux divergence of plane q
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      sF[0][f][ty][tx] = Fx[f];
+      if (DIM == 3) sF[DIM == 3 ? 1 : 0][f][ty][tx] = Fy[f];
+    }
+    __syncthreads();
+    R Dq[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      Dq[f] = sF[0][f][ty][tx < TX - 1 ? tx + 1 : tx] - Fx[f];
+      if (DIM == 3) Dq[f] += sF[DIM == 3 ? 1 : 0][f][ty < TY - 1 ? ty + 1 : ty][tx] - Fy[f];
+    }
+
+    // e. marching-axis face between planes q-1 and q
+    R Wm[NF], Hq[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) Wm[f] = uh[f] - (R)0.5 * d[AM][f];
+    C::template hll<AM>(k, Wm_prev, Wm, Um1, Uq, Hq);
+
+    // f. update of plane q-1
+    if (q > q0 && interior) {
+      R un[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) un[f] = Um1[f] - dtdx * (D_prev[f] + Hq[f] - H_prev[f]);
+      un[1 + DIM] += dt * yE_prev;
+      un[2 + DIM] += dt * yEv_prev;
+      const int64_t o = pidx(q - 1) + col;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) Uout[f * ncell + o] = un[f];
+      R ir, p, v[DIM];
+      C::prim(k, un, ir, v, p);
+      R v2 = 0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) v2 += v[a] * v[a];
+      const R vmag = v2 > (R)0 ? Ar<R>::sqrt_pos(v2) : (R)0;
+      R kin2 = 0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) kin2 += un[1 + a] * v[a];
+      cfl_cell<R, PP, SRC>(k, un[0], kin2, vmag, un[1 + DIM], un[2 + DIM], smax, akey, flags);
+    }
+
+    // rotate the plane window
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      Um1[f] = Uq[f];
+      Uq[f] = Up1[f];
+      Up1[f] = Up2[f];
+      Wm_prev[f] = uh[f] + (R)0.5 * d[AM][f];
+      D_prev[f] = Dq[f];
+      H_prev[f] = Hq[f];
+    }
+    yE_prev = yEh;
+    yEv_prev = yEvh;
+    if (q + 3 <= q1 + 1) ld(Uin, ncell, pidx(q + 3) + col, Up2, NF);
+  }
+  reduce_and_finalize<R, NT>(ctl, kp, (double)smax, (double)akey, flags, true);
+}
+
+// ------------------------------------------------------------------ launch
+
+template <int DIM, int PREC> struct Cfg;
+template <> struct Cfg<2, PREC_FP32> { static constexpr int TX = 256, TY = 1, MINB = 2, SEG = 256; };
+template <> struct Cfg<2, PREC_FP32_P64> { static constexpr int TX = 256, TY = 1, MINB = 2, SEG = 256; };
+template <> struct Cfg<2, PREC_FP64> { static constexpr int TX = 128, TY = 1, MINB = 2, SEG = 256; };
+template <> struct Cfg<3, PREC_FP32> { static constexpr int TX = 32, TY = 16, MINB = 1, SEG = 128; };
+template <> struct Cfg<3, PREC_FP32_P64> { static constexpr int TX = 32, TY = 16, MINB = 1, SEG = 128; };
+template <> struct Cfg<3, PREC_FP64> { static constexpr int TX = 32, TY = 8, MINB = 1, SEG = 128; };
+
+// With `n` null only the kernel's shared-memory attribute is set (done once per
+// solver at init, outside any stream capture).
+template <typename R, int PP, int LIM, int SRC, int DIM, int PREC>
+static cudaError_t launch_nd(const KParams& kp, void* a, void* b, Ctl* ctl, const int64_t* n,
+                            cudaStream_t st) {
+  using G = Cfg<DIM, PREC>;
+  constexpr int NF = DIM + 3, SY = DIM == 3 ? G::TY + 2 : 1;
+  constexpr size_t smem = sizeof(R) * (NF * SY * (G::TX + 2) + 2 * (DIM - 1) * NF * G::TY * G::TX);
+  auto fn = stepnd_kernel<R, PP, LIM, SRC, DIM, G::TX, G::TY, G::MINB>;
+  if (!n) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int64_t nx = n[0], ny = n[1], nz = DIM == 3 ? n[2] : 1;
+  const int tiles_x = (int)((nx + G::TX - 3) / (G::TX - 2));
+  const int tiles_y = DIM == 3 ? (int)((ny + G::TY - 3) / (G::TY - 2)) : 1;
+  const int64_t M = DIM == 3 ? nz : ny;
+  int nseg = (int)((M + G::SEG - 1) / G::SEG);
+  if (nseg < 1) nseg = 1;
+  const int64_t blocks = (int64_t)tiles_x * tiles_y * nseg;
+  if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+  fn<<<(int)blocks, G::TX * G::TY, smem, st>>>(kp, (R*)a, (R*)b, ctl, nx, ny, nz, tiles_x, tiles_y,
+                                               nseg);
+  return cudaGetLastError();
+}
+
+template <int LIM, int SRC, int DIM>
+static cudaError_t by_prec(int precision, const KParams& kp, void* a, void* b, Ctl* ctl,
+                           const int64_t* n, cudaStream_t st) {
+  switch (precision) {
+    case PREC_FP64: return launch_nd<double, 0, LIM, SRC, DIM, PREC_FP64>(kp, a, b, ctl, n, st);
+    case PREC_FP32_P64: return launch_nd<float, 1, LIM, SRC, DIM, PREC_FP32_P64>(kp, a, b, ctl, n, st);
+    default: return launch_nd<float, 0, LIM, SRC, DIM, PREC_FP32>(kp, a, b, ctl, n, st);
+  }
+}
+
+template <int LIM, int DIM>
+static cudaError_t by_src(int precision, const KParams& kp, void* a, void* b, Ctl* ctl,
+                          const int64_t* n, cudaStream_t st) {
+  if (kp.frozen) return by_prec<LIM, 0, DIM>(precision, kp, a, b, ctl, n, st);
+  if (kp.qi_zero) return by_prec<LIM, 1, DIM>(precision, kp, a, b, ctl, n, st);
+  return by_prec<LIM, 2, DIM>(precision, kp, a, b, ctl, n, st);
+}
+
+template <int DIM>
+static cudaError_t by_lim(int precision, const KParams& kp, void* a, void* b, Ctl* ctl,
+                          const int64_t* n, cudaStream_t st) {
+  switch (kp.limiter) {
+    case 1: return by_src<1, DIM>(precision, kp, a, b, ctl, n, st);
+    case 2: return by_src<2, DIM>(precision, kp, a, b, ctl, n, st);
+    default: return by_src<0, DIM>(precision, kp, a, b, ctl, n, st);
+  }
+}
+
+int stepnd_grid(int dim, int precision, const KParams& kp) {
+  cudaError_t e = cudaErrorInvalidValue;
+  if (dim == 2) e = by_lim<2>(precision, kp, nullptr, nullptr, nullptr, nullptr, nullptr);
+  if (dim == 3) e = by_lim<3>(precision, kp, nullptr, nullptr, nullptr, nullptr, nullptr);
+  return e == cudaSuccess ? 1 : 0;
+}
+
+cudaError_t stepnd_launch(int dim, int precision, const KParams& kp, void* a, void* b, Ctl* ctl,
+                          const int64_t* n, int, cudaStream_t st) {
+  if (!n) return cudaErrorInvalidValue;
+  int64_t ncell = n[0] * n[1] * (dim == 3 ? n[2] : 1);
+  if (ncell * (dim + 3) >= (1LL << 31)) return cudaErrorInvalidValue;
+  if (dim == 2) return by_lim<2>(precision, kp, a, b, ctl, n, st);
+  if (dim == 3) return by_lim<3>(precision, kp, a, b, ctl, n, st);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace sv

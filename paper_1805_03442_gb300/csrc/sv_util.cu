@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(NTU) dt_reduce_kernel(const KParams kp, const 
                                                         Ctl* ctl, int dim, int64_t ncell) {
   const R* U = vload(&ctl->cur) ? b : a;
   const P<R> k(kp);
-  double smax = 0.0, akey = -INFINITY;
+  R smax = 0, akey = -INFINITY;
   uint32_t flags = 0;
   for (int64_t i = (int64_t)blockIdx.x * NTU + threadIdx.x; i < ncell;
        i += (int64_t)gridDim.x * NTU) {
@@ -69,10 +69,10 @@ __global__ void __launch_bounds__(NTU) dt_reduce_kernel(const KParams kp, const 
       v2 += v * v;
     }
     const R vmag = dim == 1 ? fabs(U[ncell + i] * ir) : (v2 > (R)0 ? Ar<R>::sqrt_pos(v2) : (R)0);
-    cfl_cell<R, PP>(k, rho, kin2, vmag, U[(1 + dim) * ncell + i], U[(2 + dim) * ncell + i], smax,
-                    akey, flags);
+    cfl_cell<R, PP, 1>(k, rho, kin2, vmag, U[(1 + dim) * ncell + i], U[(2 + dim) * ncell + i],
+                       smax, akey, flags);
   }
-  reduce_and_finalize<R, NTU>(ctl, kp, smax, akey, flags, false);
+  reduce_and_finalize<R, NTU>(ctl, kp, (double)smax, (double)akey, flags, false);
 }
 
 static int grid_small(int64_t count) {

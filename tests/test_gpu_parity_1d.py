@@ -1,14 +1,15 @@
 """Parity of the fused 1D CUDA step (through the C ABI) with the FP64 oracle.
 
+Errors are max|gpu - oracle| / max(|field|, 1) per field (gpu_util.rel_linf).
 Tolerances:
-* FP64 kernels: relative L-infinity <= 1e-12 per field (the kernel and the
-  oracle differ only in rounding order: FMA contraction, reciprocal-multiply
-  instead of division, pow implementations -- a few ulp per operation, far
-  below 1e-12 unless an instability amplifies it).
+* FP64 kernels: <= 1e-12 (the kernel and the oracle differ only in rounding
+  order: FMA contraction, reciprocal-multiply instead of division, pow
+  implementations -- a few ulp per operation, far below 1e-12 unless an
+  instability amplifies it).
 * FP32 kernels: the state is stored in float (unit roundoff 6e-8) and the
   approximate SFU reciprocal / sqrt / log2 / exp2 carry up to ~2 ulp each; a
-  step changes each cell by dt/h * flux differences of O(1), so one step's
-  error is O(10 ulp) of the field scale: <= 2e-6 per field after one step.
+  step changes each cell by dt/h times flux differences of O(1), so one step's
+  error is O(10 ulp) of the O(1) scale: <= 2e-6 after one step.
 """
 import math
 
@@ -177,13 +178,16 @@ def test_max_steps_and_nonphysical_status(sv):
         assert rc == 0 and s.status() == 0
 
 
-def test_fp64_unstable_eigenmode_parity(sv):
-    """Config of the linear-stage run: N = 1024 on one wavelength, tau0 0.08,
-    S = 1, growing eigenmode of amplitude 1e-4.  Pointwise FP64 parity holds
-    while rounding noise stays below the tolerance after amplification
-    (t <= 2 here: growth of noise at most ~e^(2.2 t))."""
+@pytest.mark.parametrize("limiter,t_end", [(1, 2.0), (2, 2.0), (0, 0.03)])
+def test_fp64_unstable_eigenmode_parity(sv, limiter, t_end):
+    """Linear-stage run: N = 1024 on one wavelength, tau0 0.08, S = 1, growing
+    eigenmode of amplitude 1e-4.  With van Leer or MC the scheme amplifies
+    rounding noise only at the physical rate, so FP64 parity holds to t = 2.
+    With minmod the scheme itself amplifies 1e-16 perturbations at the grid
+    scale (to ~1e-8 by t ~ 0.3, in the oracle as well), so minmod parity is
+    checked over the first ~90 steps only."""
     N = 1024
-    P = sv.Params(precision=sv.FP64, tau0=0.08)
+    P = sv.Params(precision=sv.FP64, tau0=0.08, limiter=limiter)
     Po = oracle_params(P)
     k = 2 * math.pi
     w = D.growing_acoustic_root(Po, k)
@@ -192,9 +196,9 @@ def test_fp64_unstable_eigenmode_parity(sv):
                          [inputs.Mode(m=1, shape=md["prim"], scale=1e-4)])
     with sv.Solver(P, (N,)) as s:
         s.write_state(U0)
-        rc, k_steps = s.run_to(2.0)
+        rc, k_steps = s.run_to(t_end)
         U, t = s.read_state()
-    ref, tr, kr, _ = O.run(Po, U0, N, 1.0 / N, 2.0)
+    ref, tr, kr, _ = O.run(Po, U0, N, 1.0 / N, t_end)
     assert k_steps == kr and t == tr
     assert rel_linf(U, ref) <= 1e-12
 
@@ -276,8 +280,9 @@ def test_full_size_sampled_parity(sv, prec, tol):
         U, _ = s.read_state()
     idx = np.unique(np.concatenate([[0, 1, 2, 31, 32, 33, N - 1, N - 2, N - 33],
                                     rng.integers(0, N, 200)]))
-    scale = np.max(np.abs(U0), axis=1)
+    scale = np.maximum(np.max(np.abs(U0), axis=1), 1.0)
+    errs = []
     for i in idx:
         ref = O.step_cell(Po, U0, N, h, dt, int(i))
-        err = np.max(np.abs(U[:, i] - ref) / scale)
-        assert err <= tol, (i, err)
+        errs.append(np.max(np.abs(U[:, i] - ref) / scale))
+    assert max(errs) <= tol, (idx[int(np.argmax(errs))], max(errs))
