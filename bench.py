@@ -309,6 +309,94 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def sweep_inputs(nruns: int, seed: int = 2026):
+    """Stability sweep: N ~ U[256, 16384], tau0 log-uniform [1e-3, 1e1], S in
+    [0, 2], eq. 6 exponents spanning stable and unstable regions, mode m in 1..8
+    on L = 1, frozen acoustic wave of amplitude 1e-3, t_end = 5 periods."""
+    from paper_1805_03442_gb300 import inputs
+    runs = inputs.sweep_runs(seed, nruns)
+    shape = inputs.acoustic_shape(1.4)
+    states = [inputs.waves_1d(1.4, r.N, 1.0,
+                              inputs.equilibrium_primitive(0.1, r.S),
+                              [inputs.Mode(m=r.m, shape=shape, scale=1e-3)]) for r in runs]
+    return runs, states
+
+
+class _R:
+    def __init__(self, r):
+        self.__dict__.update(r.__dict__)
+        self.n = r.N
+
+
+def run_sweep(args):
+    """Batched sweep: one persistent launch for all runs (runs/s), next to the
+    same runs looped through single 1D solvers on a stratified subset."""
+    import torch
+    from paper_1805_03442_gb300 import sv
+    from paper_1805_03442_gb300.build import build
+    build()
+    runs, states = sweep_inputs(args.runs)
+    runs = [_R(r) for r in runs]
+    P = sv.Params(precision=sv.FP32)
+    stream = torch.cuda.Stream()
+    # per-run step cap: about twice the expected CFL step count plus the tau bound
+    max_steps = 30 * max(r.n for r in runs) + 20000
+    b = sv.Batch(P, runs, states, log_cap=64, stream=stream, max_steps=max_steps)
+    times = []
+    with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for rep in range(max(1, min(args.steps, 2))):
+            if rep:
+                b.reset(states)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            b.run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e-3)
+    t_batch = min(times)
+    cells = 0
+    flags = {}
+    for i, r in enumerate(runs):
+        _, t, k, f = b.read(i, state=False)
+        cells += k * r.n
+        flags[f] = flags.get(f, 0) + 1
+    b.close()
+    # looped single runs vs the batch on the same stratified subset
+    order = sorted(range(len(runs)), key=lambda i: -(runs[i].n ** 2) * runs[i].t_end)
+    sub = order[:: max(1, len(runs) // args.subset)][: args.subset]
+    t0 = time.perf_counter()
+    for i in sub:
+        r = runs[i]
+        Pi = sv.Params(precision=sv.FP32, S=r.S, tau0=r.tau0, tau_rho=r.tau_rho, tau_T=r.tau_T,
+                       Q_rho=r.Q_rho, Q_T=r.Q_T, I_rho=r.I_rho, I_T=r.I_T)
+        with sv.Solver(Pi, (r.n,), (1.0,), stream=stream) as s:
+            s.write_state(states[i])
+            s.run_to(r.t_end, max_steps=max_steps, check=False)
+    t_loop = time.perf_counter() - t0
+    sb = sv.Batch(P, [runs[i] for i in sub], [states[i] for i in sub], log_cap=64, stream=stream,
+                  max_steps=max_steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sb.run()
+    sb.sync()
+    t_sub = time.perf_counter() - t0
+    sb.close()
+    line = {"metric": "batched sweep runs/s", "value": len(runs) / t_batch, "unit": "runs/s",
+            "n_gpus": 1, "steps": len(times), "warmup": 0, "ms_per_step": 1e3 * t_batch,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"batched 1D stability sweep, {len(runs)} runs, N~U[256,16384], "
+                                   "tau0 log-uniform [1e-3,1e1], S in [0,2], exponents in "
+                                   "[-2.5,1], m in 1..8, 5 periods", "runs": len(runs)},
+            "cell_updates_per_s": cells / t_batch, "cell_updates": cells,
+            "run_flags": {str(k): v for k, v in sorted(flags.items())},
+            "subset": {"runs": len(sub), "looped_single_runs_s": t_loop, "batched_s": t_sub,
+                       "speedup": t_loop / t_sub},
+            "gpu_launches": 2, "clocks": getattr(clk, "result", None)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -317,12 +405,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_p64"])
     ap.add_argument("--n", type=int, default=1 << 22, help="cells of the 1d workload")
-    ap.add_argument("--workload", default="1d", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="1d", choices=sorted(WORKLOADS) + ["sweep"])
+    ap.add_argument("--runs", type=int, default=4096, help="runs of the sweep workload")
+    ap.add_argument("--subset", type=int, default=64, help="looped comparison subset of the sweep")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_ours(args)
 

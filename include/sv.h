@@ -52,8 +52,9 @@ extern "C" {
 #define SV_EMAXSTEPS  -7   /* sv_run_to stopped at max_steps before t_end */
 
 /* ---- status flag bits (sv_status) */
-#define SV_FLAG_NONPHYS 1u
-#define SV_FLAG_DT      2u
+#define SV_FLAG_NONPHYS  1u
+#define SV_FLAG_DT       2u
+#define SV_FLAG_MAXSTEPS 4u   /* batched runs: step budget exhausted before t_end */
 
 /* ---- limiters (the paper asks for "TVD limiters" without naming one) */
 #define SV_MINMOD   0
@@ -142,6 +143,66 @@ int sv_state_device(sv_solver* s, void** dev_ptr, int* elem_bytes);
 
 /* Release the solver (waits for its stream). */
 void sv_free(sv_solver* s);
+
+/* ------------------------------------------------------------------------
+ * Batched sweep: many independent 1D periodic runs of uneven sizes and
+ * parameters (a stability map over S, tau0, the eq. 6 exponents and the
+ * wavenumber), advanced to their own t_end by one persistent launch that is
+ * replayed from a CUDA graph.  Every run uses the same per-cell arithmetic as
+ * a single 1D solver with the same parameters, so a batched run and a looped
+ * sv_run_to of that run give identical results.
+ * ------------------------------------------------------------------------ */
+
+typedef struct {
+  int64_t n;            /* cells (1 .. 2^24) */
+  double L;             /* domain length, h = L / n */
+  double t_end;         /* end time of the run */
+  double S, tau0;       /* degree of non-equilibrium, relaxation time (+inf: frozen) */
+  double tau_rho, tau_T, Q_rho, Q_T, I_rho, I_T;   /* eq. 6 exponents */
+  int mode;             /* index m of the logged Fourier amplitude of the velocity,
+                           a_m(t) = (1/n) sum_j v_j exp(-i 2 pi m (j + 1/2) / n);
+                           0: no log */
+} sv_run;
+
+typedef struct sv_batch sv_batch;
+
+/* Device bytes for the batch: two state buffers (each run's 4 fields padded
+   to a multiple of 32 cells), run records, order, queue and mode logs. */
+int sv_batch_required_bytes(const sv_params* common, const sv_run* runs, int64_t nruns,
+                            int log_cap, size_t* bytes);
+
+/* Create a batch.  `common` supplies gamma, C_k, cfl, c_tau, limiter and
+   precision (its S, tau0 and exponents are ignored: each run has its own).
+   `host_states`: the runs' initial states, concatenated in run order, each
+   a (4, n) field-major double block (rho, rho v, E, E_nu).  `log_cap`:
+   samples of a_m kept per run (at t = 0, every t_end / (log_cap - 1) and at
+   the end).  `max_steps_per_run` caps each run (SV_FLAG_MAXSTEPS).
+   Stream and device memory as for sv_init. */
+int sv_batch_init(const sv_params* common, const sv_run* runs, int64_t nruns,
+                  const double* host_states, int log_cap, int64_t max_steps_per_run,
+                  void* cuda_stream, void* device_mem, size_t device_bytes, sv_batch** out);
+
+/* Re-upload initial states (same layout as sv_batch_init), times back to 0. */
+int sv_batch_reset(sv_batch* b, const double* host_states);
+
+/* Advance every run to its t_end: one persistent kernel launch, replayed from
+   a CUDA graph.  Asynchronous on the batch's stream. */
+int sv_batch_run(sv_batch* b);
+
+/* Wait for the batch's stream. */
+int sv_batch_sync(sv_batch* b);
+
+/* State (4 * n doubles, may be NULL), time, steps and flags of one run.
+   Synchronous. */
+int sv_batch_read(sv_batch* b, int64_t run, double* host_soa, double* t, int64_t* steps,
+                  uint32_t* flags);
+
+/* Up to `cap` logged samples (t, Re a_m, Im a_m) of one run; *count gets the
+   number written.  Synchronous. */
+int sv_batch_mode_log(sv_batch* b, int64_t run, double* t, double* re, double* im, int64_t cap,
+                      int64_t* count);
+
+void sv_batch_free(sv_batch* b);
 
 /* Human-readable name of a status code. */
 const char* sv_strerror(int code);

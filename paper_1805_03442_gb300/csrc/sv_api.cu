@@ -195,6 +195,7 @@ int sv_init(const sv_params* p, const sv_grid* g, void* cuda_stream, void* devic
   k.cfl = p->cfl;
   k.c_tau = p->c_tau;
   k.limiter = p->limiter;
+  kparams_finish(k);
 
   if (device_mem) {
     s->mem = device_mem;
@@ -281,7 +282,7 @@ int sv_step(sv_solver* s, int64_t nsteps) {
 
 int sv_run_to(sv_solver* s, double t_end, int64_t max_steps, int64_t* steps_taken) {
   if (!s || max_steps < 0 || isnan(t_end)) return SV_EINVAL;
-  SV_TRY(set_target_launch(s->ctl, t_end, s->stream));
+  SV_TRY(set_target_launch(s->ctl, t_end, s->h, s->stream));
   int rc = read_ctl(s);
   if (rc != SV_OK) return rc;
   const int64_t n0 = s->host_ctl->nsteps;
@@ -310,7 +311,7 @@ int sv_run_to(sv_solver* s, double t_end, int64_t max_steps, int64_t* steps_take
   (void)issued;
   if (steps_taken) *steps_taken = s->host_ctl->nsteps - n0;
   // clear the target so that later sv_step calls are not clamped
-  SV_TRY(set_target_launch(s->ctl, INFINITY, s->stream));
+  SV_TRY(set_target_launch(s->ctl, INFINITY, s->h, s->stream));
   return status;
 }
 

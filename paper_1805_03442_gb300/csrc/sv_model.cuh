@@ -31,12 +31,23 @@ struct KParams {
   int limiter;   // 0 minmod, 1 van Leer, 2 MC
   int frozen;    // 1: no source at all (Q = I = 0, 1/tau = 0)
   int qi_zero;   // 1: all Q and I exponents are zero (Q = I = Q0)
+  int pad;
+  float f[12];   // the first twelve values above rounded to float (kparams_finish)
 };
+
+// Fill the float copies once on the host, so float kernels convert nothing.
+inline void kparams_finish(KParams& k) {
+  const double v[12] = {k.gamma, k.g1, k.Ck, k.Q0, k.tau0, k.inv_tau0,
+                        k.tau_rho, k.tau_T, k.Q_rho, k.Q_T, k.I_rho, k.I_T};
+  for (int i = 0; i < 12; ++i) k.f[i] = (float)v[i];
+}
 
 // Device control block: time, step size and the reductions of one solver.
 struct Ctl {
   double t;            // current time
   double dt;           // dt of the next step (0: stopped / reached t_end)
+  double dtdx, dt_2h, dt_2;   // dt / h, dt / (2h), dt / 2 of the next step
+  float fdt, fdtdx, fdt_2h, fdt_2;   // the same rounded to float
   double dt_cfl;       // unclamped eq.-16 dt of the current state
   double t_end;        // target time of the running sv_run_to (+inf otherwise)
   int64_t nsteps;      // steps taken since the last state upload
@@ -73,15 +84,43 @@ template <> struct Ar<double> {
 };
 
 // Parameters converted once to the kernel's arithmetic type.
-template <typename R> struct P {
-  R gamma, g1, Ck, Q0, inv_tau0, tau0;
-  R tau_rho, tau_T, Q_rho, Q_T, I_rho, I_T;
+template <typename R> struct P;
+
+template <> struct P<double> {
+  double gamma, g1, Ck, Q0, inv_tau0, tau0;
+  double tau_rho, tau_T, Q_rho, Q_T, I_rho, I_T;
   int limiter, frozen, qi_zero;
   __device__ __forceinline__ explicit P(const KParams& k)
-      : gamma((R)k.gamma), g1((R)k.g1), Ck((R)k.Ck), Q0((R)k.Q0), inv_tau0((R)k.inv_tau0),
-        tau0((R)k.tau0), tau_rho((R)k.tau_rho), tau_T((R)k.tau_T), Q_rho((R)k.Q_rho),
-        Q_T((R)k.Q_T), I_rho((R)k.I_rho), I_T((R)k.I_T), limiter(k.limiter),
-        frozen(k.frozen), qi_zero(k.qi_zero) {}
+      : gamma(k.gamma), g1(k.g1), Ck(k.Ck), Q0(k.Q0), inv_tau0(k.inv_tau0), tau0(k.tau0),
+        tau_rho(k.tau_rho), tau_T(k.tau_T), Q_rho(k.Q_rho), Q_T(k.Q_T), I_rho(k.I_rho),
+        I_T(k.I_T), limiter(k.limiter), frozen(k.frozen), qi_zero(k.qi_zero) {}
+};
+
+template <> struct P<float> {
+  float gamma, g1, Ck, Q0, inv_tau0, tau0;
+  float tau_rho, tau_T, Q_rho, Q_T, I_rho, I_T;
+  int limiter, frozen, qi_zero;
+  __device__ __forceinline__ explicit P(const KParams& k)
+      : gamma(k.f[0]), g1(k.f[1]), Ck(k.f[2]), Q0(k.f[3]), inv_tau0(k.f[5]), tau0(k.f[4]),
+        tau_rho(k.f[6]), tau_T(k.f[7]), Q_rho(k.f[8]), Q_T(k.f[9]), I_rho(k.f[10]),
+        I_T(k.f[11]), limiter(k.limiter), frozen(k.frozen), qi_zero(k.qi_zero) {}
+};
+
+// The dt-derived factors of the next step, read by the step kernels.
+template <typename R> struct StepDt;
+template <> struct StepDt<double> {
+  double dt, dtdx, dt_2h, dt_2;
+  __device__ __forceinline__ StepDt(const volatile Ctl* c)
+      : dt(c->dt), dtdx(c->dtdx), dt_2h(c->dt_2h), dt_2(c->dt_2) {}
+  __device__ __forceinline__ StepDt(double d, double h)
+      : dt(d), dtdx(d / h), dt_2h(d / (2.0 * h)), dt_2(0.5 * d) {}
+};
+template <> struct StepDt<float> {
+  float dt, dtdx, dt_2h, dt_2;
+  __device__ __forceinline__ StepDt(const volatile Ctl* c)
+      : dt(c->fdt), dtdx(c->fdtdx), dt_2h(c->fdt_2h), dt_2(c->fdt_2) {}
+  __device__ __forceinline__ StepDt(double d, double h)
+      : dt((float)d), dtdx((float)(d / h)), dt_2h((float)(d / (2.0 * h))), dt_2((float)(0.5 * d)) {}
 };
 
 // ---------------------------------------------------------------- eq. 5

@@ -51,6 +51,33 @@ __device__ __forceinline__ void cfl_cell(const P<R>& k, R rho, R kin2, R vmag, R
   if (SRC != 0) akey = fmax(akey, TauKey<R>::of(k, rho, p * ir));
 }
 
+// eq. 16 times cfl from the maximal signal speed, capped by c_tau * min tau;
+// raises FLAG_DT if the result is not a positive finite number.
+template <typename R>
+__device__ __forceinline__ double dt_from_maxima(const KParams& kp, double smax, double akey,
+                                                 uint32_t& flags) {
+  double dt = kp.cfl * kp.h / smax;
+  if (!kp.frozen) {
+    const double taumin = TauKey<R>::tau_min(kp, akey);
+    if (kp.c_tau * taumin < dt) dt = kp.c_tau * taumin;
+  }
+  if (!(dt > 0.0) || !isfinite(dt)) flags |= FLAG_DT;
+  return dt;
+}
+
+// Store the next step's dt and its derived factors (double and float).
+__device__ __forceinline__ void set_step_dt(Ctl* ctl, double dt, double h) {
+  const double dtdx = dt / h, dt_2h = dt / (2.0 * h), dt_2 = 0.5 * dt;
+  ctl->dt = dt;
+  ctl->dtdx = dtdx;
+  ctl->dt_2h = dt_2h;
+  ctl->dt_2 = dt_2;
+  ctl->fdt = (float)dt;
+  ctl->fdtdx = (float)dtdx;
+  ctl->fdt_2h = (float)dt_2h;
+  ctl->fdt_2 = (float)dt_2;
+}
+
 // Read a control field written by other blocks in this launch or by the
 // previous launch, bypassing L1.
 template <typename T>
@@ -68,12 +95,7 @@ __device__ void finalize(Ctl* ctl, const KParams& kp, bool advance) {
   const double akey = key_to_double(atomicExch((unsigned long long*)&ctl->tau_key,
                                                (unsigned long long)key_of(-INFINITY)));
   uint32_t flags = atomicOr(&ctl->flags, 0u);
-  double dt = kp.cfl * kp.h / smax;
-  if (!kp.frozen) {
-    double taumin = TauKey<R>::tau_min(kp, akey);
-    if (kp.c_tau * taumin < dt) dt = kp.c_tau * taumin;
-  }
-  if (!(dt > 0.0) || !isfinite(dt)) flags |= FLAG_DT;
+  const double dt = dt_from_maxima<R>(kp, smax, akey, flags);
   double t = vload(&ctl->t);
   const double t_end = vload(&ctl->t_end);
   if (advance) {
@@ -93,7 +115,7 @@ __device__ void finalize(Ctl* ctl, const KParams& kp, bool advance) {
   }
   ctl->t = t;
   ctl->dt_cfl = dt;
-  ctl->dt = dtn;
+  set_step_dt(ctl, dtn, kp.h);
   ctl->last = last;
   ctl->flags = flags;
   __threadfence();

@@ -136,7 +136,8 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
   const R* __restrict__ Uin = cur ? bufB : bufA;
   R* __restrict__ Uout = cur ? bufA : bufB;
   const P<R> k(kp);
-  const R dt = (R)dtd, dtdx = (R)(dtd / kp.h), dt_2h = (R)(dtd / (2.0 * kp.h)), dt_2 = (R)(0.5 * dtd);
+  const StepDt<R> sd((const volatile Ctl*)ctl);
+  const R dt = sd.dt, dtdx = sd.dtdx, dt_2h = sd.dt_2h, dt_2 = sd.dt_2;
 
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int seg = blockIdx.x % nseg;

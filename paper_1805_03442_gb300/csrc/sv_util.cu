@@ -10,7 +10,7 @@ constexpr int NTU = 256;
 
 __global__ void ctl_reset_kernel(Ctl* ctl, double t) {
   ctl->t = t;
-  ctl->dt = 0.0;
+  set_step_dt(ctl, 0.0, 1.0);
   ctl->dt_cfl = 0.0;
   ctl->t_end = INFINITY;
   ctl->nsteps = 0;
@@ -29,7 +29,7 @@ cudaError_t ctl_reset_launch(Ctl* ctl, double t, cudaStream_t st) {
 
 // Sets the target time and re-clamps the pending dt (same rule as the
 // step finalize: the step that would reach or pass t_end lands on it).
-__global__ void set_target_kernel(Ctl* ctl, double t_end) {
+__global__ void set_target_kernel(Ctl* ctl, double t_end, double h) {
   const double t = ctl->t, dt = ctl->dt_cfl;
   ctl->t_end = t_end;
   uint32_t last = 0;
@@ -40,12 +40,12 @@ __global__ void set_target_kernel(Ctl* ctl, double t_end) {
     dtn = t_end - t;
     last = 1;
   }
-  ctl->dt = dtn;
+  set_step_dt(ctl, dtn, h);
   ctl->last = last;
 }
 
-cudaError_t set_target_launch(Ctl* ctl, double t_end, cudaStream_t st) {
-  set_target_kernel<<<1, 1, 0, st>>>(ctl, t_end);
+cudaError_t set_target_launch(Ctl* ctl, double t_end, double h, cudaStream_t st) {
+  set_target_kernel<<<1, 1, 0, st>>>(ctl, t_end, h);
   return cudaGetLastError();
 }
 

@@ -18,13 +18,15 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libsv.so")
 
 SV_OK, SV_EINVAL, SV_ENOMEM, SV_ECUDA, SV_ENONPHYS, SV_EDT, SV_EMAXSTEPS = 0, -1, -2, -3, -4, -5, -7
-FLAG_NONPHYS, FLAG_DT = 1, 2
+FLAG_NONPHYS, FLAG_DT, FLAG_MAXSTEPS = 1, 2, 4
 MINMOD, VANLEER, MC = 0, 1, 2
 FP32, FP64, FP32_P64 = 0, 1, 2
 
 EXPORTS = ("sv_required_bytes", "sv_init", "sv_write_state", "sv_read_state", "sv_dt_cfl",
            "sv_step", "sv_run_to", "sv_time", "sv_conservation", "sv_status",
-           "sv_state_device", "sv_free", "sv_strerror")
+           "sv_state_device", "sv_free", "sv_strerror", "sv_batch_required_bytes",
+           "sv_batch_init", "sv_batch_reset", "sv_batch_run", "sv_batch_sync", "sv_batch_read",
+           "sv_batch_mode_log", "sv_batch_free")
 
 
 class SvError(RuntimeError):
@@ -37,6 +39,13 @@ class _Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
                 ("gamma", "Ck", "S", "tau0", "tau_rho", "tau_T", "Q_rho", "Q_T", "I_rho", "I_T",
                  "cfl", "c_tau")] + [("limiter", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class _Run(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("L", ctypes.c_double), ("t_end", ctypes.c_double),
+                ("S", ctypes.c_double), ("tau0", ctypes.c_double), ("tau_rho", ctypes.c_double),
+                ("tau_T", ctypes.c_double), ("Q_rho", ctypes.c_double), ("Q_T", ctypes.c_double),
+                ("I_rho", ctypes.c_double), ("I_T", ctypes.c_double), ("mode", ctypes.c_int)]
 
 
 class _Grid(ctypes.Structure):
@@ -95,6 +104,20 @@ def lib() -> ctypes.CDLL:
     L.sv_free.restype = None
     L.sv_strerror.argtypes = [ctypes.c_int]
     L.sv_strerror.restype = ctypes.c_char_p
+    rp = ctypes.POINTER(_Run)
+    L.sv_batch_required_bytes.argtypes = [ctypes.POINTER(_Params), rp, ctypes.c_int64, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_size_t)]
+    L.sv_batch_init.argtypes = [ctypes.POINTER(_Params), rp, ctypes.c_int64, dp, ctypes.c_int,
+                                ctypes.c_int64, vp, vp, ctypes.c_size_t, ctypes.POINTER(vp)]
+    L.sv_batch_reset.argtypes = [vp, dp]
+    L.sv_batch_run.argtypes = [vp]
+    L.sv_batch_sync.argtypes = [vp]
+    L.sv_batch_read.argtypes = [vp, ctypes.c_int64, dp, dp, ctypes.POINTER(ctypes.c_int64),
+                                ctypes.POINTER(ctypes.c_uint32)]
+    L.sv_batch_mode_log.argtypes = [vp, ctypes.c_int64, dp, dp, dp, ctypes.c_int64,
+                                    ctypes.POINTER(ctypes.c_int64)]
+    L.sv_batch_free.argtypes = [vp]
+    L.sv_batch_free.restype = None
     _lib = L
     return L
 
@@ -241,3 +264,97 @@ class Solver:
         p, e = ctypes.c_void_p(), ctypes.c_int()
         _check(lib().sv_state_device(self._h, ctypes.byref(p), ctypes.byref(e)), "sv_state_device")
         return p.value, e.value
+
+
+class Batch:
+    """A batched sweep of independent 1D periodic runs, advanced by one
+    persistent launch (sv_batch_*).
+
+    runs: sequence of objects with attributes n, L (optional, default 1),
+    t_end, S, tau0, tau_rho, tau_T, Q_rho, Q_T, I_rho, I_T, m (logged mode);
+    states: list of (4, n) float64 initial states in the same order.
+    `params` supplies gamma, C_k, cfl, c_tau, limiter and precision."""
+
+    def __init__(self, params: Params, runs, states, log_cap: int = 64,
+                 max_steps: int = 10 ** 6, stream=None, memory: str = "torch"):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the batch has no CPU path")
+        self.params = params
+        self.nruns = len(runs)
+        arr = (_Run * self.nruns)()
+        for i, r in enumerate(runs):
+            arr[i] = _Run(int(r.n), float(getattr(r, "L", 1.0)), float(r.t_end), float(r.S),
+                          float(r.tau0), float(r.tau_rho), float(r.tau_T), float(r.Q_rho),
+                          float(r.Q_T), float(r.I_rho), float(r.I_T), int(getattr(r, "m", 0)))
+        self._runs = arr
+        self.n = [int(r.n) for r in runs]
+        self.log_cap = int(log_cap)
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        host = self._concat(states)
+        pc = params.c()
+        nbytes = ctypes.c_size_t()
+        _check(lib().sv_batch_required_bytes(ctypes.byref(pc), arr, self.nruns, self.log_cap,
+                                             ctypes.byref(nbytes)), "sv_batch_required_bytes")
+        self.device_bytes = nbytes.value
+        self._mem = None
+        dev_ptr = None
+        if memory == "torch":
+            self._mem = torch.empty(self.device_bytes, dtype=torch.uint8, device="cuda")
+            dev_ptr = self._mem.data_ptr()
+        h = ctypes.c_void_p()
+        _check(lib().sv_batch_init(ctypes.byref(pc), arr, self.nruns, _dp(host), self.log_cap,
+                                   int(max_steps), ctypes.c_void_p(self._stream.cuda_stream),
+                                   dev_ptr, self.device_bytes, ctypes.byref(h)), "sv_batch_init")
+        self._h = h
+
+    def _concat(self, states) -> np.ndarray:
+        parts = []
+        for U, n in zip(states, self.n):
+            U = np.asarray(U, dtype=np.float64).reshape(4, n)
+            parts.append(U.reshape(-1))
+        return np.ascontiguousarray(np.concatenate(parts))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sv_batch_free(self._h)
+            self._h = None
+        self._mem = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def reset(self, states):
+        host = self._concat(states)
+        _check(lib().sv_batch_reset(self._h, _dp(host)), "sv_batch_reset")
+
+    def run(self):
+        _check(lib().sv_batch_run(self._h), "sv_batch_run")
+
+    def sync(self):
+        _check(lib().sv_batch_sync(self._h), "sv_batch_sync")
+
+    def read(self, i: int, state: bool = True):
+        U = np.empty((4, self.n[i])) if state else None
+        t, k, f = ctypes.c_double(), ctypes.c_int64(), ctypes.c_uint32()
+        _check(lib().sv_batch_read(self._h, i, _dp(U) if state else None, ctypes.byref(t),
+                                   ctypes.byref(k), ctypes.byref(f)), "sv_batch_read")
+        return U, t.value, k.value, f.value
+
+    def mode_log(self, i: int):
+        cap = self.log_cap
+        t, re, im = np.empty(cap), np.empty(cap), np.empty(cap)
+        c = ctypes.c_int64()
+        _check(lib().sv_batch_mode_log(self._h, i, _dp(t), _dp(re), _dp(im), cap, ctypes.byref(c)),
+               "sv_batch_mode_log")
+        n = c.value
+        return t[:n], re[:n] + 1j * im[:n]
