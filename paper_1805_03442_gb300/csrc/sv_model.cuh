@@ -67,10 +67,26 @@ constexpr uint32_t FLAG_DT = 2u;
 
 template <typename R> struct Ar;
 
+// The float kernels use the SFU approximations directly (PTX rcp/rsqrt/lg2/ex2
+// .approx.ftz, each within a few ulp; subnormal inputs are flushed, which a
+// physical state never produces).
 template <> struct Ar<float> {
-  static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
-  static __device__ __forceinline__ float sqrt_pos(float x) { return x * rsqrtf(x); }
-  static __device__ __forceinline__ float lg2(float x) { return __log2f(x); }
+  static __device__ __forceinline__ float rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
+  static __device__ __forceinline__ float rsqrt(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
+  static __device__ __forceinline__ float sqrt_pos(float x) { return x * rsqrt(x); }
+  static __device__ __forceinline__ float lg2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
   static __device__ __forceinline__ float ex2(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

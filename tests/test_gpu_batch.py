@@ -42,7 +42,7 @@ def _mini_sweep(seed: int, nruns: int):
     runs, states = [], []
     for i in range(nruns):
         r = inputs.sweep_runs(seed * 1000 + i, 1, n_lo=33, n_hi=700)[0]
-        run = Run(n=r.n, t_end=0.25 * r.t_end, S=r.S, tau0=max(r.tau0, 2e-3), tau_rho=r.tau_rho,
+        run = Run(n=r.N, t_end=0.25 * r.t_end, S=r.S, tau0=max(r.tau0, 2e-3), tau_rho=r.tau_rho,
                   tau_T=r.tau_T, Q_rho=r.Q_rho, Q_T=r.Q_T, I_rho=r.I_rho, I_T=r.I_T, m=r.m)
         if i % 7 == 3:                       # zero exponents (the qi_zero kernel when alone)
             run = replace(run, Q_rho=0.0, Q_T=0.0, I_rho=0.0, I_T=0.0)
@@ -125,9 +125,10 @@ def test_batch_fp64_matches_oracle(sv):
 
 @pytest.mark.parametrize("m", [1, 2, 3])
 def test_logged_mode_grows_at_eq8_rate(sv, m):
-    """Eigenmode of mode m on L = 1 (N = 512), tau0 0.1, S 1: the batch's logged
-    a_m(t) grows at Im omega within 2% and turns at Re omega within 1%."""
-    N = 512
+    """Eigenmode of mode m on L = 1 (N = 512 m: 512 cells per wavelength),
+    tau0 0.1, S 1: the batch's logged a_m(t) grows at Im omega within 2% and
+    turns at Re omega within 1%."""
+    N = 512 * m
     Po = O.Params(tau0=0.1, limiter=O.VANLEER)
     k = 2 * math.pi * m
     w = D.growing_acoustic_root(Po, k)
