@@ -82,7 +82,7 @@ def test_batch_equals_looped_single_runs(sv, prec):
             # runs that blow up (strongly unstable draws) must fail identically too
             assert fb == fs, (i, fb, fs)
             assert tb == ts and kb == ks, (i, tb, ts, kb, ks)
-            assert np.array_equal(Ub, Us), (i, np.max(np.abs(Ub - Us)))
+            assert np.array_equal(Ub, Us, equal_nan=True), (i, np.nanmax(np.abs(Ub - Us)))
             ok += fb == 0 and tb == run.t_end
         assert ok >= len(runs) // 2
 
@@ -97,7 +97,8 @@ def test_batch_rerun_after_reset_is_identical(sv):
         b.run()
         for i in range(len(runs)):
             U, t, k, f = b.read(i)
-            assert np.array_equal(U, first[i][0]) and t == first[i][1] and k == first[i][2]
+            assert np.array_equal(U, first[i][0], equal_nan=True)
+            assert t == first[i][1] and k == first[i][2]
 
 
 def test_batch_fp64_matches_oracle(sv):
@@ -126,16 +127,18 @@ def test_batch_fp64_matches_oracle(sv):
 @pytest.mark.parametrize("m", [1, 2, 3])
 def test_logged_mode_grows_at_eq8_rate(sv, m):
     """Eigenmode of mode m on L = 1 (N = 512 m: 512 cells per wavelength),
-    tau0 0.1, S 1: the batch's logged a_m(t) grows at Im omega within 2% and
-    turns at Re omega within 1%."""
+    tau0 0.1, S 1, amplitude 1e-4: the batch's logged a_m(t) grows at Im omega
+    within 2% and turns at Re omega within 1%.  (A float state cannot follow
+    much smaller amplitudes: each step changes rho by ~dt k |rho'|, which must
+    stay above float's unit roundoff at rho ~ 1.)"""
     N = 512 * m
     Po = O.Params(tau0=0.1, limiter=O.VANLEER)
     k = 2 * math.pi * m
     w = D.growing_acoustic_root(Po, k)
-    t_end = math.log(50.0) / w.imag
+    t_end = math.log(30.0) / w.imag
     md = D.eigenmode(Po, k, w)
     U0 = inputs.waves_1d(1.4, N, 1.0, inputs.equilibrium_primitive(Po.Ck, Po.S),
-                         [inputs.Mode(m=m, shape=md["prim"], scale=1e-5)])
+                         [inputs.Mode(m=m, shape=md["prim"], scale=1e-4)])
     run = Run(n=N, t_end=t_end, S=1.0, tau0=0.1, m=m)
     P = sv.Params(precision=sv.FP32, limiter=sv.VANLEER)
     with sv.Batch(P, [run, replace(run, m=0)], [U0, U0], log_cap=40) as b:
@@ -160,7 +163,7 @@ def test_stability_map_signs(sv):
         w = D.growing_acoustic_root(Po, 2 * math.pi)
         md = D.eigenmode(Po, 2 * math.pi, w)
         U0 = inputs.waves_1d(1.4, 512, 1.0, inputs.equilibrium_primitive(0.1, S),
-                             [inputs.Mode(m=1, shape=md["prim"], scale=1e-5)])
+                             [inputs.Mode(m=1, shape=md["prim"], scale=1e-4)])
         runs.append(Run(n=512, t_end=3.0, S=S, tau0=0.05, m=1))
         states.append(U0)
     P = sv.Params(precision=sv.FP32, limiter=sv.VANLEER)
