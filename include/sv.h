@@ -50,6 +50,7 @@ extern "C" {
 #define SV_ENONPHYS   -4   /* a cell reached rho <= 0, p <= 0 or a non-finite value */
 #define SV_EDT        -5   /* the time step collapsed (dt <= 0 or non-finite) */
 #define SV_EMAXSTEPS  -7   /* sv_run_to stopped at max_steps before t_end */
+#define SV_ESIZE      -8   /* a size beyond the stated maximum of an entry point */
 
 /* ---- status flag bits (sv_status) */
 #define SV_FLAG_NONPHYS  1u
@@ -203,6 +204,40 @@ int sv_batch_mode_log(sv_batch* b, int64_t run, double* t, double* re, double* i
                       int64_t* count);
 
 void sv_batch_free(sv_batch* b);
+
+/* ------------------------------------------------------------------------
+ * Allocation-free 1D step.  The paper has no counterpart: this is a service
+ * of the library for callers that cannot allocate device memory -- code that
+ * runs while another framework captures a CUDA graph (where cudaMalloc is not
+ * allowed), processes whose device memory comes from a fixed pool that
+ * forbids allocation after start-up, and hosts that must not allocate on
+ * their stepping path.  Such a caller owns the two state buffers; the small
+ * control block the fused kernel needs (time, dt, the eq.-16 reduction keys,
+ * the block-completion ticket) lives in a file-scope static device array of
+ * SV_NOALLOC_SCRATCH_BYTES bytes that every GPU loading libsv.so holds until
+ * the process exits.
+ * ------------------------------------------------------------------------ */
+#define SV_NOALLOC_SCRATCH_BYTES 256
+#define SV_NOALLOC_MAX_CELLS ((1 << 29) - 1)   /* largest grid (32-bit offsets) */
+
+/* One MUSCL-Hancock step of a 1D periodic grid of n cells (length L) from the
+   caller's device buffer U_in to the caller's device buffer U_out (each
+   4 * n elements of float for SV_FP32 / SV_FP32_P64 or double for SV_FP64,
+   field-major rho, rho v, E, E_nu; they must not overlap), with dt from
+   eq. 16 (capped by c_tau * min tau) on U_in.  Same kernels and results as
+   sv_step on a solver holding U_in.  Allocates nothing and calls no
+   allocating routine.
+   dt_used / flags (host pointers, each may be NULL) receive the dt taken and
+   the SV_FLAG_* bits of the step; giving either makes the call wait for the
+   stream, otherwise it is asynchronous on cuda_stream.
+   The first call on a device looks up the device address of the static
+   array (cudaGetSymbolAddress, with that device current): make that first
+   call before any stream capture.  Every call resets the control block it
+   finds, since the array keeps the previous call's contents; calls that
+   overlap on the GPU (other streams, other host threads) share that one
+   array and race.  n beyond SV_NOALLOC_MAX_CELLS returns SV_ESIZE. */
+int sv_step1d_noalloc(const sv_params* p, int64_t n, double L, const void* U_in, void* U_out,
+                      double* dt_used, uint32_t* flags, void* cuda_stream);
 
 /* Human-readable name of a status code. */
 const char* sv_strerror(int code);

@@ -372,6 +372,7 @@ const char* sv_strerror(int code) {
     case SV_ENONPHYS: return "non-physical state (rho <= 0, p <= 0 or non-finite)";
     case SV_EDT: return "time step collapsed";
     case SV_EMAXSTEPS: return "max_steps reached before t_end";
+    case SV_ESIZE: return "size beyond the maximum of this entry point";
     default: return "unknown status";
   }
 }

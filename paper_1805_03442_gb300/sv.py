@@ -18,6 +18,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libsv.so")
 
 SV_OK, SV_EINVAL, SV_ENOMEM, SV_ECUDA, SV_ENONPHYS, SV_EDT, SV_EMAXSTEPS = 0, -1, -2, -3, -4, -5, -7
+SV_ESIZE = -8
+NOALLOC_MAX_CELLS = (1 << 29) - 1
 FLAG_NONPHYS, FLAG_DT, FLAG_MAXSTEPS = 1, 2, 4
 MINMOD, VANLEER, MC = 0, 1, 2
 FP32, FP64, FP32_P64 = 0, 1, 2
@@ -26,7 +28,7 @@ EXPORTS = ("sv_required_bytes", "sv_init", "sv_write_state", "sv_read_state", "s
            "sv_step", "sv_run_to", "sv_time", "sv_conservation", "sv_status",
            "sv_state_device", "sv_free", "sv_strerror", "sv_batch_required_bytes",
            "sv_batch_init", "sv_batch_reset", "sv_batch_run", "sv_batch_sync", "sv_batch_read",
-           "sv_batch_mode_log", "sv_batch_free")
+           "sv_batch_mode_log", "sv_batch_free", "sv_step1d_noalloc")
 
 
 class SvError(RuntimeError):
@@ -118,6 +120,8 @@ def lib() -> ctypes.CDLL:
                                     ctypes.POINTER(ctypes.c_int64)]
     L.sv_batch_free.argtypes = [vp]
     L.sv_batch_free.restype = None
+    L.sv_step1d_noalloc.argtypes = [ctypes.POINTER(_Params), ctypes.c_int64, ctypes.c_double, vp, vp,
+                                    dp, ctypes.POINTER(ctypes.c_uint32), vp]
     _lib = L
     return L
 
@@ -150,6 +154,23 @@ def grid(n, L=None) -> _Grid:
         g.n[a] = n[a] if a < len(n) else 1
         g.L[a] = L[a] if a < len(L) else 1.0
     return g
+
+
+def step1d_noalloc(params: Params, n: int, L: float, u_in: int, u_out: int, stream=None,
+                   wait: bool = True):
+    """sv_step1d_noalloc: one 1D step from the caller's device buffer u_in to
+    u_out (device addresses, 4 * n elements of the params' precision), for
+    callers that cannot allocate device memory.  Returns (dt taken, flags)
+    when `wait`, else None (asynchronous)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    dt, fl = ctypes.c_double(), ctypes.c_uint32()
+    rc = lib().sv_step1d_noalloc(ctypes.byref(params.c()), int(n), float(L), ctypes.c_void_p(u_in),
+                                 ctypes.c_void_p(u_out), ctypes.byref(dt) if wait else None,
+                                 ctypes.byref(fl) if wait else None,
+                                 ctypes.c_void_p(st.cuda_stream))
+    _check(rc, "sv_step1d_noalloc")
+    return (dt.value, fl.value) if wait else None
 
 
 class Solver:
