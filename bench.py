@@ -50,11 +50,11 @@ WORKLOADS = {
     "1d": dict(dims=lambda a: (a.n,), params=dict(tau0=0.08, S=1.0, cfl=0.4),
                desc="1D periodic MUSCL-Hancock step, N={cells} cells, h=1/1024, 64 random-phase "
                     "acoustic modes (k^-1, 1e-3), S=1, tau0=0.08, CFL 0.4"),
-    "2d": dict(dims=lambda a: (8192, 8192), params=dict(tau0=0.01, S=1.0, cfl=0.4),
-               desc="2D periodic unsplit MUSCL-Hancock step, 8192x8192, plane wave (7,4) at 29.7 deg "
+    "2d": dict(dims=lambda a: (a.side or 8192,) * 2, params=dict(tau0=0.01, S=1.0, cfl=0.4),
+               desc="2D periodic unsplit MUSCL-Hancock step, {side}x{side}, plane wave (7,4) at 29.7 deg "
                     "amplitude 1e-3 + white noise 1e-5, S=1, tau0=0.01, CFL 0.4"),
-    "3d": dict(dims=lambda a: (512, 512, 512), params=dict(tau0=0.08, S=1.0, cfl=0.3),
-               desc="3D periodic unsplit MUSCL-Hancock step, 512^3, isotropic k^-2 random density/"
+    "3d": dict(dims=lambda a: (a.side or 512,) * 3, params=dict(tau0=0.08, S=1.0, cfl=0.3),
+               desc="3D periodic unsplit MUSCL-Hancock step, {side}^3, isotropic k^-2 random density/"
                     "velocity perturbations amplitude 1e-3, S=1, tau0=0.08, CFL 0.3"),
 }
 
@@ -175,6 +175,19 @@ def dist_init():
     return dist.get_rank(), dist.get_world_size(), dist
 
 
+def aggregate(local_seconds: float, local_units: float, dist=None, device: str = "cpu"):
+    """Whole-job figures over ranks: (max time over ranks, units of all ranks).
+    Works with gloo (CPU tensors) and nccl (CUDA tensors)."""
+    if dist is None:
+        return local_seconds, local_units
+    import torch
+    t = torch.tensor([local_seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([local_units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_reference(args):
     rank, ws, dist = dist_init()
     if rank != 0:
@@ -198,7 +211,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": W["desc"].format(cells=ncell), "cells": ncell},
+            "config": {"workload": W["desc"].format(cells=ncell, side=dims[0]), "cells": ncell},
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": O.threads(), "kind": "oracle",
                              "sample": f"{args.steps} whole-grid FP64 oracle steps of the same "
                                        f"workload"},
@@ -251,11 +264,7 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
     times = [a.elapsed_time(b) * 1e-3 for a, b in ev]
-    tot = sum(times)
-    if dist is not None:
-        t = torch.tensor([tot], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
+    tot, units = aggregate(sum(times), float(ncell * args.steps), dist, device="cuda")
     status = solver.status()
     t_sim, nsteps = solver.time()
 
@@ -282,14 +291,14 @@ def run_ours(args):
     step_s = tot / args.steps
     alg_bytes = 2 * nf * esize * ncell             # read + write every conserved field once
     achieved = alg_bytes / step_s / 1e9
-    value = ws * ncell * args.steps / tot
+    value = units / tot
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "fp32_p64": "f32"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": W["desc"].format(cells=ncell), "cells": ncell,
+        "config": {"workload": W["desc"].format(cells=ncell, side=dims[0]), "cells": ncell,
                    "precision": args.precision,
                    "l2": "flushed by a 256 MiB write before every timed step",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
@@ -406,6 +415,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_p64"])
     ap.add_argument("--n", type=int, default=1 << 22, help="cells of the 1d workload")
     ap.add_argument("--workload", default="1d", choices=sorted(WORKLOADS) + ["sweep"])
+    ap.add_argument("--side", type=int, default=0,
+                    help="cells per axis of the 2d / 3d workloads (default 8192 / 512)")
     ap.add_argument("--runs", type=int, default=4096, help="runs of the sweep workload")
     ap.add_argument("--subset", type=int, default=64, help="looped comparison subset of the sweep")
     ap.add_argument("--cpu-budget", type=float, default=10.0)

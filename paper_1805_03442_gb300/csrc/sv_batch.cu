@@ -32,6 +32,7 @@ struct RunDev {
   KParams kp;            // per-run parameters (h = L / n)
   int64_t off;           // element offset of the run's block (4 fields x stride)
   int n, stride, mode, log_count;
+  int src, pad2;         // source variant of the run (as a single solver would pick it)
   double t, t_end;
   int64_t steps;
   uint32_t flags, cur, pad0, pad1;
@@ -83,7 +84,11 @@ __device__ __forceinline__ void block_sum2(R& a, R& b, R* s_a, R* s_b) {
     }
 }
 
-template <typename R, int PP, int LIM, int SRC, int MINB>
+// Every run is stepped with the source variant a single 1D solver with the
+// same parameters would use (none in the frozen limit, pump = sink for zero
+// exponents, general otherwise), chosen per run at run time, so that a batched
+// run and a looped solver run execute the same instructions.
+template <typename R, int PP, int LIM, int MINB>
 __global__ void __launch_bounds__(NTB, MINB)
 batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns,
              int* __restrict__ queue, R* __restrict__ bufA, R* __restrict__ bufB,
@@ -92,8 +97,9 @@ batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns
   __shared__ uint32_t s_f[NTB / 32];
   __shared__ int s_run, s_stop, s_last, s_log;
   __shared__ double s_dt, s_t;
-  __shared__ R ring[NTB / 32][4 * Ring<R>::RS * 32];
+  extern __shared__ __align__(16) unsigned char smemb[];   // per-warp rings
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  R* ring = reinterpret_cast<R*>(smemb) + warp * (ring1d_bytes<R>() / sizeof(R));
 
   for (;;) {
     if (threadIdx.x == 0) s_run = atomicAdd(queue, 1);
@@ -103,11 +109,11 @@ batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns
     RunDev* rd = runs + order[qi];
     const KParams kp = rd->kp;
     const P<R> k(kp);
-    const int n = rd->n, stride = rd->stride, mode = rd->mode;
+    const int n = rd->n, stride = rd->stride, mode = rd->mode, src = rd->src;
     const double t_end = rd->t_end;
     R* A = bufA + rd->off;
     R* B = bufB + rd->off;
-    const int nchunk = (n + 31) / 32;
+    const int nchunk = (n + 63) / 64;
     const int c0 = warp * nchunk / (NTB / 32), c1 = (warp + 1) * nchunk / (NTB / 32);
     double* lg = logs + (int64_t)(order[qi]) * log_cap * 3;
     const double log_dt = log_cap > 1 ? t_end / (double)(log_cap - 1) : INFINITY;
@@ -177,8 +183,15 @@ batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns
       R* Uout = cur ? A : B;
       R smax = 0, akey = -INFINITY;
       uint32_t flags = 0;
-      step1d_warp<R, PP, LIM, SRC>(k, Uin, Uout, n, stride, c0, c1, lane, dt, dtdx, dt_2h, dt_2,
-                                   smax, akey, flags, ring[warp]);
+      if (src == 0)
+        step1d_warp<R, PP, LIM, 0>(k, Uin, Uout, n, stride, c0, c1, lane, dt, dtdx, dt_2h, dt_2,
+                                   smax, akey, flags, ring);
+      else if (src == 1)
+        step1d_warp<R, PP, LIM, 1>(k, Uin, Uout, n, stride, c0, c1, lane, dt, dtdx, dt_2h, dt_2,
+                                   smax, akey, flags, ring);
+      else
+        step1d_warp<R, PP, LIM, 2>(k, Uin, Uout, n, stride, c0, c1, lane, dt, dtdx, dt_2h, dt_2,
+                                   smax, akey, flags, ring);
       // the barrier inside block_max also orders this step's stores before the
       // next step's loads of neighbouring warps' cells
       block_max(smax, akey, flags, s_a, s_b, s_f);
@@ -216,33 +229,25 @@ batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns
   }
 }
 
-template <typename R, int PP, int LIM, int SRC>
+template <typename R, int PP, int LIM>
 struct KB {
   static constexpr int MINB = sizeof(R) == 8 ? 1 : 2;
-  static constexpr auto fn = batch_kernel<R, PP, LIM, SRC, MINB>;
+  static constexpr auto fn = batch_kernel<R, PP, LIM, MINB>;
 };
 
-template <int LIM, int SRC>
+template <int LIM>
 static void* bpick_prec(int precision) {
   switch (precision) {
-    case PREC_FP64: return (void*)KB<double, 0, LIM, SRC>::fn;
-    case PREC_FP32_P64: return (void*)KB<float, 1, LIM, SRC>::fn;
-    default: return (void*)KB<float, 0, LIM, SRC>::fn;
+    case PREC_FP64: return (void*)KB<double, 0, LIM>::fn;
+    case PREC_FP32_P64: return (void*)KB<float, 1, LIM>::fn;
+    default: return (void*)KB<float, 0, LIM>::fn;
   }
 }
-template <int LIM>
-static void* bpick_src(int precision, int src) {
-  switch (src) {
-    case 0: return bpick_prec<LIM, 0>(precision);
-    case 1: return bpick_prec<LIM, 1>(precision);
-    default: return bpick_prec<LIM, 2>(precision);
-  }
-}
-static void* bpick(int limiter, int src, int precision) {
+static void* bpick(int limiter, int precision) {
   switch (limiter) {
-    case 1: return bpick_src<1>(precision, src);
-    case 2: return bpick_src<2>(precision, src);
-    default: return bpick_src<0>(precision, src);
+    case 1: return bpick_prec<1>(precision);
+    case 2: return bpick_prec<2>(precision);
+    default: return bpick_prec<0>(precision);
   }
 }
 
@@ -255,7 +260,6 @@ struct sv_batch {
   int64_t nruns = 0;
   int log_cap = 0;
   int esize = 4;
-  int src = 0;
   cudaStream_t stream = nullptr, cap_stream = nullptr;
   void* mem = nullptr;
   bool owns_mem = false;
@@ -349,6 +353,10 @@ int upload(sv_batch* b, const double* host) {
   return cudaStreamSynchronize(b->stream) == cudaSuccess ? SV_OK : SV_ECUDA;
 }
 
+size_t batch_smem(int precision) {
+  return (size_t)(NTB / 32) * (precision == SV_FP64 ? ring1d_bytes<double>() : ring1d_bytes<float>());
+}
+
 cudaError_t launch_batch(sv_batch* b, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(b->queue, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
@@ -356,7 +364,7 @@ cudaError_t launch_batch(sv_batch* b, cudaStream_t st) {
   int lc = b->log_cap;
   int64_t ms = b->max_steps;
   void* args[] = {&b->runs, &b->order, &nr, &b->queue, &b->buf[0], &b->buf[1], &b->logs, &lc, &ms};
-  return cudaLaunchKernel(b->fn, dim3(b->grid), dim3(NTB), args, 0, st);
+  return cudaLaunchKernel(b->fn, dim3(b->grid), dim3(NTB), args, batch_smem(b->p.precision), st);
 }
 
 int read_runs(sv_batch* b) {
@@ -400,7 +408,6 @@ int sv_batch_init(const sv_params* p, const sv_run* runs, int64_t nruns,
   b->host_runs.resize((size_t)nruns);
   b->n.resize((size_t)nruns);
   int64_t off = 0;
-  bool any_general = false, all_frozen = true;
   for (int64_t i = 0; i < nruns; ++i) {
     const sv_run& r = runs[i];
     RunDev d;
@@ -425,8 +432,7 @@ int sv_batch_init(const sv_params* p, const sv_run* runs, int64_t nruns,
     k.c_tau = p->c_tau;
     k.limiter = p->limiter;
     kparams_finish(k);
-    if (!k.frozen) all_frozen = false;
-    if (!k.frozen && !k.qi_zero) any_general = true;
+    d.src = k.frozen ? 0 : (k.qi_zero ? 1 : 2);
     d.off = off;
     d.n = (int)r.n;
     d.stride = (int)stride_of(r.n);
@@ -437,10 +443,7 @@ int sv_batch_init(const sv_params* p, const sv_run* runs, int64_t nruns,
     off += 4 * stride_of(r.n);
   }
   b->total_elems = off;
-  // one kernel variant for the whole batch: the general source covers runs
-  // with zero exponents or in the frozen limit with identical results
-  b->src = all_frozen ? 0 : (any_general ? 2 : 1);
-  b->fn = bpick(p->limiter, b->src, p->precision);
+  b->fn = bpick(p->limiter, p->precision);
 
   if (device_mem) b->mem = device_mem;
   else {
@@ -471,7 +474,10 @@ int sv_batch_init(const sv_params* p, const sv_run* runs, int64_t nruns,
   if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, b->fn, NTB, 0) != cudaSuccess ||
+      cudaFuncSetAttribute(b->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)batch_smem(p->precision)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, b->fn, NTB, batch_smem(p->precision)) !=
+          cudaSuccess ||
       cudaMemcpyAsync(b->order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice,
                       b->stream) != cudaSuccess)
     rc = SV_ECUDA;

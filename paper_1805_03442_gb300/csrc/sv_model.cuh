@@ -32,7 +32,9 @@ struct KParams {
   int frozen;    // 1: no source at all (Q = I = 0, 1/tau = 0)
   int qi_zero;   // 1: all Q and I exponents are zero (Q = I = Q0)
   int pad;
-  float f[12];   // the first twelve values above rounded to float (kparams_finish)
+  // float copies for the float kernels (kparams_finish): the twelve values
+  // above, then log2(1/tau0) (0 in the frozen limit), -tau_rho, -tau_T
+  float f[16];
 };
 
 // Fill the float copies once on the host, so float kernels convert nothing.
@@ -40,6 +42,10 @@ inline void kparams_finish(KParams& k) {
   const double v[12] = {k.gamma, k.g1, k.Ck, k.Q0, k.tau0, k.inv_tau0,
                         k.tau_rho, k.tau_T, k.Q_rho, k.Q_T, k.I_rho, k.I_T};
   for (int i = 0; i < 12; ++i) k.f[i] = (float)v[i];
+  k.f[12] = k.inv_tau0 > 0.0 ? (float)log2(k.inv_tau0) : 0.0f;
+  k.f[13] = (float)(-k.tau_rho);
+  k.f[14] = (float)(-k.tau_T);
+  k.f[15] = 0.0f;
 }
 
 // Device control block: time, step size and the reductions of one solver.
@@ -115,11 +121,13 @@ template <> struct P<double> {
 template <> struct P<float> {
   float gamma, g1, Ck, Q0, inv_tau0, tau0;
   float tau_rho, tau_T, Q_rho, Q_T, I_rho, I_T;
+  float l2_inv_tau0, ntau_rho, ntau_T;   // log2(1/tau0), -tau_rho, -tau_T
   int limiter, frozen, qi_zero;
   __device__ __forceinline__ explicit P(const KParams& k)
       : gamma(k.f[0]), g1(k.f[1]), Ck(k.f[2]), Q0(k.f[3]), inv_tau0(k.f[5]), tau0(k.f[4]),
         tau_rho(k.f[6]), tau_T(k.f[7]), Q_rho(k.f[8]), Q_T(k.f[9]), I_rho(k.f[10]),
-        I_T(k.f[11]), limiter(k.limiter), frozen(k.frozen), qi_zero(k.qi_zero) {}
+        I_T(k.f[11]), l2_inv_tau0(k.f[12]), ntau_rho(k.f[13]), ntau_T(k.f[14]),
+        limiter(k.limiter), frozen(k.frozen), qi_zero(k.qi_zero) {}
 };
 
 // The dt-derived factors of the next step, read by the step kernels.
@@ -184,8 +192,9 @@ template <int SRC> struct Src<float, SRC> {
       yE = yEv = 0.0f;
       return;
     }
+    // 1/tau = (1/tau0) rho^-tau_rho T^-tau_T = 2^(log2(1/tau0) - tau_rho lg rho - tau_T lg T)
     const float lr = Ar<float>::lg2(rho), lT = Ar<float>::lg2(T);
-    const float inv_tau = k.inv_tau0 * Ar<float>::ex2(-fmaf(k.tau_rho, lr, k.tau_T * lT));
+    const float inv_tau = Ar<float>::ex2(fmaf(k.ntau_rho, lr, fmaf(k.ntau_T, lT, k.l2_inv_tau0)));
     float Q = k.Q0;
     yE = 0.0f;
     if (SRC == 2) {

@@ -26,12 +26,13 @@ step1d_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
   const P<R> k(kp);
   const StepDt<R> sd((const volatile Ctl*)ctl);
   const R dt = sd.dt, dtdx = sd.dtdx, dt_2h = sd.dt_2h, dt_2 = sd.dt_2;
-  __shared__ R ring[NT1 / 32][4 * Ring<R>::RS * 32];
+  extern __shared__ __align__(16) unsigned char smem1d[];   // per-warp rings
+  R* ring = reinterpret_cast<R*>(smem1d) + (threadIdx.x >> 5) * (ring1d_bytes<R>() / sizeof(R));
 
   const int lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * (NT1 / 32);
   const int warp = blockIdx.x * (NT1 / 32) + (threadIdx.x >> 5);
-  const int nchunk = (N + 31) / 32;
+  const int nchunk = (N + 63) / 64;
   const int c0 = (int)((int64_t)warp * nchunk / nwarps);
   const int c1 = (int)((int64_t)(warp + 1) * nchunk / nwarps);
 
@@ -39,7 +40,7 @@ step1d_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
   uint32_t flags = 0;
 
   step1d_warp<R, PP, LIM, SRC>(k, Uin, Uout, N, N, c0, c1, lane, dt, dtdx, dt_2h, dt_2, smax, akey,
-                               flags, ring[threadIdx.x >> 5]);
+                               flags, ring);
   reduce_and_finalize<R, NT1>(ctl, kp, (double)smax, (double)akey, flags, true);
 }
 
@@ -47,7 +48,7 @@ step1d_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
 // limiter and source kind are compile-time; one of them is chosen per solver.
 template <typename R, int PP, int LIM, int SRC>
 struct K1 {
-  static constexpr int MINB = sizeof(R) == 8 ? 1 : 3;
+  static constexpr int MINB = sizeof(R) == 8 ? 1 : 2;
   static constexpr auto fn = step1d_kernel<R, PP, LIM, SRC, MINB>;
 };
 
@@ -78,11 +79,21 @@ static void* pick(const KParams& kp, int precision) {
   }
 }
 
+static size_t smem_bytes(int precision) {
+  return (size_t)(NT1 / 32) * (precision == PREC_FP64 ? ring1d_bytes<double>() : ring1d_bytes<float>());
+}
+
+// Sets the kernel's dynamic shared-memory limit (host side, outside any stream
+// capture) and returns the persistent grid size.
 int step1d_grid(const KParams& kp, int precision) {
   int dev = 0, sms = 0, per = 0;
+  const void* fn = pick(kp, precision);
+  const size_t smem = smem_bytes(precision);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pick(kp, precision), NT1, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, NT1, smem);
   if (per < 1) per = 1;
   return sms * per;
 }
@@ -92,7 +103,7 @@ cudaError_t step1d_launch(int precision, const KParams& kp, void* a, void* b, Ct
   if (N >= (1LL << 31) / 4) return cudaErrorInvalidValue;
   int n32 = (int)N;
   void* args[] = {(void*)&kp, &a, &b, &ctl, &n32};
-  return cudaLaunchKernel(pick(kp, precision), dim3(grid), dim3(NT1), args, 0, st);
+  return cudaLaunchKernel(pick(kp, precision), dim3(grid), dim3(NT1), args, smem_bytes(precision), st);
 }
 
 }  // namespace sv

@@ -3,16 +3,19 @@
 // kernel and the batched sweep kernel so that both compute every cell with
 // the same operations in the same order.
 //
-// A warp owns the 32-cell chunks [c0, c1) of a periodic grid of N cells and
-// slides along them, lane i <-> cell chunk_base + i.  Per chunk it
+// A warp owns the 64-cell chunks [c0, c1) of a periodic grid of N cells and
+// slides along them; lane i holds the cell pair (2i, 2i+1) of the chunk.
+// Per chunk it
 //   1. streams the 4 conserved fields through a per-warp ring of RS chunks in
-//      shared memory (cp.async, one coalesced 128-byte copy per field and
+//      shared memory (cp.async, one coalesced 256-byte copy per field and
 //      chunk, RS - 3 chunks in flight ahead of the one being computed),
-//   2. reads U_j and its neighbours U_{j-1}, U_{j+1} from the ring,
-//   3. limited slopes, positivity guard and the half-step predictor of the
-//      chunk's cells (each cell's predictor exactly once),
-//   4. the HLL flux of each cell's left face (each face exactly once; the left
-//      state comes from lane-1, for lane 0 from the previous chunk),
+//   2. reads its pair and the two outer neighbours U_{2i-1}, U_{2i+2} from the
+//      ring,
+//   3. limited slopes, positivity guard and the half-step predictor of both
+//      cells (each cell's predictor exactly once),
+//   4. the HLL fluxes of the pair's inner face and of its left face (each face
+//      exactly once; the left state of the left face comes from lane-1, for
+//      lane 0 from the previous chunk),
 //   5. the conservative update and half-step source of the PREVIOUS chunk,
 //      whose right-most face needed this chunk's first flux,
 //   6. the signal speed / tau bound of the updated cells for the next dt.
@@ -25,23 +28,37 @@ namespace sv {
 
 // Offsets are 32-bit: the host rejects grids with nf * ncell >= 2^31.
 
-// Ring depth (chunks) per warp: deep for float (memory-bound), shallow for
-// double (arithmetic-bound).
-template <typename R> struct Ring { static constexpr int RS = sizeof(R) == 4 ? 8 : 4; };
+// Ring depth (64-cell chunks) per warp.
+constexpr int kRing1d = 8;
 
-// Asynchronous global -> shared copy of one element (cp.async, L1-allocating).
+template <typename R> struct Pair;
+template <> struct Pair<float> { using T = float2; };
+template <> struct Pair<double> { using T = double2; };
+
+// Bytes of the per-warp ring: 4 fields x kRing1d chunks x 64 cells.
 template <typename R>
-__device__ __forceinline__ void cp_async_elem(R* smem, const R* gmem) {
+constexpr int ring1d_bytes() { return 4 * kRing1d * 64 * (int)sizeof(R); }
+
+// Asynchronous global -> shared copy of BYTES bytes (cp.async, L1-allocating).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  if constexpr (sizeof(R) == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES)
+               : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Primitive recovery (eq. 5, eq. 7): 1/rho, v, rho v^2, p.
+template <typename R, int PP>
+__device__ __forceinline__ void prim1(const P<R>& k, const R (&u)[4], R& ir, R& v, R& kin2, R& p) {
+  ir = Ar<R>::rcp(u[0]);
+  v = u[1] * ir;
+  kin2 = u[1] * v;
+  p = pressure<R, PP>(k, kin2, u[2], u[3]);
 }
 
 // Steps 1-3 for one cell: slopes d (= Theta h), predictor, face states
@@ -58,23 +75,23 @@ __device__ __forceinline__ void predict(const P<R>& k, const R (&u)[4], const R 
     a[f] = u[f] + (R)0.5 * d[f];
     b[f] = u[f] - (R)0.5 * d[f];
   }
-  const R va = a[1] * Ar<R>::rcp(a[0]);
-  const R pa = pressure<R, PP>(k, a[1] * va, a[2], a[3]);
-  const R vb = b[1] * Ar<R>::rcp(b[0]);
-  const R pb = pressure<R, PP>(k, b[1] * vb, b[2], b[3]);
+  R ira, va, ka, pa, irb, vb, kb, pb;
+  prim1<R, PP>(k, a, ira, va, ka, pa);
+  prim1<R, PP>(k, b, irb, vb, kb, pb);
   R dF[4];
   dF[0] = a[1] - b[1];
-  dF[1] = (a[1] * va + pa) - (b[1] * vb + pb);
+  dF[1] = (ka + pa) - (kb + pb);
   dF[2] = va * (a[2] + pa) - vb * (b[2] + pb);
   dF[3] = va * a[3] - vb * b[3];
-  if (!((a[0] > (R)0) && (pa > (R)0) && (b[0] > (R)0) && (pb > (R)0))) {
+  // positivity guard: a non-physical extrapolated state drops the slopes
+  if (!(fmin(fmin(a[0], pa), fmin(b[0], pb)) > (R)0)) {
 #pragma unroll
     for (int f = 0; f < 4; ++f) d[f] = dF[f] = (R)0;
   }
   R yE = 0, yEv = 0;
   if (SRC != 0) {
-    const R ir = Ar<R>::rcp(u[0]);
-    const R p = pressure<R, PP>(k, u[1] * (u[1] * ir), u[2], u[3]);
+    R ir, v, kin2, p;
+    prim1<R, PP>(k, u, ir, v, kin2, p);
     Src<R, SRC>::eval(k, u[0], p * ir, u[3], yE, yEv);
   }
   R uh[4];
@@ -89,9 +106,9 @@ __device__ __forceinline__ void predict(const P<R>& k, const R (&u)[4], const R 
   }
   yEh = yEvh = (R)0;
   if (SRC != 0) {
-    const R irh = Ar<R>::rcp(uh[0]);
-    const R ph = pressure<R, PP>(k, uh[1] * (uh[1] * irh), uh[2], uh[3]);
-    Src<R, SRC>::eval(k, uh[0], ph * irh, uh[3], yEh, yEvh);
+    R ir, v, kin2, p;
+    prim1<R, PP>(k, uh, ir, v, kin2, p);
+    Src<R, SRC>::eval(k, uh[0], p * ir, uh[3], yEh, yEvh);
   }
 }
 
@@ -103,23 +120,25 @@ __device__ __forceinline__ void hll(const P<R>& k, const R (&l)[4], const R (&r)
   R L[4], Rr[4];
 #pragma unroll
   for (int f = 0; f < 4; ++f) { L[f] = l[f]; Rr[f] = r[f]; }
-  R irL = Ar<R>::rcp(L[0]), uL = L[1] * irL, pL = pressure<R, PP>(k, L[1] * uL, L[2], L[3]);
-  R irR = Ar<R>::rcp(Rr[0]), uR = Rr[1] * irR, pR = pressure<R, PP>(k, Rr[1] * uR, Rr[2], Rr[3]);
-  if (!((L[0] > (R)0) && (pL > (R)0) && (Rr[0] > (R)0) && (pR > (R)0))) {
+  R irL, uL, kL, pL, irR, uR, kR, pR;
+  prim1<R, PP>(k, L, irL, uL, kL, pL);
+  prim1<R, PP>(k, Rr, irR, uR, kR, pR);
+  if (!(fmin(fmin(L[0], pL), fmin(Rr[0], pR)) > (R)0)) {
 #pragma unroll
     for (int f = 0; f < 4; ++f) { L[f] = fl[f]; Rr[f] = fr[f]; }
-    irL = Ar<R>::rcp(L[0]); uL = L[1] * irL; pL = pressure<R, PP>(k, L[1] * uL, L[2], L[3]);
-    irR = Ar<R>::rcp(Rr[0]); uR = Rr[1] * irR; pR = pressure<R, PP>(k, Rr[1] * uR, Rr[2], Rr[3]);
+    prim1<R, PP>(k, L, irL, uL, kL, pL);
+    prim1<R, PP>(k, Rr, irR, uR, kR, pR);
   }
   const R cL = Ar<R>::sqrt_pos(k.gamma * pL * irL);
   const R cR = Ar<R>::sqrt_pos(k.gamma * pR * irR);
   const R sl = fmin(fmin(uL - cL, uR - cR), (R)0);   // min(S_L, 0)
   const R sr = fmax(fmax(uL + cL, uR + cR), (R)0);   // max(S_R, 0)
-  const R FL[4] = {L[1], L[1] * uL + pL, uL * (L[2] + pL), uL * L[3]};
-  const R FR[4] = {Rr[1], Rr[1] * uR + pR, uR * (Rr[2] + pR), uR * Rr[3]};
-  const R inv = Ar<R>::rcp(sr - sl), slsr = sl * sr;
+  const R FL[4] = {L[1], kL + pL, uL * (L[2] + pL), uL * L[3]};
+  const R FR[4] = {Rr[1], kR + pR, uR * (Rr[2] + pR), uR * Rr[3]};
+  const R inv = Ar<R>::rcp(sr - sl);
+  const R wl = sr * inv, wr = -sl * inv, wd = sl * sr * inv;
 #pragma unroll
-  for (int f = 0; f < 4; ++f) F[f] = (sr * FL[f] - sl * FR[f] + slsr * (Rr[f] - L[f])) * inv;
+  for (int f = 0; f < 4; ++f) F[f] = wl * FL[f] + wr * FR[f] + wd * (Rr[f] - L[f]);
 }
 
 template <typename R>
@@ -127,85 +146,129 @@ __device__ __forceinline__ R shfl(R v, int src) {
   return __shfl_sync(0xffffffffu, v, src);
 }
 
-// One warp's share of a step: chunks [c0, c1) of the periodic grid of N cells
-// Uin -> Uout (fields `stride` elements apart).  `ring` is this warp's shared
-// buffer of 4 * RS * 32 elements.  Folds the updated cells' signal speed /
-// tau key / flags into the per-thread accumulators.
+// Conservative update (eq. 15) of one cell and its next-dt bound.
+template <typename R, int PP, int SRC>
+__device__ __forceinline__ void update_cell(const P<R>& k, const R (&u)[4], const R (&Fl)[4],
+                                            const R (&Fr)[4], R yE, R yEv, R dt, R dtdx,
+                                            R (&un)[4], R& smax, R& akey, uint32_t& flags) {
+  un[0] = u[0] - dtdx * (Fr[0] - Fl[0]);
+  un[1] = u[1] - dtdx * (Fr[1] - Fl[1]);
+  un[2] = u[2] - dtdx * (Fr[2] - Fl[2]) + dt * yE;
+  un[3] = u[3] - dtdx * (Fr[3] - Fl[3]) + dt * yEv;
+  const R v = un[1] * Ar<R>::rcp(un[0]);
+  cfl_cell<R, PP, SRC>(k, un[0], un[1] * v, fabs(v), un[2], un[3], smax, akey, flags);
+}
+
+// One warp's share of a step: chunks [c0, c1) (64 cells each) of the periodic
+// grid of N cells Uin -> Uout (fields `stride` elements apart).  `ring` is this
+// warp's shared buffer (ring1d_bytes<R>()).  Folds the updated cells' signal
+// speed / tau key / flags into the per-thread accumulators.
 template <typename R, int PP, int LIM, int SRC>
 __device__ __forceinline__ void step1d_warp(const P<R>& k, const R* __restrict__ Uin,
                                             R* __restrict__ Uout, int N, int stride, int c0, int c1,
                                             int lane, R dt, R dtdx, R dt_2h, R dt_2, R& smax,
                                             R& akey, uint32_t& flags, R* __restrict__ ring) {
-  constexpr int RS = Ring<R>::RS, RN = RS * 32, MASK = RN - 1;
+  using R2 = typename Pair<R>::T;
+  constexpr int RS = kRing1d, RN = RS * 64, MASK = RN - 1;
   if (c1 <= c0) return;
-  // cells c0*32-64 .. (c1+2)*32-1 are read; no index wrap needed inside [0, N)
-  const bool nowrap = c0 >= 2 && (c1 + 2) * 32 <= N;
+  // cells c0*64-128 .. (c1+2)*64-1 are read; inside [0, N) no index wraps
+  const bool nowrap = c0 >= 2 && (c1 + 2) * 64 <= N;
+  const bool pairs = nowrap && (stride % 2) == 0;    // 2-element copies are aligned
   // copy chunk c (if it is needed at all) into its ring slot; always commit a
   // group so that the wait counts below stay exact
   auto issue = [&](int c) {
     if (c <= c1 + 1) {
-      const int j = c * 32 + lane;
-      const int i = nowrap ? j : (int)wrap(j, N);
-      R* dst = ring + (c & (RS - 1)) * 32 + lane;
+      const int j = c * 64 + 2 * lane;
+      R* dst = ring + (c & (RS - 1)) * 64 + 2 * lane;
+      if (pairs) {
 #pragma unroll
-      for (int f = 0; f < 4; ++f) cp_async_elem(dst + f * RN, Uin + f * stride + i);
+        for (int f = 0; f < 4; ++f) cp_async<2 * sizeof(R)>(dst + f * RN, Uin + f * stride + j);
+      } else {
+        const int i0 = (int)wrap(j, N), i1 = (int)wrap(j + 1, N);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          cp_async<sizeof(R)>(dst + f * RN, Uin + f * stride + i0);
+          cp_async<sizeof(R)>(dst + f * RN + 1, Uin + f * stride + i1);
+        }
+      }
     }
     cp_async_commit();
   };
   for (int c = c0 - 2; c <= c0 + RS - 4; ++c) issue(c);   // RS - 1 chunks ahead
 
-  R Wp_prev[4] = {0, 0, 0, 0}, F_prev[4] = {0, 0, 0, 0}, yE_prev = 0, yEv_prev = 0;
+  R Wp1_prev[4] = {0, 0, 0, 0}, Fa_prev[4] = {0, 0, 0, 0}, Fb_prev[4] = {0, 0, 0, 0};
+  R y0E_prev = 0, y0Ev_prev = 0, y1E_prev = 0, y1Ev_prev = 0;
   const int src_m = (lane + 31) & 31, src_p = (lane + 1) & 31;
   // chunk index kk runs from c0-1 (warm-up) to c1 (trailing faces)
   for (int kk = c0 - 1; kk <= c1; ++kk) {
     cp_async_wait<RS - 4>();     // chunks up to kk+1 have landed for this lane ...
     __syncwarp();                // ... and for the warp; chunk kk-2 is no longer read
     issue(kk + RS - 2);          // reuses the slot of chunk kk-2
-    const int pos = (kk & (RS - 1)) * 32 + lane;
-    R Uc[4], Um[4], Up[4], Uprev[4];
+    const int pos = (kk & (RS - 1)) * 64 + 2 * lane;
+    R x0[4], x1[4], um[4], up[4], q0[4], q1[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       const R* rf = ring + f * RN;
-      Uc[f] = rf[pos];
-      Um[f] = rf[(pos - 1) & MASK];
-      Up[f] = rf[(pos + 1) & MASK];
-      Uprev[f] = rf[(pos - 32) & MASK];
+      const R2 c2 = *reinterpret_cast<const R2*>(rf + pos);
+      const R2 p2 = *reinterpret_cast<const R2*>(rf + ((pos - 64) & MASK));
+      x0[f] = c2.x;
+      x1[f] = c2.y;
+      q0[f] = p2.x;                // the previous chunk's pair (updated below)
+      q1[f] = p2.y;
+      um[f] = rf[(pos - 1) & MASK];
+      up[f] = rf[(pos + 2) & MASK];
     }
-    const int j = kk * 32 + lane;
-    R Wp[4], Wm[4], yEh, yEvh;
-    predict<R, PP, LIM, SRC>(k, Uc, Um, Up, dt_2h, dt_2, Wp, Wm, yEh, yEvh);
-    R F[4] = {0, 0, 0, 0};
+    R Wp0[4], Wm0[4], Wp1[4], Wm1[4], y0E, y0Ev, y1E, y1Ev;
+    predict<R, PP, LIM, SRC>(k, x0, um, x1, dt_2h, dt_2, Wp0, Wm0, y0E, y0Ev);
+    predict<R, PP, LIM, SRC>(k, x1, x0, up, dt_2h, dt_2, Wp1, Wm1, y1E, y1Ev);
+    R Fa[4] = {0, 0, 0, 0}, Fb[4];
+    hll<R, PP>(k, Wp0, Wm1, x0, x1, Fb);            // face 2i + 1/2
     if (kk >= c0) {
       R WL[4];
 #pragma unroll
-      for (int f = 0; f < 4; ++f) WL[f] = shfl(lane == 31 ? Wp_prev[f] : Wp[f], src_m);
-      hll<R, PP>(k, WL, Wm, Um, Uc, F);          // face j - 1/2
+      for (int f = 0; f < 4; ++f) WL[f] = shfl(lane == 31 ? Wp1_prev[f] : Wp1[f], src_m);
+      hll<R, PP>(k, WL, Wm0, um, x0, Fa);           // face 2i - 1/2
     }
     if (kk > c0) {
-      // update of cell j - 32 (previous chunk)
+      // update of the pair of chunk kk-1
       R FR[4];
 #pragma unroll
-      for (int f = 0; f < 4; ++f) FR[f] = shfl(lane == 0 ? F[f] : F_prev[f], src_p);
-      const int jo = j - 32;
+      for (int f = 0; f < 4; ++f) FR[f] = shfl(lane == 0 ? Fa[f] : Fa_prev[f], src_p);
+      const int jo = (kk - 1) * 64 + 2 * lane;
+      R n0[4], n1[4];
       if (jo < N) {
-        R un[4];
-        un[0] = Uprev[0] - dtdx * (FR[0] - F_prev[0]);
-        un[1] = Uprev[1] - dtdx * (FR[1] - F_prev[1]);
-        un[2] = Uprev[2] - dtdx * (FR[2] - F_prev[2]) + dt * yE_prev;
-        un[3] = Uprev[3] - dtdx * (FR[3] - F_prev[3]) + dt * yEv_prev;
+        update_cell<R, PP, SRC>(k, q0, Fa_prev, Fb_prev, y0E_prev, y0Ev_prev, dt, dtdx, n0, smax,
+                                akey, flags);
+        if (jo + 1 < N) {
+          update_cell<R, PP, SRC>(k, q1, Fb_prev, FR, y1E_prev, y1Ev_prev, dt, dtdx, n1, smax,
+                                  akey, flags);
+          if ((stride % 2) == 0) {
 #pragma unroll
-        for (int f = 0; f < 4; ++f) Uout[f * stride + jo] = un[f];
-        const R v = un[1] * Ar<R>::rcp(un[0]);
-        cfl_cell<R, PP, SRC>(k, un[0], un[1] * v, fabs(v), un[2], un[3], smax, akey, flags);
+            for (int f = 0; f < 4; ++f)
+              *reinterpret_cast<R2*>(Uout + f * stride + jo) = R2{n0[f], n1[f]};
+          } else {
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+              Uout[f * stride + jo] = n0[f];
+              Uout[f * stride + jo + 1] = n1[f];
+            }
+          }
+        } else {
+#pragma unroll
+          for (int f = 0; f < 4; ++f) Uout[f * stride + jo] = n0[f];
+        }
       }
     }
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-      Wp_prev[f] = Wp[f];
-      F_prev[f] = F[f];
+      Wp1_prev[f] = Wp1[f];
+      Fa_prev[f] = Fa[f];
+      Fb_prev[f] = Fb[f];
     }
-    yE_prev = yEh;
-    yEv_prev = yEvh;
+    y0E_prev = y0E;
+    y0Ev_prev = y0Ev;
+    y1E_prev = y1E;
+    y1Ev_prev = y1Ev;
   }
   cp_async_wait<0>();            // nothing in flight when the warp moves on
   __syncwarp();

@@ -20,9 +20,12 @@
 //   e. computes the marching-axis face between planes q-1 and q,
 //   f. updates plane q-1 (all its faces are now known) and folds its
 //      signal speed / tau bound for the next dt.
-// Three barriers per plane; loads are coalesced along x.
+// Three barriers per plane.  Each thread streams its own column (and the halo
+// threads their second-ring cells) through a per-thread ring of kPlaneRing
+// planes in shared memory with cp.async, four planes ahead of the one being
+// computed; copies are coalesced along x.
 #include "sv_internal.h"
-#include "sv_reduce.cuh"
+#include "sv_step1d.cuh"      // cp.async helpers
 
 namespace sv {
 
@@ -68,7 +71,7 @@ struct Nd {
     flux<A>(b, vb, pb, Fb);
 #pragma unroll
     for (int f = 0; f < NF; ++f) dF[f] = Fa[f] - Fb[f];
-    return (a[0] > (R)0) && (pa > (R)0) && (b[0] > (R)0) && (pb > (R)0);
+    return fmin(fmin(a[0], pa), fmin(b[0], pb)) > (R)0;
   }
 
   static __device__ __forceinline__ void source(const P<R>& k, const V& u, R& yE, R& yEv) {
@@ -89,7 +92,7 @@ struct Nd {
     R irL, pL, vL[DIM], irR, pR, vR[DIM];
     prim(k, L, irL, vL, pL);
     prim(k, Rr, irR, vR, pR);
-    if (!((L[0] > (R)0) && (pL > (R)0) && (Rr[0] > (R)0) && (pR > (R)0))) {
+    if (!(fmin(fmin(L[0], pL), fmin(Rr[0], pR)) > (R)0)) {
 #pragma unroll
       for (int f = 0; f < NF; ++f) { L[f] = fl[f]; Rr[f] = fr[f]; }
       prim(k, L, irL, vL, pL);
@@ -102,15 +105,27 @@ struct Nd {
     V FL, FR;
     flux<A>(L, vL, pL, FL);
     flux<A>(Rr, vR, pR, FR);
-    const R inv = Ar<R>::rcp(sr - sl), slsr = sl * sr;
+    const R inv = Ar<R>::rcp(sr - sl);
+    const R wl = sr * inv, wr = -sl * inv, wd = sl * sr * inv;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) F[f] = (sr * FL[f] - sl * FR[f] + slsr * (Rr[f] - L[f])) * inv;
+    for (int f = 0; f < NF; ++f) F[f] = wl * FL[f] + wr * FR[f] + wd * (Rr[f] - L[f]);
   }
 };
 
-template <typename R>
-__device__ __forceinline__ void ld(const R* __restrict__ U, int64_t ncell, int64_t idx, R* u, int nf) {
-  for (int f = 0; f < nf; ++f) u[f] = __ldg(U + f * ncell + idx);
+// Planes per thread ring (a power of two; four planes are in flight).
+constexpr int kPlaneRing = 8;
+
+// Slots of the second-ring cells: two per tile row (x ring) and, in 3D, two
+// per tile column (y ring).
+template <int DIM, int TX, int TY> struct HaloSlots {
+  static constexpr int N = 2 * TY + (DIM == 3 ? 2 * TX : 0);
+};
+
+template <typename R, int DIM, int TX, int TY>
+constexpr size_t stepnd_smem() {
+  constexpr int NF = DIM + 3, SY = DIM == 3 ? TY + 2 : 1, NT = TX * TY;
+  return sizeof(R) * ((size_t)NF * SY * (TX + 2) + 2 * (size_t)(DIM - 1) * NF * TY * TX +
+                      (size_t)kPlaneRing * NF * NT + (size_t)kPlaneRing * NF * HaloSlots<DIM, TX, TY>::N);
 }
 
 // DIM 2: TY must be 1; marching axis y.  DIM 3: marching axis z.
@@ -123,12 +138,19 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
   constexpr int NT = TX * TY;
   constexpr int SY = DIM == 3 ? TY + 2 : 1;     // rows of the shared state plane
   constexpr int AM = DIM - 1;                   // marching axis
-  // dynamic shared memory: sU[NF][SY][TX+2], sW[DIM-1][NF][TY][TX], sF[DIM-1][NF][TY][TX]
+  // dynamic shared memory: sU[NF][SY][TX+2], sW[DIM-1][NF][TY][TX],
+  // sF[DIM-1][NF][TY][TX], sR[D][NF][NT] (own-column ring), sH[D][NF][NH]
+  // (second-ring cells of the halo threads)
+  constexpr int D = kPlaneRing, NH = HaloSlots<DIM, TX, TY>::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R (*sU)[SY][TX + 2] = reinterpret_cast<R (*)[SY][TX + 2]>(smem_raw);
   R (*sW)[NF][TY][TX] = reinterpret_cast<R (*)[NF][TY][TX]>(smem_raw + sizeof(R) * NF * SY * (TX + 2));
   R (*sF)[NF][TY][TX] = reinterpret_cast<R (*)[NF][TY][TX]>(
       smem_raw + sizeof(R) * (NF * SY * (TX + 2) + (DIM - 1) * NF * TY * TX));
+  R (*sR)[NF][NT] = reinterpret_cast<R (*)[NF][NT]>(
+      smem_raw + sizeof(R) * (NF * SY * (TX + 2) + 2 * (DIM - 1) * NF * TY * TX));
+  R (*sH)[NF][NH] = reinterpret_cast<R (*)[NF][NH]>(
+      smem_raw + sizeof(R) * (NF * SY * (TX + 2) + 2 * (DIM - 1) * NF * TY * TX + D * NF * NT));
 
   const double dtd = vload(&ctl->dt);
   if (!(dtd > 0.0)) return;
@@ -163,30 +185,51 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
   R smax = 0, akey = -INFINITY;
   uint32_t flags = 0;
 
-  R Um1[NF], Uq[NF], Up1[NF], Up2[NF], Rx[NF], Ry[NF];
+  const int tid = threadIdx.x;
+  const int hx = ty * 2 + (tx == 0 ? 0 : 1);                              // x-ring slot
+  const int hy = 2 * TY + tx * 2 + (ty == 0 ? 0 : 1);                     // y-ring slot
+  // copy plane p of the own column (p <= q1 + 1) and of the second ring
+  // (p <= q1) into ring slot p mod D; always commit a group
+  auto issue = [&](int64_t p) {
+    const int sl = (int)(p & (D - 1));
+    if (p <= q1 + 1) {
+      const int64_t o = wrap(p, M) * plane;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) cp_async<sizeof(R)>(&sR[sl][f][tid], Uin + f * ncell + o + col);
+      if (p <= q1) {
+        if (ringx)
+#pragma unroll
+          for (int f = 0; f < NF; ++f) cp_async<sizeof(R)>(&sH[sl][f][hx], Uin + f * ncell + o + col_rx);
+        if (ringy)
+#pragma unroll
+          for (int f = 0; f < NF; ++f) cp_async<sizeof(R)>(&sH[sl][f][hy], Uin + f * ncell + o + col_ry);
+      }
+    }
+    cp_async_commit();
+  };
+
+  R Um1[NF], Uq[NF], Up1[NF];
   R Wm_prev[NF], D_prev[NF], H_prev[NF], yE_prev = 0, yEv_prev = 0;
 #pragma unroll
-  for (int f = 0; f < NF; ++f) Wm_prev[f] = D_prev[f] = H_prev[f] = Rx[f] = Ry[f] = (R)0;
+  for (int f = 0; f < NF; ++f) Wm_prev[f] = D_prev[f] = H_prev[f] = (R)0;
   auto pidx = [&](int64_t q) { return wrap(q, M) * plane; };
-  ld(Uin, ncell, pidx(q0 - 2) + col, Um1, NF);
-  ld(Uin, ncell, pidx(q0 - 1) + col, Uq, NF);
-  ld(Uin, ncell, pidx(q0) + col, Up1, NF);
-  ld(Uin, ncell, pidx(q0 + 1) + col, Up2, NF);
-  if (ringx) ld(Uin, ncell, pidx(q0 - 1) + col_rx, Rx, NF);
-  if (ringy) ld(Uin, ncell, pidx(q0 - 1) + col_ry, Ry, NF);
+  for (int64_t p = q0 - 2; p <= q0 + D - 4; ++p) issue(p);    // D - 1 planes ahead
 
   for (int64_t q = q0 - 1; q <= q1; ++q) {
-    // a. publish plane q
+    // a. planes q-1, q, q+1 of the own column and plane q's second ring have
+    //    landed; publish plane q
+    cp_async_wait<D - 4>();
+    const int sm = (int)((q - 1) & (D - 1)), s0 = (int)(q & (D - 1)), sp = (int)((q + 1) & (D - 1));
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
+      Um1[f] = sR[sm][f][tid];
+      Uq[f] = sR[s0][f][tid];
+      Up1[f] = sR[sp][f][tid];
       sU[f][oy][tx + 1] = Uq[f];
-      if (ringx) sU[f][oy][tx == 0 ? 0 : TX + 1] = Rx[f];
-      if (DIM == 3 && ringy) sU[f][ty == 0 ? 0 : SY - 1][tx + 1] = Ry[f];
+      if (ringx) sU[f][oy][tx == 0 ? 0 : TX + 1] = sH[s0][f][hx];
+      if (DIM == 3 && ringy) sU[f][ty == 0 ? 0 : SY - 1][tx + 1] = sH[s0][f][hy];
     }
-    if (q + 1 <= q1) {
-      if (ringx) ld(Uin, ncell, pidx(q + 1) + col_rx, Rx, NF);
-      if (ringy) ld(Uin, ncell, pidx(q + 1) + col_ry, Ry, NF);
-    }
+    issue(q + D - 2);    // reuses the slot of plane q-2 (read one barrier ago)
     __syncthreads();
 
     // b. slopes and predictor of plane q
@@ -297,17 +340,14 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
     // rotate the plane window
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      Um1[f] = Uq[f];
-      Uq[f] = Up1[f];
-      Up1[f] = Up2[f];
       Wm_prev[f] = uh[f] + (R)0.5 * d[AM][f];
       D_prev[f] = Dq[f];
       H_prev[f] = Hq[f];
     }
     yE_prev = yEh;
     yEv_prev = yEvh;
-    if (q + 3 <= q1 + 1) ld(Uin, ncell, pidx(q + 3) + col, Up2, NF);
   }
+  cp_async_wait<0>();
   reduce_and_finalize<R, NT>(ctl, kp, (double)smax, (double)akey, flags, true);
 }
 
@@ -327,8 +367,7 @@ template <typename R, int PP, int LIM, int SRC, int DIM, int PREC>
 static cudaError_t launch_nd(const KParams& kp, void* a, void* b, Ctl* ctl, const int64_t* n,
                             cudaStream_t st) {
   using G = Cfg<DIM, PREC>;
-  constexpr int NF = DIM + 3, SY = DIM == 3 ? G::TY + 2 : 1;
-  constexpr size_t smem = sizeof(R) * (NF * SY * (G::TX + 2) + 2 * (DIM - 1) * NF * G::TY * G::TX);
+  constexpr size_t smem = stepnd_smem<R, DIM, G::TX, G::TY>();
   auto fn = stepnd_kernel<R, PP, LIM, SRC, DIM, G::TX, G::TY, G::MINB>;
   if (!n) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int64_t nx = n[0], ny = n[1], nz = DIM == 3 ? n[2] : 1;
