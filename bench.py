@@ -34,6 +34,12 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s"
 L2_FLUSH_BYTES = 256 << 20
 
+# DRAM bytes (read + write) of one launch of the 1D FP32 step kernel at N = 2^22,
+# from one ncu capture of the current kernel (74.4 MB read + 16.9 MB written
+# during the launch; the remaining writes are still dirty in L2 when it ends).
+# Only valid for that workload and precision; other lines report null.
+TRAFFIC_1D_FP32_N22 = 91.3e6
+
 
 def workload(n_cells: int, gamma: float, Ck: float, S: float):
     from paper_1805_03442_gb300 import inputs
@@ -304,7 +310,9 @@ def run_ours(args):
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
                      "peak_src": f"{pk['src']} hbm_gbs (burst copy)", "unit": "GB/s",
-                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                     "frac": achieved / pk["hbm_gbs"],
+                     "traffic": (TRAFFIC_1D_FP32_N22 if (args.workload == "1d" and ncell == 1 << 22
+                                                         and args.precision == "fp32") else None),
                      "alg_bytes_per_launch": alg_bytes},
         "e2e": {"value": ws * ncell * e2e_steps / e2e_t, "unit": METRIC,
                 "h2d_bytes_per_step": int(host_in.numel() * 8),
