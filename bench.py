@@ -414,6 +414,48 @@ def run_sweep(args):
     print(json.dumps(line), flush=True)
 
 
+def run_wc(args):
+    """The paper's colliding-shock test at its reference resolution: N = 10^5
+    cells between solid walls, run to t = 0.038 (time to solution and
+    cell-updates/s; the 3.2 MB state stays in L2 during the run)."""
+    import torch
+    from paper_1805_03442_gb300 import inputs, sv
+    from paper_1805_03442_gb300.build import build
+    build()
+    N = args.n if args.n != 1 << 22 else 100000
+    prec = {"fp32": sv.FP32, "fp64": sv.FP64, "fp32_p64": sv.FP32_P64}[args.precision]
+    P = sv.Params(precision=prec, tau0=math.inf, S=0.0)
+    x = inputs.cell_centres(N, 1.0)
+    p = np.where(x < 0.1, 1000.0, np.where(x <= 0.9, 0.01, 100.0))
+    U0 = inputs.prim_to_cons(1.4, np.ones(N), [np.zeros(N)], p, np.full(N, 0.3))
+    stream = torch.cuda.Stream()
+    s = sv.Solver(P, (N,), (1.0,), stream=stream, bc=(sv.BC_REFLECT, sv.BC_REFLECT))
+    s.write_state(U0)
+    s.run_to(0.004)                    # warm-up (graph capture, clocks)
+    s.write_state(U0)
+    torch.cuda.synchronize()
+    with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t0 = time.perf_counter()
+        rc, steps = s.run_to(0.038)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    gpu_s = e0.elapsed_time(e1) * 1e-3
+    s.close()
+    line = {"metric": "cell-updates/s", "value": N * steps / wall, "unit": "cell-updates/s",
+            "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": 1e3 * wall / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp64": "f64", "fp32_p64": "f32"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": f"colliding shock waves, N={N} cells, solid walls, t_end 0.038",
+                       "cells": N, "l2": "not flushed: whole run timed (3.2 MB state)"},
+            "time_to_solution_s": wall, "gpu_event_s": gpu_s, "gpu_launches": steps,
+            "clocks": getattr(clk, "result", None)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -422,7 +464,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_p64"])
     ap.add_argument("--n", type=int, default=1 << 22, help="cells of the 1d workload")
-    ap.add_argument("--workload", default="1d", choices=sorted(WORKLOADS) + ["sweep"])
+    ap.add_argument("--workload", default="1d", choices=sorted(WORKLOADS) + ["sweep", "wc"])
     ap.add_argument("--side", type=int, default=0,
                     help="cells per axis of the 2d / 3d workloads (default 8192 / 512)")
     ap.add_argument("--runs", type=int, default=4096, help="runs of the sweep workload")
@@ -434,6 +476,8 @@ def main():
         run_reference(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "wc":
+        run_wc(args)
     else:
         run_ours(args)
 

@@ -22,8 +22,10 @@
  *   rho, rho*v_x [, rho*v_y [, rho*v_z]], E, E_nu.
  * Host buffers are always double, field-major structure-of-arrays:
  *   buf[f * ncell + idx], idx = i + n[0] * (j + n[1] * k), x fastest.
- * Periodic boundaries in every axis.  All axes share one cell size
- * h = L[0] / n[0] (the equal-step grid of Sec. 2.3).
+ * Periodic boundaries in every axis, except that a 1D grid may have solid
+ * walls or free outflow at either end (two ghost cells per side, as needed
+ * by the five-point stencil).  All axes share one cell size h = L[0] / n[0]
+ * (the equal-step grid of Sec. 2.3).
  *
  * Errors.  Every call returns an int status, 0 on success, never throws.
  * Ownership.  Host buffers belong to the caller.  Device memory belongs to
@@ -82,10 +84,17 @@ typedef struct {
   int precision;                /* SV_FP32, SV_FP64, SV_FP32_P64 */
 } sv_params;
 
+/* ---- boundary conditions (1D grids; 2D and 3D grids are periodic) */
+#define SV_BC_PERIODIC 0
+#define SV_BC_REFLECT  1   /* solid wall: mirrored ghost cells with the velocity reversed */
+#define SV_BC_OUTFLOW  2   /* zero-gradient ghost cells (free outflow) */
+
 typedef struct {
   int dim;                      /* 1, 2 or 3 */
   int64_t n[3];                 /* cells per axis (unused axes ignored) */
   double L[3];                  /* domain length per axis; L[a]/n[a] must agree */
+  int bc[2];                    /* 1D: SV_BC_* at x = 0 and at x = L[0]; must be
+                                   SV_BC_PERIODIC (0) when dim > 1 */
 } sv_grid;
 
 typedef struct sv_solver sv_solver;

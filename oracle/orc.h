@@ -68,6 +68,19 @@ double orc_dt(const orc_params* P, int dim, const long* n, double h, const doubl
 int orc_run(const orc_params* P, int dim, const long* n, double h, double* U,
             double t0, double t_end, long max_steps, double* t_out, long* steps_out);
 
+/* 1D boundary conditions (per side). */
+#define ORC_BC_PERIODIC 0
+#define ORC_BC_REFLECT  1   /* solid wall: mirrored ghost cells, velocity reversed */
+#define ORC_BC_OUTFLOW  2   /* zero-gradient ghost cells */
+
+/* One 1D step (and a run to t_end) with the boundary conditions bc_lo at
+   x = 0 and bc_hi at x = L, on two ghost cells per side.  N >= 2.
+   Returns as orc_step / orc_run, and -3 for N < 2. */
+int orc_step_bc1(const orc_params* P, long N, double h, double dt, int bc_lo, int bc_hi,
+                 const double* U, double* Unew);
+int orc_run_bc1(const orc_params* P, long N, double h, int bc_lo, int bc_hi, double* U,
+                double t0, double t_end, long max_steps, double* t_out, long* steps_out);
+
 /* Number of OpenMP threads the array loops use (1 without OpenMP). */
 int orc_threads(void);
 

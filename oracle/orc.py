@@ -24,6 +24,7 @@ _SO = os.path.join(_BUILD, "liborc.so")
 _SRC = os.path.join(_HERE, "orc_muscl.c")
 
 MINMOD, VANLEER, MC = 0, 1, 2
+PERIODIC, REFLECT, OUTFLOW = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -105,6 +106,10 @@ def lib():
         L.orc_run.argtypes = [pp, ctypes.c_int, lp, ctypes.c_double, dp, ctypes.c_double,
                               ctypes.c_double, ctypes.c_long, dp, lp]
         L.orc_threads.restype = ctypes.c_int
+        L.orc_step_bc1.argtypes = [pp, ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                   ctypes.c_int, dp, dp]
+        L.orc_run_bc1.argtypes = [pp, ctypes.c_long, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                  dp, ctypes.c_double, ctypes.c_double, ctypes.c_long, dp, lp]
         _lib = L
     return _lib
 
@@ -199,3 +204,21 @@ def run(P: Params, U: np.ndarray, n, h: float, t_end: float, t0: float = 0.0,
 
 def threads() -> int:
     return int(lib().orc_threads())
+
+
+def step_bc1(P: Params, U: np.ndarray, N: int, h: float, dt: float, bc_lo: int, bc_hi: int):
+    """One 1D step with boundary conditions (PERIODIC / REFLECT / OUTFLOW per side)."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    out = np.empty_like(U)
+    rc = lib().orc_step_bc1(ctypes.byref(P.c()), int(N), h, dt, bc_lo, bc_hi, _dp(U), _dp(out))
+    return out, rc
+
+
+def run_bc1(P: Params, U: np.ndarray, N: int, h: float, t_end: float, bc_lo: int, bc_hi: int,
+            t0: float = 0.0, max_steps: int = 1 << 40):
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    t = ctypes.c_double()
+    k = ctypes.c_long()
+    rc = lib().orc_run_bc1(ctypes.byref(P.c()), int(N), h, bc_lo, bc_hi, _dp(U), t0, t_end,
+                           max_steps, ctypes.byref(t), ctypes.byref(k))
+    return U, t.value, k.value, rc

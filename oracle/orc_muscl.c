@@ -323,3 +323,95 @@ int orc_run(const orc_params* P, int dim, const long* n, double h, double* U,
   *steps_out = k;
   return rc;
 }
+
+/* ------------------------------------------------------------ 1D boundaries */
+
+/* One 1D step with boundary conditions at x = 0 (bc_lo) and x = L (bc_hi):
+   ORC_BC_PERIODIC, ORC_BC_REFLECT (solid wall: mirrored ghost cells with the
+   velocity reversed) or ORC_BC_OUTFLOW (zero-gradient ghost cells).  The grid
+   is extended by two ghost cells per side filled by those rules; the predictor
+   runs on cells -1..N, the faces -1/2..N-1/2, the update on 0..N-1, with the
+   same functions as the periodic step. */
+static void fill_ghost(const grid_t* g, const double* U, int bc, long src_near, long src_far,
+                       double* near, double* far) {
+  for (int f = 0; f < g->nf; ++f) {
+    if (bc == ORC_BC_OUTFLOW) {
+      near[f] = U[(long)f * g->ncell + src_near];
+      far[f] = near[f];
+    } else {
+      near[f] = U[(long)f * g->ncell + src_near];
+      far[f] = U[(long)f * g->ncell + src_far];
+    }
+  }
+  if (bc == ORC_BC_REFLECT) {
+    near[1] = -near[1];
+    far[1] = -far[1];
+  }
+}
+
+int orc_step_bc1(const orc_params* P, long N, double h, double dt, int bc_lo, int bc_hi,
+                 const double* U, double* Unew) {
+  if (N < 2) return -3;
+  const long n1 = N;
+  grid_t g = make_grid(1, &n1);
+  const long ne = N + 4;
+  grid_t ge = make_grid(1, &ne);
+  const int nf = 4;
+  double* Ue = malloc(sizeof(double) * (size_t)nf * (size_t)ne);
+  double (*dU)[3][NF_MAX] = malloc(sizeof(double[3][NF_MAX]) * (size_t)ne);
+  double (*uh)[NF_MAX] = malloc(sizeof(double[NF_MAX]) * (size_t)ne);
+  double (*Fface)[NF_MAX] = malloc(sizeof(double[NF_MAX]) * (size_t)ne);
+  if (!Ue || !dU || !uh || !Fface) { free(Ue); free(dU); free(uh); free(Fface); return -2; }
+  for (int f = 0; f < nf; ++f)
+    for (long j = 0; j < N; ++j) Ue[(long)f * ne + j + 2] = U[(long)f * N + j];
+  double gn[NF_MAX], gf[NF_MAX];
+  /* left ghosts: extended index 1 (cell -1) and 0 (cell -2) */
+  if (bc_lo == ORC_BC_PERIODIC) fill_ghost(&g, U, bc_lo, N - 1, N - 2, gn, gf);
+  else fill_ghost(&g, U, bc_lo, 0, 1, gn, gf);
+  for (int f = 0; f < nf; ++f) { Ue[(long)f * ne + 1] = gn[f]; Ue[(long)f * ne + 0] = gf[f]; }
+  /* right ghosts: extended index N+2 (cell N) and N+3 (cell N+1) */
+  if (bc_hi == ORC_BC_PERIODIC) fill_ghost(&g, U, bc_hi, 0, 1, gn, gf);
+  else fill_ghost(&g, U, bc_hi, N - 1, N - 2, gn, gf);
+  for (int f = 0; f < nf; ++f) { Ue[(long)f * ne + N + 2] = gn[f]; Ue[(long)f * ne + N + 3] = gf[f]; }
+
+  for (long q = 1; q <= N + 2; ++q) predict(P, &ge, h, dt, Ue, q, dU[q], uh[q]);
+  for (long q = 1; q <= N + 1; ++q)
+    face_flux(P, &ge, Ue, 0, q, dU[q], uh[q], q + 1, dU[q + 1], uh[q + 1], Fface[q]);
+  int bad = 0;
+  for (long q = 2; q <= N + 1; ++q) {
+    double u[NF_MAX], out[NF_MAX], Fp[3][NF_MAX], Fm[3][NF_MAX];
+    gather(&ge, Ue, q, u);
+    memcpy(Fp[0], Fface[q], sizeof(double) * NF_MAX);
+    memcpy(Fm[0], Fface[q - 1], sizeof(double) * NF_MAX);
+    correct(P, &ge, h, dt, u, uh[q], Fp, Fm, out);
+    for (int f = 0; f < nf; ++f) Unew[(long)f * N + q - 2] = out[f];
+    if (!orc_physical(P, 1, out)) bad = 1;
+  }
+  free(Ue); free(dU); free(uh); free(Fface);
+  return bad ? -1 : 0;
+}
+
+int orc_run_bc1(const orc_params* P, long N, double h, int bc_lo, int bc_hi, double* U,
+                double t0, double t_end, long max_steps, double* t_out, long* steps_out) {
+  size_t bytes = sizeof(double) * 4 * (size_t)N;
+  double* tmp = malloc(bytes);
+  if (!tmp) return -2;
+  const long n1 = N;
+  double t = t0;
+  long k = 0;
+  int rc = 0;
+  while (t < t_end && k < max_steps) {
+    double dt = orc_dt(P, 1, &n1, h, U);
+    int last = 0;
+    if (dt >= t_end - t) { dt = t_end - t; last = 1; }
+    rc = orc_step_bc1(P, N, h, dt, bc_lo, bc_hi, U, tmp);
+    memcpy(U, tmp, bytes);
+    t = last ? t_end : t + dt;
+    ++k;
+    if (rc != 0) break;
+  }
+  free(tmp);
+  *t_out = t;
+  *steps_out = k;
+  return rc;
+}

@@ -64,6 +64,12 @@ int check_inputs(const sv_params* p, const sv_grid* g) {
     return SV_EINVAL;
   if (p->limiter < SV_MINMOD || p->limiter > SV_MC) return SV_EINVAL;
   if (p->precision < SV_FP32 || p->precision > SV_FP32_P64) return SV_EINVAL;
+  for (int side = 0; side < 2; ++side) {
+    if (g->bc[side] < SV_BC_PERIODIC || g->bc[side] > SV_BC_OUTFLOW) return SV_EINVAL;
+    if (g->dim > 1 && g->bc[side] != SV_BC_PERIODIC) return SV_EINVAL;
+  }
+  if (g->dim == 1 && (g->bc[0] != SV_BC_PERIODIC || g->bc[1] != SV_BC_PERIODIC) && g->n[0] < 2)
+    return SV_EINVAL;
   return SV_OK;
 }
 
@@ -195,6 +201,8 @@ int sv_init(const sv_params* p, const sv_grid* g, void* cuda_stream, void* devic
   k.cfl = p->cfl;
   k.c_tau = p->c_tau;
   k.limiter = p->limiter;
+  k.bc_lo = g->dim == 1 ? g->bc[0] : SV_BC_PERIODIC;
+  k.bc_hi = g->dim == 1 ? g->bc[1] : SV_BC_PERIODIC;
   kparams_finish(k);
 
   if (device_mem) {

@@ -31,6 +31,7 @@ struct KParams {
   int limiter;   // 0 minmod, 1 van Leer, 2 MC
   int frozen;    // 1: no source at all (Q = I = 0, 1/tau = 0)
   int qi_zero;   // 1: all Q and I exponents are zero (Q = I = Q0)
+  int bc_lo, bc_hi;   // 1D boundary conditions at x = 0 / x = L (BC_*)
   int pad;
   // float copies for the float kernels (kparams_finish): the twelve values
   // above, then log2(1/tau0) (0 in the frozen limit), -tau_rho, -tau_T
@@ -65,6 +66,9 @@ struct Ctl {
   uint64_t tau_key;    // order-preserving key of the tau bound (see finalize)
   double pad[4];
 };
+
+// 1D boundary conditions (the values of SV_BC_* in sv.h).
+constexpr int BC_PERIODIC = 0, BC_REFLECT = 1, BC_OUTFLOW = 2;
 
 constexpr uint32_t FLAG_NONPHYS = 1u;
 constexpr uint32_t FLAG_DT = 2u;
@@ -111,23 +115,25 @@ template <typename R> struct P;
 template <> struct P<double> {
   double gamma, g1, Ck, Q0, inv_tau0, tau0;
   double tau_rho, tau_T, Q_rho, Q_T, I_rho, I_T;
-  int limiter, frozen, qi_zero;
+  int limiter, frozen, qi_zero, bc_lo, bc_hi;
   __device__ __forceinline__ explicit P(const KParams& k)
       : gamma(k.gamma), g1(k.g1), Ck(k.Ck), Q0(k.Q0), inv_tau0(k.inv_tau0), tau0(k.tau0),
         tau_rho(k.tau_rho), tau_T(k.tau_T), Q_rho(k.Q_rho), Q_T(k.Q_T), I_rho(k.I_rho),
-        I_T(k.I_T), limiter(k.limiter), frozen(k.frozen), qi_zero(k.qi_zero) {}
+        I_T(k.I_T), limiter(k.limiter), frozen(k.frozen), qi_zero(k.qi_zero), bc_lo(k.bc_lo),
+        bc_hi(k.bc_hi) {}
 };
 
 template <> struct P<float> {
   float gamma, g1, Ck, Q0, inv_tau0, tau0;
   float tau_rho, tau_T, Q_rho, Q_T, I_rho, I_T;
   float l2_inv_tau0, ntau_rho, ntau_T;   // log2(1/tau0), -tau_rho, -tau_T
-  int limiter, frozen, qi_zero;
+  int limiter, frozen, qi_zero, bc_lo, bc_hi;
   __device__ __forceinline__ explicit P(const KParams& k)
       : gamma(k.f[0]), g1(k.f[1]), Ck(k.f[2]), Q0(k.f[3]), inv_tau0(k.f[5]), tau0(k.f[4]),
         tau_rho(k.f[6]), tau_T(k.f[7]), Q_rho(k.f[8]), Q_T(k.f[9]), I_rho(k.f[10]),
         I_T(k.f[11]), l2_inv_tau0(k.f[12]), ntau_rho(k.f[13]), ntau_T(k.f[14]),
-        limiter(k.limiter), frozen(k.frozen), qi_zero(k.qi_zero) {}
+        limiter(k.limiter), frozen(k.frozen), qi_zero(k.qi_zero), bc_lo(k.bc_lo),
+        bc_hi(k.bc_hi) {}
 };
 
 // The dt-derived factors of the next step, read by the step kernels.

@@ -141,6 +141,25 @@ __device__ __forceinline__ void hll(const P<R>& k, const R (&l)[4], const R (&r)
   for (int f = 0; f < 4; ++f) F[f] = wl * FL[f] + wr * FR[f] + wd * (Rr[f] - L[f]);
 }
 
+// Cell whose state fills position j of a 1D grid of N cells: periodic wrap,
+// wall mirror (ghost -1-g holds cell g with the velocity reversed: *flip) or
+// outflow copy of the boundary cell.  Ghosts deeper than the two the stencil
+// uses are clamped into the grid; their values never reach an updated cell.
+__device__ __forceinline__ int bc_index(int j, int N, int bc_lo, int bc_hi, bool& flip) {
+  flip = false;
+  if (j >= 0 && j < N) return j;
+  const int bc = j < 0 ? bc_lo : bc_hi;
+  if (bc == BC_PERIODIC) return (int)wrap(j, N);
+  int m;
+  if (bc == BC_REFLECT) {
+    flip = true;
+    m = j < 0 ? -1 - j : 2 * N - 1 - j;
+  } else {
+    m = j < 0 ? 0 : N - 1;
+  }
+  return m < 0 ? 0 : (m >= N ? N - 1 : m);
+}
+
 template <typename R>
 __device__ __forceinline__ R shfl(R v, int src) {
   return __shfl_sync(0xffffffffu, v, src);
@@ -184,7 +203,9 @@ __device__ __forceinline__ void step1d_warp(const P<R>& k, const R* __restrict__
 #pragma unroll
         for (int f = 0; f < 4; ++f) cp_async<2 * sizeof(R)>(dst + f * RN, Uin + f * stride + j);
       } else {
-        const int i0 = (int)wrap(j, N), i1 = (int)wrap(j + 1, N);
+        bool f0, f1;
+        const int i0 = bc_index(j, N, k.bc_lo, k.bc_hi, f0);
+        const int i1 = bc_index(j + 1, N, k.bc_lo, k.bc_hi, f1);
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
           cp_async<sizeof(R)>(dst + f * RN, Uin + f * stride + i0);
@@ -194,7 +215,24 @@ __device__ __forceinline__ void step1d_warp(const P<R>& k, const R* __restrict__
     }
     cp_async_commit();
   };
+  // wall ghosts: reverse the velocity of the landed copies of chunk c (each
+  // lane its own pair; a __syncwarp must follow)
+  const bool walls = !nowrap && (k.bc_lo == BC_REFLECT || k.bc_hi == BC_REFLECT);
+  auto flip_ghosts = [&](int c) {
+    const int j = c * 64 + 2 * lane;
+    R* m = ring + RN + (c & (RS - 1)) * 64 + 2 * lane;
+    bool f0, f1;
+    bc_index(j, N, k.bc_lo, k.bc_hi, f0);
+    bc_index(j + 1, N, k.bc_lo, k.bc_hi, f1);
+    if (f0) m[0] = -m[0];
+    if (f1) m[1] = -m[1];
+  };
   for (int c = c0 - 2; c <= c0 + RS - 4; ++c) issue(c);   // RS - 1 chunks ahead
+  if (walls) {
+    cp_async_wait<RS - 3>();     // chunks c0-2 and c0-1 have landed
+    flip_ghosts(c0 - 2);
+    flip_ghosts(c0 - 1);
+  }
 
   R Wp1_prev[4] = {0, 0, 0, 0}, Fa_prev[4] = {0, 0, 0, 0}, Fb_prev[4] = {0, 0, 0, 0};
   R y0E_prev = 0, y0Ev_prev = 0, y1E_prev = 0, y1Ev_prev = 0;
@@ -202,6 +240,7 @@ __device__ __forceinline__ void step1d_warp(const P<R>& k, const R* __restrict__
   // chunk index kk runs from c0-1 (warm-up) to c1 (trailing faces)
   for (int kk = c0 - 1; kk <= c1; ++kk) {
     cp_async_wait<RS - 4>();     // chunks up to kk+1 have landed for this lane ...
+    if (walls) flip_ghosts(kk + 1);
     __syncwarp();                // ... and for the warp; chunk kk-2 is no longer read
     issue(kk + RS - 2);          // reuses the slot of chunk kk-2
     const int pos = (kk & (RS - 1)) * 64 + 2 * lane;

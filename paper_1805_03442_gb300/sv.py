@@ -23,6 +23,7 @@ NOALLOC_MAX_CELLS = (1 << 29) - 1
 FLAG_NONPHYS, FLAG_DT, FLAG_MAXSTEPS = 1, 2, 4
 MINMOD, VANLEER, MC = 0, 1, 2
 FP32, FP64, FP32_P64 = 0, 1, 2
+BC_PERIODIC, BC_REFLECT, BC_OUTFLOW = 0, 1, 2
 
 EXPORTS = ("sv_required_bytes", "sv_init", "sv_write_state", "sv_read_state", "sv_dt_cfl",
            "sv_step", "sv_run_to", "sv_time", "sv_conservation", "sv_status",
@@ -51,7 +52,8 @@ class _Run(ctypes.Structure):
 
 
 class _Grid(ctypes.Structure):
-    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("L", ctypes.c_double * 3)]
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("L", ctypes.c_double * 3),
+                ("bc", ctypes.c_int * 2)]
 
 
 @dataclass
@@ -143,7 +145,7 @@ def _dp(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def grid(n, L=None) -> _Grid:
+def grid(n, L=None, bc=(BC_PERIODIC, BC_PERIODIC)) -> _Grid:
     n = tuple(int(x) for x in (n if hasattr(n, "__len__") else (n,)))
     if L is None:
         L = tuple(float(x) / n[0] for x in n)          # h = 1 / n[0]
@@ -153,6 +155,7 @@ def grid(n, L=None) -> _Grid:
     for a in range(3):
         g.n[a] = n[a] if a < len(n) else 1
         g.L[a] = L[a] if a < len(L) else 1.0
+    g.bc[0], g.bc[1] = int(bc[0]), int(bc[1])
     return g
 
 
@@ -179,14 +182,16 @@ class Solver:
     n: cells per axis (tuple of 1-3 ints), L: lengths per axis (equal cell size).
     memory="torch" backs the solver's device block by a torch uint8 tensor;
     memory="library" lets libsv allocate it.  stream: a torch.cuda.Stream, or
-    None for torch's current stream."""
+    None for torch's current stream.  bc: boundary conditions (BC_*) at x = 0
+    and x = L of a 1D grid."""
 
-    def __init__(self, params: Params, n, L=None, stream=None, memory: str = "torch"):
+    def __init__(self, params: Params, n, L=None, stream=None, memory: str = "torch",
+                 bc=(BC_PERIODIC, BC_PERIODIC)):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the solver has no CPU path")
         self.params = params
-        self.g = grid(n, L)
+        self.g = grid(n, L, bc)
         self.dim = self.g.dim
         self.n = tuple(self.g.n[a] for a in range(self.dim))
         self.nf = self.dim + 3

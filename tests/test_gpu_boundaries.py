@@ -1,0 +1,106 @@
+"""1D walls and outflow on the GPU (through the C ABI) against the oracle, and
+the paper's colliding-shock test.  Error measure as in the other parity tests
+(max |gpu - oracle| / max(|field|, 1) per field)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from gpu_util import need_gpu, oracle_params, rel_linf
+from oracle import orc as O
+from paper_1805_03442_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "woodward_colella.json")
+
+
+@pytest.fixture(scope="module")
+def sv():
+    return need_gpu()
+
+
+def wc_state(N):
+    g = json.load(open(GOLDEN))["initial"]
+    x = inputs.cell_centres(N, 1.0)
+    p = np.where(x < g["x_left"], g["p_left"], np.where(x <= g["x_right"], g["p_middle"], g["p_right"]))
+    return inputs.prim_to_cons(g["gamma"], np.full(N, g["rho"]), [np.full(N, g["u"])], p,
+                               np.full(N, 0.3))
+
+
+BCS = [(1, 1), (2, 2), (1, 2), (2, 1), (0, 1)]
+
+
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("N", [7, 130, 1000, 4099])
+def test_fp64_matches_oracle(sv, bc, N):
+    P = sv.Params(precision=sv.FP64, tau0=0.3)
+    Po = oracle_params(P)
+    h = 1.0 / N
+    U0 = inputs.random_states(1, N, seed=N + 3, smooth=True)
+    with sv.Solver(P, (N,), (1.0,), bc=bc) as s:
+        s.write_state(U0)
+        s.step(3)
+        U, t = s.read_state()
+        assert s.status() == 0
+    ref = U0
+    for _ in range(3):
+        ref, rc = O.step_bc1(Po, ref, N, h, O.dt_cfl(Po, ref, N, h), bc[0], bc[1])
+        assert rc == 0
+    assert rel_linf(U, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("bc", [(1, 1), (2, 2)])
+def test_fp32_one_step(sv, bc):
+    N = 3001
+    P = sv.Params(precision=sv.FP32, tau0=0.3)
+    Po = oracle_params(P)
+    U0 = inputs.random_states(1, N, seed=5, smooth=True).astype(np.float32).astype(np.float64)
+    with sv.Solver(P, (N,), (1.0,), bc=bc) as s:
+        s.write_state(U0)
+        dt = s.dt()
+        s.step(1)
+        U, _ = s.read_state()
+    ref, _ = O.step_bc1(Po, U0, N, 1.0 / N, dt, bc[0], bc[1])
+    assert rel_linf(U, ref) <= 2e-6
+
+
+def test_walls_conserve_mass_on_gpu(sv):
+    N = 5000
+    P = sv.Params(precision=sv.FP64, tau0=math.inf, S=0.0)
+    with sv.Solver(P, (N,), (1.0,), bc=(1, 1)) as s:
+        s.write_state(wc_state(N))
+        c0 = s.conservation()
+        s.step(300)
+        c1 = s.conservation()
+        assert s.status() == 0
+    assert abs(c1[0] - c0[0]) <= 1e-13 * c0[0]
+
+
+@pytest.mark.parametrize("prec", ["FP64", "FP32"])
+def test_colliding_shocks(sv, prec):
+    """The paper's test: collision peak at x = 0.7 at t1 = 0.028 (N = 1000); the
+    FP64 run follows the oracle to t = 0.038, the FP32 run stays within 1e-3 of
+    it in density L1."""
+    g = json.load(open(GOLDEN))
+    N = g["grid_cells_fig1"]
+    P = sv.Params(precision=getattr(sv, prec), tau0=math.inf, S=0.0)
+    Po = oracle_params(P)
+    x = inputs.cell_centres(N, 1.0)
+    with sv.Solver(P, (N,), (1.0,), bc=(1, 1)) as s:
+        s.write_state(wc_state(N))
+        s.run_to(g["collision_time"])
+        U1, t1 = s.read_state()
+        s.run_to(g["comparison_time"])
+        U2, t2 = s.read_state()
+    assert t1 == g["collision_time"] and t2 == g["comparison_time"]
+    p = 0.4 * (U1[2] - 0.5 * U1[1] ** 2 / U1[0] - U1[3])
+    assert abs(x[np.argmax(p)] - g["collision_position"]) <= 0.02
+    ref1, _, _, _ = O.run_bc1(Po, wc_state(N), N, 1.0 / N, g["collision_time"], 1, 1)
+    ref2, _, _, _ = O.run_bc1(Po, ref1, N, 1.0 / N, g["comparison_time"], 1, 1,
+                              t0=g["collision_time"])
+    if prec == "FP64":
+        assert rel_linf(U2, ref2) <= 1e-9
+    else:
+        assert np.mean(np.abs(U2[0] - ref2[0])) <= 1e-3 * np.mean(ref2[0])
