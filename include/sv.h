@@ -88,13 +88,15 @@ typedef struct {
 #define SV_BC_PERIODIC 0
 #define SV_BC_REFLECT  1   /* solid wall: mirrored ghost cells with the velocity reversed */
 #define SV_BC_OUTFLOW  2   /* zero-gradient ghost cells (free outflow) */
+#define SV_BC_DRIVEN   3   /* x = 0 only: ghost cells hold a prescribed wave (sv_set_drive),
+                              the forced source of the paper's Sec. 3 runs */
 
 typedef struct {
   int dim;                      /* 1, 2 or 3 */
   int64_t n[3];                 /* cells per axis (unused axes ignored) */
   double L[3];                  /* domain length per axis; L[a]/n[a] must agree */
-  int bc[2];                    /* 1D: SV_BC_* at x = 0 and at x = L[0]; must be
-                                   SV_BC_PERIODIC (0) when dim > 1 */
+  int bc[2];                    /* 1D: SV_BC_* at x = 0 and at x = L[0] (SV_BC_DRIVEN
+                                   only at x = 0); SV_BC_PERIODIC (0) when dim > 1 */
 } sv_grid;
 
 typedef struct sv_solver sv_solver;
@@ -247,6 +249,20 @@ void sv_batch_free(sv_batch* b);
    array and race.  n beyond SV_NOALLOC_MAX_CELLS returns SV_ESIZE. */
 int sv_step1d_noalloc(const sv_params* p, int64_t n, double L, const void* U_in, void* U_out,
                       double* dt_used, uint32_t* flags, void* cuda_stream);
+
+/* Prescribed wave of an SV_BC_DRIVEN boundary: the ghost cell centred at x < 0
+   holds U(x, t) = base + Re(amp e^{i (k x - omega t)}), k = k_re + i k_im,
+   evaluated at the start time of each step (conserved variables rho, rho v,
+   E, E_nu). */
+typedef struct {
+  double omega, k_re, k_im;
+  double base[4], amp_re[4], amp_im[4];
+} sv_drive;
+
+/* Set the wave of a 1D solver whose grid has bc[0] = SV_BC_DRIVEN (until it
+   is set the ghost cells hold the uniform equilibrium).  SV_EINVAL for other
+   grids. */
+int sv_set_drive(sv_solver* s, const sv_drive* d);
 
 /* Human-readable name of a status code. */
 const char* sv_strerror(int code);

@@ -107,3 +107,17 @@ def equilibrium(P, dim: int = 1) -> np.ndarray:
     u[1 + dim] = 1.0 / (P.gamma - 1.0) + ev0
     u[2 + dim] = ev0
     return u
+
+
+def spatial_root(P, omega: float) -> complex:
+    """Spatial problem (real omega, Sec. 3 forced source): eq. 8 is a quadratic
+    in k: k^2 = omega^2 [delta (A - i delta) + i a (1 - i delta)]
+                / (c0^2 [delta (B - i delta) + i b (1 - i delta)]), delta = omega tau0.
+    Returns the root with Re k > 0 (the wave travelling away from the source);
+    Im k < 0 means amplification with distance."""
+    c = constants(P)
+    d = omega * P.tau0
+    lhs = omega * omega * (d * (c["A"] - 1j * d) + 1j * c["a"] * (1 - 1j * d))
+    rhs = c["c0sq"] * (d * (c["B"] - 1j * d) + 1j * c["b"] * (1 - 1j * d))
+    k = np.sqrt(lhs / rhs)
+    return complex(k if k.real > 0 else -k)

@@ -72,6 +72,22 @@ int orc_run(const orc_params* P, int dim, const long* n, double h, double* U,
 #define ORC_BC_PERIODIC 0
 #define ORC_BC_REFLECT  1   /* solid wall: mirrored ghost cells, velocity reversed */
 #define ORC_BC_OUTFLOW  2   /* zero-gradient ghost cells */
+#define ORC_BC_DRIVEN   3   /* x = 0 only: ghost cells hold a prescribed wave */
+
+/* Prescribed wave of the driven boundary: a ghost cell at x (< 0) holds
+   U(x, t) = base + Re(amp e^{i (k x - omega t)}), k = k_re + i k_im. */
+typedef struct {
+  double omega, k_re, k_im;
+  double base[4], amp_re[4], amp_im[4];
+} orc_drive;
+
+/* As orc_step_bc1 / orc_run_bc1 with a driven boundary at x = 0 (bc_lo =
+   ORC_BC_DRIVEN) evaluated at the step's start time t. */
+int orc_step_bc1d(const orc_params* P, long N, double h, double dt, int bc_lo, int bc_hi,
+                  const orc_drive* drive, double t, const double* U, double* Unew);
+int orc_run_bc1d(const orc_params* P, long N, double h, int bc_lo, int bc_hi,
+                 const orc_drive* drive, double* U, double t0, double t_end, long max_steps,
+                 double* t_out, long* steps_out);
 
 /* One 1D step (and a run to t_end) with the boundary conditions bc_lo at
    x = 0 and bc_hi at x = L, on two ghost cells per side.  N >= 2.

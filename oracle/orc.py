@@ -24,7 +24,24 @@ _SO = os.path.join(_BUILD, "liborc.so")
 _SRC = os.path.join(_HERE, "orc_muscl.c")
 
 MINMOD, VANLEER, MC = 0, 1, 2
-PERIODIC, REFLECT, OUTFLOW = 0, 1, 2
+PERIODIC, REFLECT, OUTFLOW, DRIVEN = 0, 1, 2, 3
+
+
+class _CDrive(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_double), ("k_re", ctypes.c_double), ("k_im", ctypes.c_double),
+                ("base", ctypes.c_double * 4), ("amp_re", ctypes.c_double * 4),
+                ("amp_im", ctypes.c_double * 4)]
+
+
+def drive(omega: float, k: complex, base, amp) -> _CDrive:
+    """Prescribed boundary wave U = base + Re(amp e^{i(k x - omega t)})."""
+    d = _CDrive()
+    d.omega, d.k_re, d.k_im = float(omega), float(complex(k).real), float(complex(k).imag)
+    for f in range(4):
+        d.base[f] = float(base[f])
+        d.amp_re[f] = float(complex(amp[f]).real)
+        d.amp_im[f] = float(complex(amp[f]).imag)
+    return d
 
 
 def build(force: bool = False) -> str:
@@ -110,6 +127,9 @@ def lib():
                                    ctypes.c_int, dp, dp]
         L.orc_run_bc1.argtypes = [pp, ctypes.c_long, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                   dp, ctypes.c_double, ctypes.c_double, ctypes.c_long, dp, lp]
+        L.orc_run_bc1d.argtypes = [pp, ctypes.c_long, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(_CDrive), dp, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_long, dp, lp]
         _lib = L
     return _lib
 
@@ -221,4 +241,15 @@ def run_bc1(P: Params, U: np.ndarray, N: int, h: float, t_end: float, bc_lo: int
     k = ctypes.c_long()
     rc = lib().orc_run_bc1(ctypes.byref(P.c()), int(N), h, bc_lo, bc_hi, _dp(U), t0, t_end,
                            max_steps, ctypes.byref(t), ctypes.byref(k))
+    return U, t.value, k.value, rc
+
+
+def run_driven(P: Params, U: np.ndarray, N: int, h: float, t_end: float, drv: _CDrive,
+               bc_hi: int = OUTFLOW, t0: float = 0.0, max_steps: int = 1 << 40):
+    """1D run with the driven boundary at x = 0 and bc_hi at x = L."""
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    t = ctypes.c_double()
+    k = ctypes.c_long()
+    rc = lib().orc_run_bc1d(ctypes.byref(P.c()), int(N), h, DRIVEN, bc_hi, ctypes.byref(drv),
+                            _dp(U), t0, t_end, max_steps, ctypes.byref(t), ctypes.byref(k))
     return U, t.value, k.value, rc

@@ -349,8 +349,23 @@ static void fill_ghost(const grid_t* g, const double* U, int bc, long src_near, 
   }
 }
 
+/* Ghost cell at position x of the driven boundary at time t. */
+static void drive_state(const orc_drive* d, double x, double t, double* u) {
+  const double env = exp(-d->k_im * x);
+  const double ph = d->k_re * x - d->omega * t;
+  const double c = cos(ph), s = sin(ph);
+  for (int f = 0; f < 4; ++f) u[f] = d->base[f] + env * (d->amp_re[f] * c - d->amp_im[f] * s);
+}
+
 int orc_step_bc1(const orc_params* P, long N, double h, double dt, int bc_lo, int bc_hi,
                  const double* U, double* Unew) {
+  return orc_step_bc1d(P, N, h, dt, bc_lo, bc_hi, NULL, 0.0, U, Unew);
+}
+
+int orc_step_bc1d(const orc_params* P, long N, double h, double dt, int bc_lo, int bc_hi,
+                  const orc_drive* drive, double t, const double* U, double* Unew) {
+  if (bc_lo == ORC_BC_DRIVEN && !drive) return -3;
+  if (bc_hi == ORC_BC_DRIVEN) return -3;
   if (N < 2) return -3;
   const long n1 = N;
   grid_t g = make_grid(1, &n1);
@@ -367,7 +382,10 @@ int orc_step_bc1(const orc_params* P, long N, double h, double dt, int bc_lo, in
   double gn[NF_MAX], gf[NF_MAX];
   /* left ghosts: extended index 1 (cell -1) and 0 (cell -2) */
   if (bc_lo == ORC_BC_PERIODIC) fill_ghost(&g, U, bc_lo, N - 1, N - 2, gn, gf);
-  else fill_ghost(&g, U, bc_lo, 0, 1, gn, gf);
+  else if (bc_lo == ORC_BC_DRIVEN) {
+    drive_state(drive, -0.5 * h, t, gn);   /* cell -1 centre */
+    drive_state(drive, -1.5 * h, t, gf);   /* cell -2 centre */
+  } else fill_ghost(&g, U, bc_lo, 0, 1, gn, gf);
   for (int f = 0; f < nf; ++f) { Ue[(long)f * ne + 1] = gn[f]; Ue[(long)f * ne + 0] = gf[f]; }
   /* right ghosts: extended index N+2 (cell N) and N+3 (cell N+1) */
   if (bc_hi == ORC_BC_PERIODIC) fill_ghost(&g, U, bc_hi, 0, 1, gn, gf);
@@ -393,6 +411,12 @@ int orc_step_bc1(const orc_params* P, long N, double h, double dt, int bc_lo, in
 
 int orc_run_bc1(const orc_params* P, long N, double h, int bc_lo, int bc_hi, double* U,
                 double t0, double t_end, long max_steps, double* t_out, long* steps_out) {
+  return orc_run_bc1d(P, N, h, bc_lo, bc_hi, NULL, U, t0, t_end, max_steps, t_out, steps_out);
+}
+
+int orc_run_bc1d(const orc_params* P, long N, double h, int bc_lo, int bc_hi,
+                 const orc_drive* drive, double* U, double t0, double t_end, long max_steps,
+                 double* t_out, long* steps_out) {
   size_t bytes = sizeof(double) * 4 * (size_t)N;
   double* tmp = malloc(bytes);
   if (!tmp) return -2;
@@ -404,7 +428,7 @@ int orc_run_bc1(const orc_params* P, long N, double h, int bc_lo, int bc_hi, dou
     double dt = orc_dt(P, 1, &n1, h, U);
     int last = 0;
     if (dt >= t_end - t) { dt = t_end - t; last = 1; }
-    rc = orc_step_bc1(P, N, h, dt, bc_lo, bc_hi, U, tmp);
+    rc = orc_step_bc1d(P, N, h, dt, bc_lo, bc_hi, drive, t, U, tmp);
     memcpy(U, tmp, bytes);
     t = last ? t_end : t + dt;
     ++k;

@@ -65,9 +65,10 @@ int check_inputs(const sv_params* p, const sv_grid* g) {
   if (p->limiter < SV_MINMOD || p->limiter > SV_MC) return SV_EINVAL;
   if (p->precision < SV_FP32 || p->precision > SV_FP32_P64) return SV_EINVAL;
   for (int side = 0; side < 2; ++side) {
-    if (g->bc[side] < SV_BC_PERIODIC || g->bc[side] > SV_BC_OUTFLOW) return SV_EINVAL;
+    if (g->bc[side] < SV_BC_PERIODIC || g->bc[side] > SV_BC_DRIVEN) return SV_EINVAL;
     if (g->dim > 1 && g->bc[side] != SV_BC_PERIODIC) return SV_EINVAL;
   }
+  if (g->bc[1] == SV_BC_DRIVEN) return SV_EINVAL;
   if (g->dim == 1 && (g->bc[0] != SV_BC_PERIODIC || g->bc[1] != SV_BC_PERIODIC) && g->n[0] < 2)
     return SV_EINVAL;
   return SV_OK;
@@ -203,6 +204,11 @@ int sv_init(const sv_params* p, const sv_grid* g, void* cuda_stream, void* devic
   k.limiter = p->limiter;
   k.bc_lo = g->dim == 1 ? g->bc[0] : SV_BC_PERIODIC;
   k.bc_hi = g->dim == 1 ? g->bc[1] : SV_BC_PERIODIC;
+  {   // a driven boundary holds the uniform equilibrium until sv_set_drive
+    const double ev0 = p->Ck + p->S;
+    const double base[4] = {1.0, 0.0, 1.0 / (p->gamma - 1.0) + ev0, ev0};
+    for (int f = 0; f < 4; ++f) k.drv_base[f] = base[f];
+  }
   kparams_finish(k);
 
   if (device_mem) {
@@ -321,6 +327,26 @@ int sv_run_to(sv_solver* s, double t_end, int64_t max_steps, int64_t* steps_take
   // clear the target so that later sv_step calls are not clamped
   SV_TRY(set_target_launch(s->ctl, INFINITY, s->h, s->stream));
   return status;
+}
+
+int sv_set_drive(sv_solver* s, const sv_drive* d) {
+  if (!s || !d || s->dim != 1 || s->kp.bc_lo != SV_BC_DRIVEN) return SV_EINVAL;
+  if (!isfinite(d->omega) || !isfinite(d->k_re) || !isfinite(d->k_im)) return SV_EINVAL;
+  s->kp.drv_omega = d->omega;
+  s->kp.drv_kre = d->k_re;
+  s->kp.drv_kim = d->k_im;
+  for (int f = 0; f < 4; ++f) {
+    s->kp.drv_base[f] = d->base[f];
+    s->kp.drv_are[f] = d->amp_re[f];
+    s->kp.drv_aim[f] = d->amp_im[f];
+  }
+  // the captured graph holds the old parameters: capture again on next use
+  if (s->graph) {
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return SV_ECUDA;
+    cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+  }
+  return SV_OK;
 }
 
 int sv_time(sv_solver* s, double* t, int64_t* steps) {

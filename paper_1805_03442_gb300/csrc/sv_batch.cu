@@ -185,13 +185,13 @@ batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns
       uint32_t flags = 0;
       if (src == 0)
         step1d_warp<R, PP, LIM, 0>(k, Uin, Uout, n, stride, c0, c1, lane, dt, dtdx, dt_2h, dt_2,
-                                   smax, akey, flags, ring);
+                                   smax, akey, flags, ring, kp, s_t);
       else if (src == 1)
         step1d_warp<R, PP, LIM, 1>(k, Uin, Uout, n, stride, c0, c1, lane, dt, dtdx, dt_2h, dt_2,
-                                   smax, akey, flags, ring);
+                                   smax, akey, flags, ring, kp, s_t);
       else
         step1d_warp<R, PP, LIM, 2>(k, Uin, Uout, n, stride, c0, c1, lane, dt, dtdx, dt_2h, dt_2,
-                                   smax, akey, flags, ring);
+                                   smax, akey, flags, ring, kp, s_t);
       // the barrier inside block_max also orders this step's stores before the
       // next step's loads of neighbouring warps' cells
       block_max(smax, akey, flags, s_a, s_b, s_f);

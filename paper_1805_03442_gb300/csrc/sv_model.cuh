@@ -33,6 +33,8 @@ struct KParams {
   int qi_zero;   // 1: all Q and I exponents are zero (Q = I = Q0)
   int bc_lo, bc_hi;   // 1D boundary conditions at x = 0 / x = L (BC_*)
   int pad;
+  // driven boundary wave: U = base + Re(amp e^{i (k x - omega t)})
+  double drv_omega, drv_kre, drv_kim, drv_base[4], drv_are[4], drv_aim[4];
   // float copies for the float kernels (kparams_finish): the twelve values
   // above, then log2(1/tau0) (0 in the frozen limit), -tau_rho, -tau_T
   float f[16];
@@ -68,7 +70,7 @@ struct Ctl {
 };
 
 // 1D boundary conditions (the values of SV_BC_* in sv.h).
-constexpr int BC_PERIODIC = 0, BC_REFLECT = 1, BC_OUTFLOW = 2;
+constexpr int BC_PERIODIC = 0, BC_REFLECT = 1, BC_OUTFLOW = 2, BC_DRIVEN = 3;
 
 constexpr uint32_t FLAG_NONPHYS = 1u;
 constexpr uint32_t FLAG_DT = 2u;

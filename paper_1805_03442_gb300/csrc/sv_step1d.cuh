@@ -178,15 +178,26 @@ __device__ __forceinline__ void update_cell(const P<R>& k, const R (&u)[4], cons
   cfl_cell<R, PP, SRC>(k, un[0], un[1] * v, fabs(v), un[2], un[3], smax, akey, flags);
 }
 
+// State of the driven boundary's ghost cell centred at x at time t (double).
+__device__ __forceinline__ void drive_state(const KParams& kp, double x, double t, double (&u)[4]) {
+  const double env = exp(-kp.drv_kim * x);
+  double s, c;
+  sincos(kp.drv_kre * x - kp.drv_omega * t, &s, &c);
+#pragma unroll
+  for (int f = 0; f < 4; ++f) u[f] = kp.drv_base[f] + env * (kp.drv_are[f] * c - kp.drv_aim[f] * s);
+}
+
 // One warp's share of a step: chunks [c0, c1) (64 cells each) of the periodic
 // grid of N cells Uin -> Uout (fields `stride` elements apart).  `ring` is this
 // warp's shared buffer (ring1d_bytes<R>()).  Folds the updated cells' signal
 // speed / tau key / flags into the per-thread accumulators.
+// `kp` and `t` (the step's start time) only serve a driven boundary.
 template <typename R, int PP, int LIM, int SRC>
 __device__ __forceinline__ void step1d_warp(const P<R>& k, const R* __restrict__ Uin,
                                             R* __restrict__ Uout, int N, int stride, int c0, int c1,
                                             int lane, R dt, R dtdx, R dt_2h, R dt_2, R& smax,
-                                            R& akey, uint32_t& flags, R* __restrict__ ring) {
+                                            R& akey, uint32_t& flags, R* __restrict__ ring,
+                                            const KParams& kp, double t) {
   using R2 = typename Pair<R>::T;
   constexpr int RS = kRing1d, RN = RS * 64, MASK = RN - 1;
   if (c1 <= c0) return;
@@ -203,13 +214,19 @@ __device__ __forceinline__ void step1d_warp(const P<R>& k, const R* __restrict__
 #pragma unroll
         for (int f = 0; f < 4; ++f) cp_async<2 * sizeof(R)>(dst + f * RN, Uin + f * stride + j);
       } else {
-        bool f0, f1;
-        const int i0 = bc_index(j, N, k.bc_lo, k.bc_hi, f0);
-        const int i1 = bc_index(j + 1, N, k.bc_lo, k.bc_hi, f1);
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          cp_async<sizeof(R)>(dst + f * RN, Uin + f * stride + i0);
-          cp_async<sizeof(R)>(dst + f * RN + 1, Uin + f * stride + i1);
+        for (int e = 0; e < 2; ++e) {
+          if (j + e < 0 && k.bc_lo == BC_DRIVEN) {
+            double u[4];
+            drive_state(kp, ((double)(j + e) + 0.5) * kp.h, t, u);
+#pragma unroll
+            for (int f = 0; f < 4; ++f) dst[f * RN + e] = (R)u[f];
+          } else {
+            bool fl;
+            const int i = bc_index(j + e, N, k.bc_lo, k.bc_hi, fl);
+#pragma unroll
+            for (int f = 0; f < 4; ++f) cp_async<sizeof(R)>(dst + f * RN + e, Uin + f * stride + i);
+          }
         }
       }
     }

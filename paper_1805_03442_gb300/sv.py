@@ -23,13 +23,13 @@ NOALLOC_MAX_CELLS = (1 << 29) - 1
 FLAG_NONPHYS, FLAG_DT, FLAG_MAXSTEPS = 1, 2, 4
 MINMOD, VANLEER, MC = 0, 1, 2
 FP32, FP64, FP32_P64 = 0, 1, 2
-BC_PERIODIC, BC_REFLECT, BC_OUTFLOW = 0, 1, 2
+BC_PERIODIC, BC_REFLECT, BC_OUTFLOW, BC_DRIVEN = 0, 1, 2, 3
 
 EXPORTS = ("sv_required_bytes", "sv_init", "sv_write_state", "sv_read_state", "sv_dt_cfl",
            "sv_step", "sv_run_to", "sv_time", "sv_conservation", "sv_status",
            "sv_state_device", "sv_free", "sv_strerror", "sv_batch_required_bytes",
            "sv_batch_init", "sv_batch_reset", "sv_batch_run", "sv_batch_sync", "sv_batch_read",
-           "sv_batch_mode_log", "sv_batch_free", "sv_step1d_noalloc")
+           "sv_batch_mode_log", "sv_batch_free", "sv_step1d_noalloc", "sv_set_drive")
 
 
 class SvError(RuntimeError):
@@ -49,6 +49,12 @@ class _Run(ctypes.Structure):
                 ("S", ctypes.c_double), ("tau0", ctypes.c_double), ("tau_rho", ctypes.c_double),
                 ("tau_T", ctypes.c_double), ("Q_rho", ctypes.c_double), ("Q_T", ctypes.c_double),
                 ("I_rho", ctypes.c_double), ("I_T", ctypes.c_double), ("mode", ctypes.c_int)]
+
+
+class _Drive(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_double), ("k_re", ctypes.c_double), ("k_im", ctypes.c_double),
+                ("base", ctypes.c_double * 4), ("amp_re", ctypes.c_double * 4),
+                ("amp_im", ctypes.c_double * 4)]
 
 
 class _Grid(ctypes.Structure):
@@ -122,6 +128,7 @@ def lib() -> ctypes.CDLL:
                                     ctypes.POINTER(ctypes.c_int64)]
     L.sv_batch_free.argtypes = [vp]
     L.sv_batch_free.restype = None
+    L.sv_set_drive.argtypes = [vp, ctypes.POINTER(_Drive)]
     L.sv_step1d_noalloc.argtypes = [ctypes.POINTER(_Params), ctypes.c_int64, ctypes.c_double, vp, vp,
                                     dp, ctypes.POINTER(ctypes.c_uint32), vp]
     _lib = L
@@ -269,6 +276,17 @@ class Solver:
         if check and rc not in (SV_OK,):
             raise SvError(rc, "sv_run_to")
         return rc, k.value
+
+    def set_drive(self, omega: float, k: complex, base, amp):
+        """Driven boundary (bc[0] = BC_DRIVEN): ghost cells at x < 0 hold
+        base + Re(amp e^{i(k x - omega t)}) (conserved variables)."""
+        d = _Drive()
+        d.omega, d.k_re, d.k_im = float(omega), float(complex(k).real), float(complex(k).imag)
+        for f in range(4):
+            d.base[f] = float(base[f])
+            d.amp_re[f] = float(complex(amp[f]).real)
+            d.amp_im[f] = float(complex(amp[f]).imag)
+        _check(lib().sv_set_drive(self._h, ctypes.byref(d)), "sv_set_drive")
 
     def time(self) -> tuple[float, int]:
         t, k = ctypes.c_double(), ctypes.c_int64()
