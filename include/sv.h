@@ -69,6 +69,11 @@ extern "C" {
 #define SV_FP64     1   /* double state and arithmetic */
 #define SV_FP32_P64 2   /* float state, pressure recovery of eq. 5 in double */
 
+/* ---- time integration */
+#define SV_HANCOCK  0   /* MUSCL-Hancock: half-step predictor + corrector (eqs. 14-15) */
+#define SV_HEUN     1   /* Heun / SSP-RK2 (the predictor-corrector of eqs. 10-11) over the
+                           same spatial operator; 1D periodic grids, SV_FP32 or SV_FP64 */
+
 typedef struct {
   double gamma;                 /* adiabatic exponent (eq. 5) */
   double Ck;                    /* C_k = dE_nue/(R dT) (under eq. 8) */
@@ -82,6 +87,7 @@ typedef struct {
   double c_tau;                 /* dt <= c_tau * min tau (explicit source), e.g. 0.5 */
   int limiter;                  /* SV_MINMOD, SV_VANLEER, SV_MC */
   int precision;                /* SV_FP32, SV_FP64, SV_FP32_P64 */
+  int method;                   /* SV_HANCOCK (0) or SV_HEUN */
 } sv_params;
 
 /* ---- boundary conditions (1D grids; 2D and 3D grids are periodic) */

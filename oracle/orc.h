@@ -97,6 +97,15 @@ int orc_step_bc1(const orc_params* P, long N, double h, double dt, int bc_lo, in
 int orc_run_bc1(const orc_params* P, long N, double h, int bc_lo, int bc_hi, double* U,
                 double t0, double t_end, long max_steps, double* t_out, long* steps_out);
 
+/* Heun (SSP-RK2) time integration of the same spatial operator on a periodic
+   grid: U* = U + dt L(U), U^{n+1} = (U + U*)/2 + dt/2 L(U*), with L the
+   flux divergence of eq. 13/14 faces at the stage's own time level plus Y.
+   Returns and runs as orc_step / orc_run. */
+int orc_step_heun(const orc_params* P, int dim, const long* n, double h, double dt,
+                  const double* U, double* Unew);
+int orc_run_heun(const orc_params* P, int dim, const long* n, double h, double* U,
+                 double t0, double t_end, long max_steps, double* t_out, long* steps_out);
+
 /* Number of OpenMP threads the array loops use (1 without OpenMP). */
 int orc_threads(void);
 

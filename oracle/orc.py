@@ -127,6 +127,9 @@ def lib():
                                    ctypes.c_int, dp, dp]
         L.orc_run_bc1.argtypes = [pp, ctypes.c_long, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                   dp, ctypes.c_double, ctypes.c_double, ctypes.c_long, dp, lp]
+        L.orc_step_heun.argtypes = [pp, ctypes.c_int, lp, ctypes.c_double, ctypes.c_double, dp, dp]
+        L.orc_run_heun.argtypes = [pp, ctypes.c_int, lp, ctypes.c_double, dp, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_long, dp, lp]
         L.orc_run_bc1d.argtypes = [pp, ctypes.c_long, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                    ctypes.POINTER(_CDrive), dp, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_long, dp, lp]
@@ -252,4 +255,24 @@ def run_driven(P: Params, U: np.ndarray, N: int, h: float, t_end: float, drv: _C
     k = ctypes.c_long()
     rc = lib().orc_run_bc1d(ctypes.byref(P.c()), int(N), h, DRIVEN, bc_hi, ctypes.byref(drv),
                             _dp(U), t0, t_end, max_steps, ctypes.byref(t), ctypes.byref(k))
+    return U, t.value, k.value, rc
+
+
+def step_heun(P: Params, U: np.ndarray, n, h: float, dt: float):
+    """One Heun (SSP-RK2) step of the same spatial operator; periodic grid."""
+    dim, na = _shape(n)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    out = np.empty_like(U)
+    rc = lib().orc_step_heun(ctypes.byref(P.c()), dim, na, h, dt, _dp(U), _dp(out))
+    return out, rc
+
+
+def run_heun(P: Params, U: np.ndarray, n, h: float, t_end: float, t0: float = 0.0,
+             max_steps: int = 1 << 40):
+    dim, na = _shape(n)
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    t = ctypes.c_double()
+    k = ctypes.c_long()
+    rc = lib().orc_run_heun(ctypes.byref(P.c()), dim, na, h, _dp(U), t0, t_end, max_steps,
+                            ctypes.byref(t), ctypes.byref(k))
     return U, t.value, k.value, rc

@@ -439,3 +439,96 @@ int orc_run_bc1d(const orc_params* P, long N, double h, int bc_lo, int bc_hi,
   *steps_out = k;
   return rc;
 }
+
+/* ------------------------------------------------------------ Heun / SSP-RK2 */
+
+/* Spatial operator of the method of lines on a periodic grid:
+   L(U)_j = -1/h sum_axes (F_{j+1/2} - F_{j-1/2}) + Y(U_j), with the faces of
+   eq. 13 between the piecewise-linear states of eq. 14 taken at time level n
+   (U_j +- Theta_j h / 2, no half step), the same limiter and positivity guard
+   as the MUSCL-Hancock step. */
+static int rhs(const orc_params* P, const grid_t* g, double h, const double* U, double* Lu) {
+  const int dim = g->dim, nf = g->nf;
+  const long N = g->ncell;
+  double (*dU)[3][NF_MAX] = malloc(sizeof(double[3][NF_MAX]) * (size_t)N);
+  double (*Fface)[3][NF_MAX] = malloc(sizeof(double[3][NF_MAX]) * (size_t)N);
+  double (*u0)[NF_MAX] = malloc(sizeof(double[NF_MAX]) * (size_t)N);
+  if (!dU || !Fface || !u0) { free(dU); free(Fface); free(u0); return -2; }
+  /* slopes: the predictor with dt = 0 leaves the state unchanged (U^{n+1/2} = U) */
+#pragma omp parallel for schedule(static)
+  for (long q = 0; q < N; ++q) predict(P, g, h, 0.0, U, q, dU[q], u0[q]);
+#pragma omp parallel for schedule(static)
+  for (long q = 0; q < N; ++q)
+    for (int a = 0; a < dim; ++a) {
+      long r = neighbour(g, q, a, +1);
+      face_flux(P, g, U, a, q, dU[q], u0[q], r, dU[r], u0[r], Fface[q][a]);
+    }
+#pragma omp parallel for schedule(static)
+  for (long q = 0; q < N; ++q) {
+    double u[NF_MAX], Y[NF_MAX], div[NF_MAX];
+    gather(g, U, q, u);
+    for (int f = 0; f < nf; ++f) div[f] = 0.0;
+    for (int a = 0; a < dim; ++a) {
+      long l = neighbour(g, q, a, -1);
+      for (int f = 0; f < nf; ++f) div[f] += Fface[q][a][f] - Fface[l][a][f];
+    }
+    orc_source(P, dim, u, Y);
+    for (int f = 0; f < nf; ++f) Lu[(long)f * N + q] = -div[f] / h + Y[f];
+  }
+  free(dU); free(Fface); free(u0);
+  return 0;
+}
+
+/* One Heun step (the two-stage predictor-corrector of eqs. 10-11 applied to
+   the whole MUSCL operator):
+     U*      = U^n + dt L(U^n)
+     U^{n+1} = (U^n + U*) / 2 + dt/2 L(U*). */
+int orc_step_heun(const orc_params* P, int dim, const long* n, double h, double dt,
+                  const double* U, double* Unew) {
+  grid_t g = make_grid(dim, n);
+  const long M = (long)g.nf * g.ncell;
+  double* Lu = malloc(sizeof(double) * (size_t)M);
+  double* Us = malloc(sizeof(double) * (size_t)M);
+  if (!Lu || !Us) { free(Lu); free(Us); return -2; }
+  int rc = rhs(P, &g, h, U, Lu);
+  if (rc == 0) {
+    for (long i = 0; i < M; ++i) Us[i] = U[i] + dt * Lu[i];
+    rc = rhs(P, &g, h, Us, Lu);
+  }
+  int bad = 0;
+  if (rc == 0) {
+    for (long i = 0; i < M; ++i) Unew[i] = 0.5 * (U[i] + Us[i]) + 0.5 * dt * Lu[i];
+    for (long q = 0; q < g.ncell && !bad; ++q) {
+      double u[NF_MAX];
+      gather(&g, Unew, q, u);
+      if (!orc_physical(P, dim, u)) bad = 1;
+    }
+  }
+  free(Lu); free(Us);
+  return rc ? rc : (bad ? -1 : 0);
+}
+
+int orc_run_heun(const orc_params* P, int dim, const long* n, double h, double* U,
+                 double t0, double t_end, long max_steps, double* t_out, long* steps_out) {
+  grid_t g = make_grid(dim, n);
+  size_t bytes = sizeof(double) * (size_t)g.nf * (size_t)g.ncell;
+  double* tmp = malloc(bytes);
+  if (!tmp) return -2;
+  double t = t0;
+  long k = 0;
+  int rc = 0;
+  while (t < t_end && k < max_steps) {
+    double dt = orc_dt(P, dim, n, h, U);
+    int last = 0;
+    if (dt >= t_end - t) { dt = t_end - t; last = 1; }
+    rc = orc_step_heun(P, dim, n, h, dt, U, tmp);
+    memcpy(U, tmp, bytes);
+    t = last ? t_end : t + dt;
+    ++k;
+    if (rc != 0) break;
+  }
+  free(tmp);
+  *t_out = t;
+  *steps_out = k;
+  return rc;
+}

@@ -69,6 +69,11 @@ int check_inputs(const sv_params* p, const sv_grid* g) {
     if (g->dim > 1 && g->bc[side] != SV_BC_PERIODIC) return SV_EINVAL;
   }
   if (g->bc[1] == SV_BC_DRIVEN) return SV_EINVAL;
+  if (p->method != SV_HANCOCK && p->method != SV_HEUN) return SV_EINVAL;
+  if (p->method == SV_HEUN &&
+      (g->dim != 1 || g->bc[0] != SV_BC_PERIODIC || g->bc[1] != SV_BC_PERIODIC ||
+       p->precision == SV_FP32_P64))
+    return SV_EINVAL;
   if (g->dim == 1 && (g->bc[0] != SV_BC_PERIODIC || g->bc[1] != SV_BC_PERIODIC) && g->n[0] < 2)
     return SV_EINVAL;
   return SV_OK;
@@ -96,6 +101,13 @@ Layout layout(const sv_params* p, const sv_grid* g) {
   } while (0)
 
 cudaError_t launch_step(sv_solver* s, cudaStream_t st) {
+  if (s->dim == 1 && s->p.method == SV_HEUN) {
+    cudaError_t e = heun1d_launch(s->p.precision, 1, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell,
+                                  s->grid, st);
+    if (e != cudaSuccess) return e;
+    return heun1d_launch(s->p.precision, 2, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell, s->grid,
+                         st);
+  }
   if (s->dim == 1)
     return step1d_launch(s->p.precision, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell, s->grid, st);
   return stepnd_launch(s->dim, s->p.precision, s->kp, s->buf[0], s->buf[1], s->ctl, s->g.n,
@@ -234,7 +246,9 @@ int sv_init(const sv_params* p, const sv_grid* g, void* cuda_stream, void* devic
       cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     rc = SV_ECUDA;
   if (rc == SV_OK) {
-    s->grid = s->dim == 1 ? step1d_grid(s->kp, p->precision) : stepnd_grid(s->dim, p->precision, s->kp);
+    s->grid = s->dim == 1 ? (p->method == SV_HEUN ? heun1d_grid(s->kp, p->precision)
+                                                  : step1d_grid(s->kp, p->precision))
+                          : stepnd_grid(s->dim, p->precision, s->kp);
     if (s->grid < 1) rc = SV_ECUDA;
   }
   if (rc == SV_OK) {

@@ -17,6 +17,11 @@ int step1d_grid(const KParams& kp, int precision);
 cudaError_t step1d_launch(int precision, const KParams& kp, void* a, void* b, Ctl* ctl, int64_t N,
                           int grid, cudaStream_t st);
 
+// 1D Heun (SSP-RK2) stages (sv_heun1d.cu); stage 1 or 2
+int heun1d_grid(const KParams& kp, int precision);
+cudaError_t heun1d_launch(int precision, int stage, const KParams& kp, void* a, void* b, Ctl* ctl,
+                          int64_t N, int grid, cudaStream_t st);
+
 // 2D / 3D fused steps (sv_stepnd.cu); n[] cells per axis
 int stepnd_grid(int dim, int precision, const KParams& kp);
 cudaError_t stepnd_launch(int dim, int precision, const KParams& kp, void* a, void* b, Ctl* ctl,

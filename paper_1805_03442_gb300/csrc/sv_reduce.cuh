@@ -88,7 +88,7 @@ __device__ __forceinline__ T vload(const T* p) {
 // Turn the reduced maxima into the next dt (eq. 16 capped by c_tau tau and by
 // t_end).  `advance` = the kernel just completed a step.
 template <typename R>
-__device__ void finalize(Ctl* ctl, const KParams& kp, bool advance) {
+__device__ void finalize(Ctl* ctl, const KParams& kp, bool advance, bool flip = true) {
   __threadfence();
   const double smax = key_to_double(atomicExch((unsigned long long*)&ctl->smax_key,
                                                (unsigned long long)key_of(0.0)));
@@ -100,7 +100,7 @@ __device__ void finalize(Ctl* ctl, const KParams& kp, bool advance) {
   const double t_end = vload(&ctl->t_end);
   if (advance) {
     t = vload(&ctl->last) ? t_end : t + vload(&ctl->dt);
-    ctl->cur = vload(&ctl->cur) ^ 1u;
+    if (flip) ctl->cur = vload(&ctl->cur) ^ 1u;
     ctl->nsteps = vload(&ctl->nsteps) + 1;
   }
   uint32_t last = 0;
@@ -126,7 +126,8 @@ __device__ void finalize(Ctl* ctl, const KParams& kp, bool advance) {
 // Must be called by every thread of the block, after its last store.
 template <typename R, int NT>
 __device__ __forceinline__ void reduce_and_finalize(Ctl* ctl, const KParams& kp, double smax,
-                                                    double akey, uint32_t flags, bool advance) {
+                                                    double akey, uint32_t flags, bool advance,
+                                                    bool flip = true) {
   __shared__ double s_s[NT / 32], s_a[NT / 32];
   __shared__ uint32_t s_f[NT / 32];
   __shared__ bool s_last;
@@ -158,7 +159,7 @@ __device__ __forceinline__ void reduce_and_finalize(Ctl* ctl, const KParams& kp,
     s_last = (ticket == gridDim.x - 1);
   }
   __syncthreads();
-  if (s_last && threadIdx.x == 0) finalize<R>(ctl, kp, advance);
+  if (s_last && threadIdx.x == 0) finalize<R>(ctl, kp, advance, flip);
 }
 
 // Periodic index for |j| within a few periods of [0, N).

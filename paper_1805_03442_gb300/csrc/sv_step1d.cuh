@@ -112,6 +112,39 @@ __device__ __forceinline__ void predict(const P<R>& k, const R (&u)[4], const R 
   }
 }
 
+// Heun stages: slopes with the same guard, face states at the stage's own time
+// level (wp = u + d/2, wm = u - d/2) and the source Y(u) for the update.
+template <typename R, int PP, int LIM, int SRC>
+__device__ __forceinline__ void level_states(const P<R>& k, const R (&u)[4], const R (&um)[4],
+                                             const R (&up)[4], R (&wp)[4], R (&wm)[4], R& yE,
+                                             R& yEv) {
+  R d[4], a[4], b[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    d[f] = limit<LIM, R>(u[f] - um[f], up[f] - u[f]);
+    a[f] = u[f] + (R)0.5 * d[f];
+    b[f] = u[f] - (R)0.5 * d[f];
+  }
+  R ira, va, ka, pa, irb, vb, kb, pb;
+  prim1<R, PP>(k, a, ira, va, ka, pa);
+  prim1<R, PP>(k, b, irb, vb, kb, pb);
+  if (!(fmin(fmin(a[0], pa), fmin(b[0], pb)) > (R)0)) {
+#pragma unroll
+    for (int f = 0; f < 4; ++f) a[f] = b[f] = u[f];
+  }
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    wp[f] = a[f];
+    wm[f] = b[f];
+  }
+  yE = yEv = (R)0;
+  if (SRC != 0) {
+    R ir, v, kin2, p;
+    prim1<R, PP>(k, u, ir, v, kin2, p);
+    Src<R, SRC>::eval(k, u[0], p * ir, u[3], yE, yEv);
+  }
+}
+
 // eq. 13 at one face; a face with a non-physical state uses the cell values
 // (fl, fr) instead.
 template <typename R, int PP>
@@ -165,8 +198,8 @@ __device__ __forceinline__ R shfl(R v, int src) {
   return __shfl_sync(0xffffffffu, v, src);
 }
 
-// Conservative update (eq. 15) of one cell and its next-dt bound.
-template <typename R, int PP, int SRC>
+// Conservative update (eq. 15) of one cell and, with CFL, its next-dt bound.
+template <typename R, int PP, int SRC, bool CFL = true>
 __device__ __forceinline__ void update_cell(const P<R>& k, const R (&u)[4], const R (&Fl)[4],
                                             const R (&Fr)[4], R yE, R yEv, R dt, R dtdx,
                                             R (&un)[4], R& smax, R& akey, uint32_t& flags) {
@@ -174,8 +207,10 @@ __device__ __forceinline__ void update_cell(const P<R>& k, const R (&u)[4], cons
   un[1] = u[1] - dtdx * (Fr[1] - Fl[1]);
   un[2] = u[2] - dtdx * (Fr[2] - Fl[2]) + dt * yE;
   un[3] = u[3] - dtdx * (Fr[3] - Fl[3]) + dt * yEv;
-  const R v = un[1] * Ar<R>::rcp(un[0]);
-  cfl_cell<R, PP, SRC>(k, un[0], un[1] * v, fabs(v), un[2], un[3], smax, akey, flags);
+  if (CFL) {
+    const R v = un[1] * Ar<R>::rcp(un[0]);
+    cfl_cell<R, PP, SRC>(k, un[0], un[1] * v, fabs(v), un[2], un[3], smax, akey, flags);
+  }
 }
 
 // State of the driven boundary's ghost cell centred at x at time t (double).
@@ -191,13 +226,20 @@ __device__ __forceinline__ void drive_state(const KParams& kp, double x, double 
 // grid of N cells Uin -> Uout (fields `stride` elements apart).  `ring` is this
 // warp's shared buffer (ring1d_bytes<R>()).  Folds the updated cells' signal
 // speed / tau key / flags into the per-thread accumulators.
+// Step modes: the MUSCL-Hancock step, or one of the two stages of the Heun
+// (SSP-RK2) integration of the same spatial operator L:
+//   stage 1: Uout = Uin + dt L(Uin)
+//   stage 2: Uout = (U0 + Uin) / 2 + dt/2 L(Uin)   (U0 read cell by cell; Uout
+//            may be U0: each cell reads its own U0 before writing it)
+enum { MODE_HANCOCK = 0, MODE_HEUN1 = 1, MODE_HEUN2 = 2 };
+
 // `kp` and `t` (the step's start time) only serve a driven boundary.
-template <typename R, int PP, int LIM, int SRC>
-__device__ __forceinline__ void step1d_warp(const P<R>& k, const R* __restrict__ Uin,
-                                            R* __restrict__ Uout, int N, int stride, int c0, int c1,
-                                            int lane, R dt, R dtdx, R dt_2h, R dt_2, R& smax,
-                                            R& akey, uint32_t& flags, R* __restrict__ ring,
-                                            const KParams& kp, double t) {
+template <typename R, int PP, int LIM, int SRC, int MODE = MODE_HANCOCK>
+__device__ __forceinline__ void step1d_warp(const P<R>& k, const R* __restrict__ Uin, R* Uout,
+                                            int N, int stride, int c0, int c1, int lane, R dt,
+                                            R dtdx, R dt_2h, R dt_2, R& smax, R& akey,
+                                            uint32_t& flags, R* __restrict__ ring,
+                                            const KParams& kp, double t, const R* U0 = nullptr) {
   using R2 = typename Pair<R>::T;
   constexpr int RS = kRing1d, RN = RS * 64, MASK = RN - 1;
   if (c1 <= c0) return;
@@ -275,8 +317,13 @@ __device__ __forceinline__ void step1d_warp(const P<R>& k, const R* __restrict__
       up[f] = rf[(pos + 2) & MASK];
     }
     R Wp0[4], Wm0[4], Wp1[4], Wm1[4], y0E, y0Ev, y1E, y1Ev;
-    predict<R, PP, LIM, SRC>(k, x0, um, x1, dt_2h, dt_2, Wp0, Wm0, y0E, y0Ev);
-    predict<R, PP, LIM, SRC>(k, x1, x0, up, dt_2h, dt_2, Wp1, Wm1, y1E, y1Ev);
+    if (MODE == MODE_HANCOCK) {
+      predict<R, PP, LIM, SRC>(k, x0, um, x1, dt_2h, dt_2, Wp0, Wm0, y0E, y0Ev);
+      predict<R, PP, LIM, SRC>(k, x1, x0, up, dt_2h, dt_2, Wp1, Wm1, y1E, y1Ev);
+    } else {
+      level_states<R, PP, LIM, SRC>(k, x0, um, x1, Wp0, Wm0, y0E, y0Ev);
+      level_states<R, PP, LIM, SRC>(k, x1, x0, up, Wp1, Wm1, y1E, y1Ev);
+    }
     R Fa[4] = {0, 0, 0, 0}, Fb[4];
     hll<R, PP>(k, Wp0, Wm1, x0, x1, Fb);            // face 2i + 1/2
     if (kk >= c0) {
@@ -293,11 +340,21 @@ __device__ __forceinline__ void step1d_warp(const P<R>& k, const R* __restrict__
       const int jo = (kk - 1) * 64 + 2 * lane;
       R n0[4], n1[4];
       if (jo < N) {
-        update_cell<R, PP, SRC>(k, q0, Fa_prev, Fb_prev, y0E_prev, y0Ev_prev, dt, dtdx, n0, smax,
-                                akey, flags);
+        if (MODE == MODE_HEUN2) {
+          // (U0 + U*)/2 + dt/2 L(U*) = (U0 + U*)/2 - dt/(2h) dF + dt/2 Y(U*)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) {
+            // plain loads: U0 may be the buffer this kernel writes
+            q0[f] = (R)0.5 * (U0[f * stride + jo] + q0[f]);
+            if (jo + 1 < N) q1[f] = (R)0.5 * (U0[f * stride + jo + 1] + q1[f]);
+          }
+        }
+        const R udt = MODE == MODE_HEUN2 ? dt_2 : dt, udx = MODE == MODE_HEUN2 ? dt_2h : dtdx;
+        update_cell<R, PP, SRC, MODE != MODE_HEUN1>(k, q0, Fa_prev, Fb_prev, y0E_prev, y0Ev_prev,
+                                                     udt, udx, n0, smax, akey, flags);
         if (jo + 1 < N) {
-          update_cell<R, PP, SRC>(k, q1, Fb_prev, FR, y1E_prev, y1Ev_prev, dt, dtdx, n1, smax,
-                                  akey, flags);
+          update_cell<R, PP, SRC, MODE != MODE_HEUN1>(k, q1, Fb_prev, FR, y1E_prev, y1Ev_prev, udt,
+                                                       udx, n1, smax, akey, flags);
           if ((stride % 2) == 0) {
 #pragma unroll
             for (int f = 0; f < 4; ++f)

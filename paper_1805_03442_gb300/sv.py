@@ -24,6 +24,7 @@ FLAG_NONPHYS, FLAG_DT, FLAG_MAXSTEPS = 1, 2, 4
 MINMOD, VANLEER, MC = 0, 1, 2
 FP32, FP64, FP32_P64 = 0, 1, 2
 BC_PERIODIC, BC_REFLECT, BC_OUTFLOW, BC_DRIVEN = 0, 1, 2, 3
+HANCOCK, HEUN = 0, 1
 
 EXPORTS = ("sv_required_bytes", "sv_init", "sv_write_state", "sv_read_state", "sv_dt_cfl",
            "sv_step", "sv_run_to", "sv_time", "sv_conservation", "sv_status",
@@ -41,7 +42,8 @@ class SvError(RuntimeError):
 class _Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
                 ("gamma", "Ck", "S", "tau0", "tau_rho", "tau_T", "Q_rho", "Q_T", "I_rho", "I_T",
-                 "cfl", "c_tau")] + [("limiter", ctypes.c_int), ("precision", ctypes.c_int)]
+                 "cfl", "c_tau")] + [("limiter", ctypes.c_int), ("precision", ctypes.c_int),
+                                     ("method", ctypes.c_int)]
 
 
 class _Run(ctypes.Structure):
@@ -80,6 +82,7 @@ class Params:
     c_tau: float = 0.5
     limiter: int = MINMOD
     precision: int = FP32
+    method: int = HANCOCK
 
     def c(self) -> _Params:
         return _Params(*[getattr(self, f.name) for f in fields(self)])
