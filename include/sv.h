@@ -53,11 +53,13 @@ extern "C" {
 #define SV_EDT        -5   /* the time step collapsed (dt <= 0 or non-finite) */
 #define SV_EMAXSTEPS  -7   /* sv_run_to stopped at max_steps before t_end */
 #define SV_ESIZE      -8   /* a size beyond the stated maximum of an entry point */
+#define SV_ESTALL     -9   /* a grid-wide wait of the persistent step loop timed out */
 
 /* ---- status flag bits (sv_status) */
 #define SV_FLAG_NONPHYS  1u
 #define SV_FLAG_DT       2u
 #define SV_FLAG_MAXSTEPS 4u   /* batched runs: step budget exhausted before t_end */
+#define SV_FLAG_STALL    8u   /* persistent step loop: a grid-wide wait gave up after ~2 s */
 
 /* ---- limiters (the paper asks for "TVD limiters" without naming one) */
 #define SV_MINMOD   0
@@ -137,10 +139,37 @@ int sv_dt_cfl(sv_solver* s, double* dt);
    solver's stream; errors of the steps show up in sv_status. */
 int sv_step(sv_solver* s, int64_t nsteps);
 
+/* How the steps of a solver are launched (sv_set_launch).
+   SV_LAUNCH_PER_STEP: one kernel launch per step (two for SV_HEUN), replayed
+     from a CUDA graph of 32 steps.
+   SV_LAUNCH_PERSISTENT: 1D MUSCL-Hancock only -- one cooperative launch runs
+     up to 65536 steps, its blocks resident throughout; the block that
+     finishes a step last computes the next dt and releases the others (a
+     grid-wide barrier).  Bitwise the same results as per-step launches.
+     Every barrier wait gives up after about 2 s with SV_FLAG_STALL, which
+     sv_run_to reports as SV_ESTALL.
+   SV_LAUNCH_AUTO (default): persistent for 1D MUSCL-Hancock grids of at most
+     one 64-cell chunk per SM (9728 cells on a GB300), where a step is short
+     enough for the gap between launches to matter; per-step launches
+     otherwise. */
+#define SV_LAUNCH_AUTO       0
+#define SV_LAUNCH_PER_STEP   1
+#define SV_LAUNCH_PERSISTENT 2
+
+/* Choose the launch mode.  SV_EINVAL for an unknown mode, or for
+   SV_LAUNCH_PERSISTENT on a solver that cannot use it (not 1D MUSCL-Hancock,
+   or no cooperative launch on the device).  Takes effect at the next step. */
+int sv_set_launch(sv_solver* s, int mode);
+
+/* The mode the next steps will use (SV_LAUNCH_PER_STEP or
+   SV_LAUNCH_PERSISTENT; AUTO resolved). */
+int sv_get_launch(sv_solver* s, int* mode);
+
 /* Advance until t_end, the last step clamped to land on t_end, or until
    max_steps steps.  Synchronous.  Returns SV_EMAXSTEPS if stopped early,
    SV_ENONPHYS / SV_EDT if the run failed (the state of the failing step is
-   kept).  *steps_taken (may be NULL) receives the number of steps. */
+   kept), SV_ESTALL if a persistent launch lost its barrier (the state is
+   then undefined).  *steps_taken (may be NULL) receives the number of steps. */
 int sv_run_to(sv_solver* s, double t_end, int64_t max_steps, int64_t* steps_taken);
 
 /* Current time and number of steps taken since the last sv_write_state. */

@@ -37,6 +37,9 @@ struct sv_solver {
   Ctl* host_ctl = nullptr;             // pinned mirror of the control block
   double* host_sums = nullptr;
   int grid = 0;
+  int loop_grid = 0;                   // persistent 1D loop: blocks (0 = not available)
+  bool loop_fits = false;              // ... at most one 64-cell chunk per SM
+  int launch = SV_LAUNCH_AUTO;
   cudaGraphExec_t graph = nullptr;
   int graph_len = 0;
 };
@@ -45,6 +48,7 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kGraphLen = 32;
+constexpr int64_t kLoopChunk = 1 << 16;   // steps per persistent launch at most
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -135,8 +139,27 @@ int ensure_graph(sv_solver* s) {
   return SV_OK;
 }
 
+// The persistent loop serves 1D MUSCL-Hancock solvers: always when asked for,
+// by default on grids of at most one 64-cell chunk per SM, where a step is
+// short enough for the gap between launches to matter (measured on a GB300:
+// 11-12 us instead of 14-15 us per float step up to 5000 cells, equal or
+// slightly slower from 2e4 cells on).
+bool use_loop(const sv_solver* s) {
+  if (s->loop_grid < 1) return false;
+  return s->launch == SV_LAUNCH_PERSISTENT || (s->launch == SV_LAUNCH_AUTO && s->loop_fits);
+}
+
 int issue_steps(sv_solver* s, int64_t n) {
   if (n <= 0) return SV_OK;
+  if (use_loop(s)) {
+    while (n > 0) {
+      const int64_t m = n < kLoopChunk ? n : kLoopChunk;
+      SV_TRY(loop1d_launch(s->p.precision, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell,
+                           s->loop_grid, m, s->stream));
+      n -= m;
+    }
+    return SV_OK;
+  }
   if (n >= kGraphLen) {
     int rc = ensure_graph(s);
     if (rc != SV_OK) return rc;
@@ -156,6 +179,7 @@ int read_ctl(sv_solver* s) {
 }
 
 int flags_to_status(uint32_t f) {
+  if (f & FLAG_STALL) return SV_ESTALL;
   if (f & FLAG_NONPHYS) return SV_ENONPHYS;
   if (f & FLAG_DT) return SV_EDT;
   return SV_OK;
@@ -251,6 +275,14 @@ int sv_init(const sv_params* p, const sv_grid* g, void* cuda_stream, void* devic
                           : stepnd_grid(s->dim, p->precision, s->kp);
     if (s->grid < 1) rc = SV_ECUDA;
   }
+  if (rc == SV_OK && s->dim == 1 && p->method == SV_HANCOCK) {
+    // 0 where the device has no cooperative launch: the per-step path remains
+    int dev = 0, sms = 0, cap = 0;
+    s->loop_grid = loop1d_grid(s->kp, p->precision, s->ncell, &cap);
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    s->loop_fits = s->loop_grid > 0 && (s->ncell + 63) / 64 <= (int64_t)sms;
+  }
   if (rc == SV_OK) {
     // uniform equilibrium start: rho = p = 1, v = 0, E_nu = C_k + S
     if (ctl_reset_launch(s->ctl, 0.0, s->stream) != cudaSuccess ||
@@ -328,6 +360,8 @@ int sv_run_to(sv_solver* s, double t_end, int64_t max_steps, int64_t* steps_take
     if (!(est >= 1.0)) est = 1.0;
     int64_t n = est > 1e15 ? (int64_t)1e15 : (int64_t)est;
     n = n > 4096 ? 4096 : n;
+    // the persistent loop stops by itself at t_end: no estimate needed
+    if (use_loop(s)) n = kLoopChunk;
     if (n > max_steps - done) n = max_steps - done;
     if (n < 1) n = 1;
     rc = issue_steps(s, n);
@@ -341,6 +375,19 @@ int sv_run_to(sv_solver* s, double t_end, int64_t max_steps, int64_t* steps_take
   // clear the target so that later sv_step calls are not clamped
   SV_TRY(set_target_launch(s->ctl, INFINITY, s->h, s->stream));
   return status;
+}
+
+int sv_set_launch(sv_solver* s, int mode) {
+  if (!s || mode < SV_LAUNCH_AUTO || mode > SV_LAUNCH_PERSISTENT) return SV_EINVAL;
+  if (mode == SV_LAUNCH_PERSISTENT && s->loop_grid < 1) return SV_EINVAL;
+  s->launch = mode;
+  return SV_OK;
+}
+
+int sv_get_launch(sv_solver* s, int* mode) {
+  if (!s || !mode) return SV_EINVAL;
+  *mode = use_loop(s) ? SV_LAUNCH_PERSISTENT : SV_LAUNCH_PER_STEP;
+  return SV_OK;
 }
 
 int sv_set_drive(sv_solver* s, const sv_drive* d) {
@@ -421,6 +468,7 @@ const char* sv_strerror(int code) {
     case SV_EDT: return "time step collapsed";
     case SV_EMAXSTEPS: return "max_steps reached before t_end";
     case SV_ESIZE: return "size beyond the maximum of this entry point";
+    case SV_ESTALL: return "a grid-wide wait of the persistent step loop timed out";
     default: return "unknown status";
   }
 }

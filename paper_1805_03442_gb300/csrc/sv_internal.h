@@ -17,6 +17,11 @@ int step1d_grid(const KParams& kp, int precision);
 cudaError_t step1d_launch(int precision, const KParams& kp, void* a, void* b, Ctl* ctl, int64_t N,
                           int grid, cudaStream_t st);
 
+// 1D persistent loop of up to nmax steps (sv_loop1d.cu); grid 0 = unavailable
+int loop1d_grid(const KParams& kp, int precision, int64_t N, int* cap);
+cudaError_t loop1d_launch(int precision, const KParams& kp, void* a, void* b, Ctl* ctl, int64_t N,
+                          int grid, int64_t nmax, cudaStream_t st);
+
 // 1D Heun (SSP-RK2) stages (sv_heun1d.cu); stage 1 or 2
 int heun1d_grid(const KParams& kp, int precision);
 cudaError_t heun1d_launch(int precision, int stage, const KParams& kp, void* a, void* b, Ctl* ctl,

@@ -66,7 +66,9 @@ struct Ctl {
   uint32_t ticket;     // blocks finished in the running launch
   uint64_t smax_key;   // order-preserving key of max signal speed
   uint64_t tau_key;    // order-preserving key of the tau bound (see finalize)
-  double pad[4];
+  uint32_t gen;        // grid-barrier generation of the persistent step loop
+  uint32_t pad32;
+  double pad[3];
 };
 
 // 1D boundary conditions (the values of SV_BC_* in sv.h).
@@ -74,6 +76,7 @@ constexpr int BC_PERIODIC = 0, BC_REFLECT = 1, BC_OUTFLOW = 2, BC_DRIVEN = 3;
 
 constexpr uint32_t FLAG_NONPHYS = 1u;
 constexpr uint32_t FLAG_DT = 2u;
+constexpr uint32_t FLAG_STALL = 8u;   // a grid-barrier wait ran out (sv.h SV_FLAG_STALL)
 
 // ---------------------------------------------------------------- arithmetic
 

@@ -122,12 +122,12 @@ __device__ void finalize(Ctl* ctl, const KParams& kp, bool advance, bool flip = 
   atomicExch(&ctl->ticket, 0u);
 }
 
-// Block-wide fold of (smax, akey, flags) followed by the last-block finalize.
-// Must be called by every thread of the block, after its last store.
-template <typename R, int NT>
-__device__ __forceinline__ void reduce_and_finalize(Ctl* ctl, const KParams& kp, double smax,
-                                                    double akey, uint32_t flags, bool advance,
-                                                    bool flip = true) {
+// Block-wide fold of (smax, akey, flags) into the control block, then this
+// block's ticket.  Returns, in every thread, whether this block was the last
+// of the launch to arrive.  Must be called by every thread of the block, after
+// its last store.
+template <int NT>
+__device__ __forceinline__ bool block_arrive(Ctl* ctl, double smax, double akey, uint32_t flags) {
   __shared__ double s_s[NT / 32], s_a[NT / 32];
   __shared__ uint32_t s_f[NT / 32];
   __shared__ bool s_last;
@@ -159,7 +159,16 @@ __device__ __forceinline__ void reduce_and_finalize(Ctl* ctl, const KParams& kp,
     s_last = (ticket == gridDim.x - 1);
   }
   __syncthreads();
-  if (s_last && threadIdx.x == 0) finalize<R>(ctl, kp, advance, flip);
+  return s_last;
+}
+
+// block_arrive followed by the last block's finalize.
+template <typename R, int NT>
+__device__ __forceinline__ void reduce_and_finalize(Ctl* ctl, const KParams& kp, double smax,
+                                                    double akey, uint32_t flags, bool advance,
+                                                    bool flip = true) {
+  const bool last = block_arrive<NT>(ctl, smax, akey, flags);
+  if (last && threadIdx.x == 0) finalize<R>(ctl, kp, advance, flip);
 }
 
 // Periodic index for |j| within a few periods of [0, N).

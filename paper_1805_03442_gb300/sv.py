@@ -18,9 +18,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libsv.so")
 
 SV_OK, SV_EINVAL, SV_ENOMEM, SV_ECUDA, SV_ENONPHYS, SV_EDT, SV_EMAXSTEPS = 0, -1, -2, -3, -4, -5, -7
-SV_ESIZE = -8
+SV_ESIZE, SV_ESTALL = -8, -9
 NOALLOC_MAX_CELLS = (1 << 29) - 1
-FLAG_NONPHYS, FLAG_DT, FLAG_MAXSTEPS = 1, 2, 4
+FLAG_NONPHYS, FLAG_DT, FLAG_MAXSTEPS, FLAG_STALL = 1, 2, 4, 8
+LAUNCH_AUTO, LAUNCH_PER_STEP, LAUNCH_PERSISTENT = 0, 1, 2
 MINMOD, VANLEER, MC = 0, 1, 2
 FP32, FP64, FP32_P64 = 0, 1, 2
 BC_PERIODIC, BC_REFLECT, BC_OUTFLOW, BC_DRIVEN = 0, 1, 2, 3
@@ -30,7 +31,8 @@ EXPORTS = ("sv_required_bytes", "sv_init", "sv_write_state", "sv_read_state", "s
            "sv_step", "sv_run_to", "sv_time", "sv_conservation", "sv_status",
            "sv_state_device", "sv_free", "sv_strerror", "sv_batch_required_bytes",
            "sv_batch_init", "sv_batch_reset", "sv_batch_run", "sv_batch_sync", "sv_batch_read",
-           "sv_batch_mode_log", "sv_batch_free", "sv_step1d_noalloc", "sv_set_drive")
+           "sv_batch_mode_log", "sv_batch_free", "sv_step1d_noalloc", "sv_set_drive",
+           "sv_set_launch", "sv_get_launch")
 
 
 class SvError(RuntimeError):
@@ -132,6 +134,8 @@ def lib() -> ctypes.CDLL:
     L.sv_batch_free.argtypes = [vp]
     L.sv_batch_free.restype = None
     L.sv_set_drive.argtypes = [vp, ctypes.POINTER(_Drive)]
+    L.sv_set_launch.argtypes = [vp, ctypes.c_int]
+    L.sv_get_launch.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.sv_step1d_noalloc.argtypes = [ctypes.POINTER(_Params), ctypes.c_int64, ctypes.c_double, vp, vp,
                                     dp, ctypes.POINTER(ctypes.c_uint32), vp]
     _lib = L
@@ -290,6 +294,17 @@ class Solver:
             d.amp_re[f] = float(complex(amp[f]).real)
             d.amp_im[f] = float(complex(amp[f]).imag)
         _check(lib().sv_set_drive(self._h, ctypes.byref(d)), "sv_set_drive")
+
+    def set_launch(self, mode: int):
+        """LAUNCH_AUTO, LAUNCH_PER_STEP or LAUNCH_PERSISTENT (1D MUSCL-Hancock)."""
+        _check(lib().sv_set_launch(self._h, int(mode)), "sv_set_launch")
+
+    @property
+    def launch(self) -> int:
+        """The launch mode the next steps use (LAUNCH_PER_STEP or LAUNCH_PERSISTENT)."""
+        m = ctypes.c_int()
+        _check(lib().sv_get_launch(self._h, ctypes.byref(m)), "sv_get_launch")
+        return m.value
 
     def time(self) -> tuple[float, int]:
         t, k = ctypes.c_double(), ctypes.c_int64()
