@@ -37,6 +37,7 @@ struct sv_solver {
   Ctl* host_ctl = nullptr;             // pinned mirror of the control block
   double* host_sums = nullptr;
   int grid = 0;
+  int tile_grid = 0;                   // float 1D MUSCL-Hancock on block tiles (0 = not used)
   int loop_grid = 0;                   // persistent 1D loop: blocks (0 = not available)
   bool loop_fits = false;              // ... at most one 64-cell chunk per SM
   int launch = SV_LAUNCH_AUTO;
@@ -112,6 +113,8 @@ cudaError_t launch_step(sv_solver* s, cudaStream_t st) {
     return heun1d_launch(s->p.precision, 2, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell, s->grid,
                          st);
   }
+  if (s->dim == 1 && s->tile_grid > 0)
+    return tile1d_launch(s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell, s->tile_grid, st);
   if (s->dim == 1)
     return step1d_launch(s->p.precision, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell, s->grid, st);
   return stepnd_launch(s->dim, s->p.precision, s->kp, s->buf[0], s->buf[1], s->ctl, s->g.n,
@@ -274,6 +277,11 @@ int sv_init(const sv_params* p, const sv_grid* g, void* cuda_stream, void* devic
                                                   : step1d_grid(s->kp, p->precision))
                           : stepnd_grid(s->dim, p->precision, s->kp);
     if (s->grid < 1) rc = SV_ECUDA;
+  }
+  if (rc == SV_OK && s->dim == 1 && p->method == SV_HANCOCK && p->precision == SV_FP32 &&
+      s->ncell >= kTile1dMinCells) {
+    s->tile_grid = tile1d_grid(s->kp);
+    if (s->tile_grid < 1) rc = SV_ECUDA;
   }
   if (rc == SV_OK && s->dim == 1 && p->method == SV_HANCOCK) {
     // 0 where the device has no cooperative launch: the per-step path remains

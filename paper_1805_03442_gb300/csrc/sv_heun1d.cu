@@ -17,16 +17,15 @@ template <typename R, int PP, int LIM, int SRC, int MODE, int MINB>
 __global__ void __launch_bounds__(NTH, MINB)
 heun1d_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl* __restrict__ ctl,
               int N) {
-  const double dtd = vload(&ctl->dt);
-  if (!(dtd > 0.0)) return;
-  const uint32_t cur = vload(&ctl->cur);
-  R* Un = cur ? bufB : bufA;        // U^n (and U^{n+1} after stage 2)
-  R* Us = cur ? bufA : bufB;        // U*
+  const StepCtl sc = block_step_ctl(ctl);
+  if (!(sc.dt > 0.0)) return;
+  R* Un = sc.cur ? bufB : bufA;     // U^n (and U^{n+1} after stage 2)
+  R* Us = sc.cur ? bufA : bufB;     // U*
   const R* Uin = MODE == MODE_HEUN1 ? Un : Us;
   R* Uout = MODE == MODE_HEUN1 ? Us : Un;
 
   const P<R> k(kp);
-  const StepDt<R> sd((const volatile Ctl*)ctl);
+  const StepDt<R> sd(sc);
   extern __shared__ __align__(16) unsigned char smemh[];
   R* ring = reinterpret_cast<R*>(smemh) + (threadIdx.x >> 5) * (ring1d_bytes<R>() / sizeof(R));
 
@@ -39,7 +38,7 @@ heun1d_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
   R smax = 0, akey = -INFINITY;
   uint32_t flags = 0;
   step1d_warp<R, PP, LIM, SRC, MODE>(k, Uin, Uout, N, N, c0, c1, lane, sd.dt, sd.dtdx, sd.dt_2h,
-                                     sd.dt_2, smax, akey, flags, ring, kp, vload(&ctl->t), Un);
+                                     sd.dt_2, smax, akey, flags, ring, kp, sc.t, Un);
   if (MODE == MODE_HEUN2)
     reduce_and_finalize<R, NTH>(ctl, kp, (double)smax, (double)akey, flags, true, false);
 }

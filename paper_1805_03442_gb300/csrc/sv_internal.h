@@ -17,6 +17,13 @@ int step1d_grid(const KParams& kp, int precision);
 cudaError_t step1d_launch(int precision, const KParams& kp, void* a, void* b, Ctl* ctl, int64_t N,
                           int grid, cudaStream_t st);
 
+// Float 1D MUSCL-Hancock step on block tiles (sv_tile1d.cu), grids of at
+// least kTile1dMinCells cells
+constexpr int64_t kTile1dMinCells = 4096;
+int tile1d_grid(const KParams& kp);
+cudaError_t tile1d_launch(const KParams& kp, void* a, void* b, Ctl* ctl, int64_t N, int grid,
+                          cudaStream_t st);
+
 // 1D persistent loop of up to nmax steps (sv_loop1d.cu); grid 0 = unavailable
 int loop1d_grid(const KParams& kp, int precision, int64_t N, int* cap);
 cudaError_t loop1d_launch(int precision, const KParams& kp, void* a, void* b, Ctl* ctl, int64_t N,

@@ -78,16 +78,16 @@ loop1d_kernel(const KParams kp, R* bufA, R* bufB, Ctl* ctl, int N, long long nma
   for (long long s = 0; s < nmax; ++s) {
     // ctl changes only inside the barrier below: every block sees the same
     // dt here and leaves the loop at the same step.
-    if (!(vload(&ctl->dt) > 0.0)) break;
-    const uint32_t gen0 = vload(&ctl->gen);
-    const uint32_t cur = vload(&ctl->cur);
-    const R* Uin = cur ? bufB : bufA;
-    R* Uout = cur ? bufA : bufB;
-    const StepDt<R> sd((const volatile Ctl*)ctl);
+    const StepCtl sc = block_step_ctl(ctl);
+    if (!(sc.dt > 0.0)) break;
+    const uint32_t gen0 = sc.gen;
+    const R* Uin = sc.cur ? bufB : bufA;
+    R* Uout = sc.cur ? bufA : bufB;
+    const StepDt<R> sd(sc);
     R smax = 0, akey = -INFINITY;
     uint32_t flags = 0;
     step1d_warp<R, PP, LIM, SRC>(k, Uin, Uout, N, N, c0, c1, lane, sd.dt, sd.dtdx, sd.dt_2h,
-                                 sd.dt_2, smax, akey, flags, ring, kp, vload(&ctl->t));
+                                 sd.dt_2, smax, akey, flags, ring, kp, sc.t);
     const bool last = block_arrive<NTL>(ctl, (double)smax, (double)akey, flags);
     if (threadIdx.x == 0) {
       bool ok = true;

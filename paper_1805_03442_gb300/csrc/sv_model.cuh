@@ -141,19 +141,51 @@ template <> struct P<float> {
         bc_hi(k.bc_hi) {}
 };
 
-// The dt-derived factors of the next step, read by the step kernels.
+// The control-block fields a step kernel reads: written by the previous
+// launch (or, in the persistent loop, by another block), so read with volatile
+// loads -- by one thread per block, which publishes them in shared memory.
+// (Every thread reading them itself sends tens of thousands of requests per
+// launch to the one L2 line of the control block.)
+struct StepCtl {
+  double t, dt, dtdx, dt_2h, dt_2;
+  float fdt, fdtdx, fdt_2h, fdt_2;
+  uint32_t cur, gen;
+};
+
+// Must be called by every thread of the block; ends with a block barrier.
+__device__ __forceinline__ StepCtl block_step_ctl(const Ctl* ctl) {
+  __shared__ StepCtl s;
+  if (threadIdx.x == 0) {
+    const volatile Ctl* c = (const volatile Ctl*)ctl;
+    s.t = c->t;
+    s.dt = c->dt;
+    s.dtdx = c->dtdx;
+    s.dt_2h = c->dt_2h;
+    s.dt_2 = c->dt_2;
+    s.fdt = c->fdt;
+    s.fdtdx = c->fdtdx;
+    s.fdt_2h = c->fdt_2h;
+    s.fdt_2 = c->fdt_2;
+    s.cur = c->cur;
+    s.gen = c->gen;
+  }
+  __syncthreads();
+  return s;
+}
+
+// The dt-derived factors of the next step in the kernel's arithmetic type.
 template <typename R> struct StepDt;
 template <> struct StepDt<double> {
   double dt, dtdx, dt_2h, dt_2;
-  __device__ __forceinline__ StepDt(const volatile Ctl* c)
-      : dt(c->dt), dtdx(c->dtdx), dt_2h(c->dt_2h), dt_2(c->dt_2) {}
+  __device__ __forceinline__ explicit StepDt(const StepCtl& c)
+      : dt(c.dt), dtdx(c.dtdx), dt_2h(c.dt_2h), dt_2(c.dt_2) {}
   __device__ __forceinline__ StepDt(double d, double h)
       : dt(d), dtdx(d / h), dt_2h(d / (2.0 * h)), dt_2(0.5 * d) {}
 };
 template <> struct StepDt<float> {
   float dt, dtdx, dt_2h, dt_2;
-  __device__ __forceinline__ StepDt(const volatile Ctl* c)
-      : dt(c->fdt), dtdx(c->fdtdx), dt_2h(c->fdt_2h), dt_2(c->fdt_2) {}
+  __device__ __forceinline__ explicit StepDt(const StepCtl& c)
+      : dt(c.fdt), dtdx(c.fdtdx), dt_2h(c.fdt_2h), dt_2(c.fdt_2) {}
   __device__ __forceinline__ StepDt(double d, double h)
       : dt((float)d), dtdx((float)(d / h)), dt_2h((float)(d / (2.0 * h))), dt_2((float)(0.5 * d)) {}
 };

@@ -17,14 +17,13 @@ template <typename R, int PP, int LIM, int SRC, int MINB>
 __global__ void __launch_bounds__(NT1, MINB)
 step1d_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl* __restrict__ ctl,
               int N) {
-  const double dtd = vload(&ctl->dt);
-  if (!(dtd > 0.0)) return;                       // stopped, or t_end reached
-  const uint32_t cur = vload(&ctl->cur);
-  const R* __restrict__ Uin = cur ? bufB : bufA;
-  R* __restrict__ Uout = cur ? bufA : bufB;
+  const StepCtl sc = block_step_ctl(ctl);
+  if (!(sc.dt > 0.0)) return;                     // stopped, or t_end reached
+  const R* __restrict__ Uin = sc.cur ? bufB : bufA;
+  R* __restrict__ Uout = sc.cur ? bufA : bufB;
 
   const P<R> k(kp);
-  const StepDt<R> sd((const volatile Ctl*)ctl);
+  const StepDt<R> sd(sc);
   const R dt = sd.dt, dtdx = sd.dtdx, dt_2h = sd.dt_2h, dt_2 = sd.dt_2;
   extern __shared__ __align__(16) unsigned char smem1d[];   // per-warp rings
   R* ring = reinterpret_cast<R*>(smem1d) + (threadIdx.x >> 5) * (ring1d_bytes<R>() / sizeof(R));
@@ -40,7 +39,7 @@ step1d_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
   uint32_t flags = 0;
 
   step1d_warp<R, PP, LIM, SRC>(k, Uin, Uout, N, N, c0, c1, lane, dt, dtdx, dt_2h, dt_2, smax, akey,
-                               flags, ring, kp, vload(&ctl->t));
+                               flags, ring, kp, sc.t);
   reduce_and_finalize<R, NT1>(ctl, kp, (double)smax, (double)akey, flags, true);
 }
 

@@ -20,8 +20,14 @@
 //      whose right-most face needed this chunk's first flux,
 //   6. the signal speed / tau bound of the updated cells for the next dt.
 // Only the two chunks around each warp's run are computed twice.
+// In float (all-float pressure, MUSCL-Hancock) steps 3-6 run on the lane's
+// two cells at once in packed f32x2 arithmetic (sv_pair1d.cuh); there both
+// faces of step 4 are one packed HLL evaluation.
 #pragma once
 
+#include <type_traits>
+
+#include "sv_pair1d.cuh"
 #include "sv_reduce.cuh"
 
 namespace sv {
@@ -296,6 +302,17 @@ __device__ __forceinline__ void step1d_warp(const P<R>& k, const R* __restrict__
   R Wp1_prev[4] = {0, 0, 0, 0}, Fa_prev[4] = {0, 0, 0, 0}, Fb_prev[4] = {0, 0, 0, 0};
   R y0E_prev = 0, y0Ev_prev = 0, y1E_prev = 0, y1Ev_prev = 0;
   const int src_m = (lane + 31) & 31, src_p = (lane + 1) & 31;
+  // The float MUSCL-Hancock step runs both cells of a lane in packed f32x2
+  // arithmetic (sv_pair1d.cuh); double, double-pressure and Heun stay scalar.
+  constexpr bool PACKED = std::is_same<R, float>::value && PP == 0 && MODE == MODE_HANCOCK;
+  using pk::f2;
+  // carried from chunk to chunk: the odd cell's right face state (its first
+  // use, by lane 0 of the warm-up chunk, only needs to be physical), the
+  // (left, inner) face fluxes and the half-step sources of the pair
+  float Wy_prev[4] = {1.0f, 0.0f, 1.0f, 0.0f};
+  f2 F_prev[4] = {}, YE_prev = {}, YEv_prev = {};
+  const f2 dt2 = pk::splat((float)dt), ndtdx2 = pk::splat(-(float)dtdx);
+  const f2 ndt_2h2 = pk::splat(-(float)dt_2h), dt_22 = pk::splat((float)dt_2);
   // chunk index kk runs from c0-1 (warm-up) to c1 (trailing faces)
   for (int kk = c0 - 1; kk <= c1; ++kk) {
     cp_async_wait<RS - 4>();     // chunks up to kk+1 have landed for this lane ...
@@ -303,85 +320,135 @@ __device__ __forceinline__ void step1d_warp(const P<R>& k, const R* __restrict__
     __syncwarp();                // ... and for the warp; chunk kk-2 is no longer read
     issue(kk + RS - 2);          // reuses the slot of chunk kk-2
     const int pos = (kk & (RS - 1)) * 64 + 2 * lane;
-    R x0[4], x1[4], um[4], up[4], q0[4], q1[4];
+    if constexpr (PACKED) {
+      f2 X[4], XM[4], A[4], B[4], Qp[4];
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      const R* rf = ring + f * RN;
-      const R2 c2 = *reinterpret_cast<const R2*>(rf + pos);
-      const R2 p2 = *reinterpret_cast<const R2*>(rf + ((pos - 64) & MASK));
-      x0[f] = c2.x;
-      x1[f] = c2.y;
-      q0[f] = p2.x;                // the previous chunk's pair (updated below)
-      q1[f] = p2.y;
-      um[f] = rf[(pos - 1) & MASK];
-      up[f] = rf[(pos + 2) & MASK];
-    }
-    R Wp0[4], Wm0[4], Wp1[4], Wm1[4], y0E, y0Ev, y1E, y1Ev;
-    if (MODE == MODE_HANCOCK) {
-      predict<R, PP, LIM, SRC>(k, x0, um, x1, dt_2h, dt_2, Wp0, Wm0, y0E, y0Ev);
-      predict<R, PP, LIM, SRC>(k, x1, x0, up, dt_2h, dt_2, Wp1, Wm1, y1E, y1Ev);
-    } else {
-      level_states<R, PP, LIM, SRC>(k, x0, um, x1, Wp0, Wm0, y0E, y0Ev);
-      level_states<R, PP, LIM, SRC>(k, x1, x0, up, Wp1, Wm1, y1E, y1Ev);
-    }
-    R Fa[4] = {0, 0, 0, 0}, Fb[4];
-    hll<R, PP>(k, Wp0, Wm1, x0, x1, Fb);            // face 2i + 1/2
-    if (kk >= c0) {
-      R WL[4];
+      for (int f = 0; f < 4; ++f) {
+        const float* rf = reinterpret_cast<const float*>(ring) + f * RN;
+        X[f] = *reinterpret_cast<const f2*>(rf + pos);
+        Qp[f] = *reinterpret_cast<const f2*>(rf + ((pos - 64) & MASK));   // previous chunk's pair
+        XM[f] = pk::pair(rf[(pos - 1) & MASK], X[f].x);
+        A[f] = pk::sub(X[f], XM[f]);
+        B[f] = pk::sub(pk::pair(X[f].y, rf[(pos + 2) & MASK]), X[f]);
+      }
+      f2 WP[4], WM[4], YE, YEv, L[4], F[4];
+      pk::predict<LIM, SRC>(k, X, A, B, ndt_2h2, dt_22, WP, WM, YE, YEv);
 #pragma unroll
-      for (int f = 0; f < 4; ++f) WL[f] = shfl(lane == 31 ? Wp1_prev[f] : Wp1[f], src_m);
-      hll<R, PP>(k, WL, Wm0, um, x0, Fa);           // face 2i - 1/2
-    }
-    if (kk > c0) {
-      // update of the pair of chunk kk-1
-      R FR[4];
+      for (int f = 0; f < 4; ++f) L[f] = pk::pair(shfl(lane == 31 ? Wy_prev[f] : WP[f].y, src_m), WP[f].x);
+      pk::hll(k, L, WM, XM, X, F);                  // faces 2i - 1/2 and 2i + 1/2
+      if (kk > c0) {
+        // update of the pair of chunk kk-1: left faces F_prev, right faces
+        // (inner face, next lane's left face)
+        f2 FRt[4];
 #pragma unroll
-      for (int f = 0; f < 4; ++f) FR[f] = shfl(lane == 0 ? Fa[f] : Fa_prev[f], src_p);
-      const int jo = (kk - 1) * 64 + 2 * lane;
-      R n0[4], n1[4];
-      if (jo < N) {
-        if (MODE == MODE_HEUN2) {
-          // (U0 + U*)/2 + dt/2 L(U*) = (U0 + U*)/2 - dt/(2h) dF + dt/2 Y(U*)
+        for (int f = 0; f < 4; ++f)
+          FRt[f] = pk::pair(F_prev[f].y, shfl(lane == 0 ? F[f].x : F_prev[f].x, src_p));
+        const int jo = (kk - 1) * 64 + 2 * lane;
+        if (jo < N) {
+          f2 Nw[4];
+          pk::update<SRC>(Qp, F_prev, FRt, YE_prev, YEv_prev, dt2, ndtdx2, Nw);
+          const bool two = jo + 1 < N;
+          pk::cfl<SRC>(k, Nw, two ? 3 : 1, smax, akey, flags);
+          if (two && (stride % 2) == 0) {
 #pragma unroll
-          for (int f = 0; f < 4; ++f) {
-            // plain loads: U0 may be the buffer this kernel writes
-            q0[f] = (R)0.5 * (U0[f * stride + jo] + q0[f]);
-            if (jo + 1 < N) q1[f] = (R)0.5 * (U0[f * stride + jo + 1] + q1[f]);
-          }
-        }
-        const R udt = MODE == MODE_HEUN2 ? dt_2 : dt, udx = MODE == MODE_HEUN2 ? dt_2h : dtdx;
-        update_cell<R, PP, SRC, MODE != MODE_HEUN1>(k, q0, Fa_prev, Fb_prev, y0E_prev, y0Ev_prev,
-                                                     udt, udx, n0, smax, akey, flags);
-        if (jo + 1 < N) {
-          update_cell<R, PP, SRC, MODE != MODE_HEUN1>(k, q1, Fb_prev, FR, y1E_prev, y1Ev_prev, udt,
-                                                       udx, n1, smax, akey, flags);
-          if ((stride % 2) == 0) {
-#pragma unroll
-            for (int f = 0; f < 4; ++f)
-              *reinterpret_cast<R2*>(Uout + f * stride + jo) = R2{n0[f], n1[f]};
+            for (int f = 0; f < 4; ++f) *reinterpret_cast<f2*>(Uout + f * stride + jo) = Nw[f];
           } else {
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
-              Uout[f * stride + jo] = n0[f];
-              Uout[f * stride + jo + 1] = n1[f];
+              Uout[f * stride + jo] = Nw[f].x;
+              if (two) Uout[f * stride + jo + 1] = Nw[f].y;
             }
           }
-        } else {
-#pragma unroll
-          for (int f = 0; f < 4; ++f) Uout[f * stride + jo] = n0[f];
         }
       }
-    }
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      Wp1_prev[f] = Wp1[f];
-      Fa_prev[f] = Fa[f];
-      Fb_prev[f] = Fb[f];
-    }
-    y0E_prev = y0E;
-    y0Ev_prev = y0Ev;
-    y1E_prev = y1E;
-    y1Ev_prev = y1Ev;
+      for (int f = 0; f < 4; ++f) {
+        Wy_prev[f] = WP[f].y;
+        F_prev[f] = F[f];
+      }
+      YE_prev = YE;
+      YEv_prev = YEv;
+    } else {
+      R x0[4], x1[4], um[4], up[4], q0[4], q1[4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const R* rf = ring + f * RN;
+        const R2 c2 = *reinterpret_cast<const R2*>(rf + pos);
+        const R2 p2 = *reinterpret_cast<const R2*>(rf + ((pos - 64) & MASK));
+        x0[f] = c2.x;
+        x1[f] = c2.y;
+        q0[f] = p2.x;                // the previous chunk's pair (updated below)
+        q1[f] = p2.y;
+        um[f] = rf[(pos - 1) & MASK];
+        up[f] = rf[(pos + 2) & MASK];
+      }
+      R Wp0[4], Wm0[4], Wp1[4], Wm1[4], y0E, y0Ev, y1E, y1Ev;
+      if (MODE == MODE_HANCOCK) {
+        predict<R, PP, LIM, SRC>(k, x0, um, x1, dt_2h, dt_2, Wp0, Wm0, y0E, y0Ev);
+        predict<R, PP, LIM, SRC>(k, x1, x0, up, dt_2h, dt_2, Wp1, Wm1, y1E, y1Ev);
+      } else {
+        level_states<R, PP, LIM, SRC>(k, x0, um, x1, Wp0, Wm0, y0E, y0Ev);
+        level_states<R, PP, LIM, SRC>(k, x1, x0, up, Wp1, Wm1, y1E, y1Ev);
+      }
+      R Fa[4] = {0, 0, 0, 0}, Fb[4];
+      hll<R, PP>(k, Wp0, Wm1, x0, x1, Fb);            // face 2i + 1/2
+      if (kk >= c0) {
+        R WL[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) WL[f] = shfl(lane == 31 ? Wp1_prev[f] : Wp1[f], src_m);
+        hll<R, PP>(k, WL, Wm0, um, x0, Fa);           // face 2i - 1/2
+      }
+      if (kk > c0) {
+        // update of the pair of chunk kk-1
+        R FR[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) FR[f] = shfl(lane == 0 ? Fa[f] : Fa_prev[f], src_p);
+        const int jo = (kk - 1) * 64 + 2 * lane;
+        R n0[4], n1[4];
+        if (jo < N) {
+          if (MODE == MODE_HEUN2) {
+            // (U0 + U*)/2 + dt/2 L(U*) = (U0 + U*)/2 - dt/(2h) dF + dt/2 Y(U*)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+              // plain loads: U0 may be the buffer this kernel writes
+              q0[f] = (R)0.5 * (U0[f * stride + jo] + q0[f]);
+              if (jo + 1 < N) q1[f] = (R)0.5 * (U0[f * stride + jo + 1] + q1[f]);
+            }
+          }
+          const R udt = MODE == MODE_HEUN2 ? dt_2 : dt, udx = MODE == MODE_HEUN2 ? dt_2h : dtdx;
+          update_cell<R, PP, SRC, MODE != MODE_HEUN1>(k, q0, Fa_prev, Fb_prev, y0E_prev, y0Ev_prev,
+                                                       udt, udx, n0, smax, akey, flags);
+          if (jo + 1 < N) {
+            update_cell<R, PP, SRC, MODE != MODE_HEUN1>(k, q1, Fb_prev, FR, y1E_prev, y1Ev_prev, udt,
+                                                         udx, n1, smax, akey, flags);
+            if ((stride % 2) == 0) {
+#pragma unroll
+              for (int f = 0; f < 4; ++f)
+                *reinterpret_cast<R2*>(Uout + f * stride + jo) = R2{n0[f], n1[f]};
+            } else {
+#pragma unroll
+              for (int f = 0; f < 4; ++f) {
+                Uout[f * stride + jo] = n0[f];
+                Uout[f * stride + jo + 1] = n1[f];
+              }
+            }
+          } else {
+#pragma unroll
+            for (int f = 0; f < 4; ++f) Uout[f * stride + jo] = n0[f];
+          }
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        Wp1_prev[f] = Wp1[f];
+        Fa_prev[f] = Fa[f];
+        Fb_prev[f] = Fb[f];
+      }
+      y0E_prev = y0E;
+      y0Ev_prev = y0Ev;
+      y1E_prev = y1E;
+      y1Ev_prev = y1Ev;
+    }   // scalar body
   }
   cp_async_wait<0>();            // nothing in flight when the warp moves on
   __syncwarp();

@@ -152,13 +152,12 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
   R (*sH)[NF][NH] = reinterpret_cast<R (*)[NF][NH]>(
       smem_raw + sizeof(R) * (NF * SY * (TX + 2) + 2 * (DIM - 1) * NF * TY * TX + D * NF * NT));
 
-  const double dtd = vload(&ctl->dt);
-  if (!(dtd > 0.0)) return;
-  const uint32_t cur = vload(&ctl->cur);
-  const R* __restrict__ Uin = cur ? bufB : bufA;
-  R* __restrict__ Uout = cur ? bufA : bufB;
+  const StepCtl sc = block_step_ctl(ctl);
+  if (!(sc.dt > 0.0)) return;
+  const R* __restrict__ Uin = sc.cur ? bufB : bufA;
+  R* __restrict__ Uout = sc.cur ? bufA : bufB;
   const P<R> k(kp);
-  const StepDt<R> sd((const volatile Ctl*)ctl);
+  const StepDt<R> sd(sc);
   const R dt = sd.dt, dtdx = sd.dtdx, dt_2h = sd.dt_2h, dt_2 = sd.dt_2;
 
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;

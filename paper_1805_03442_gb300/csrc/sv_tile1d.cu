@@ -1,0 +1,228 @@
+// sv_tile1d.cu -- the fused float 1D MUSCL-Hancock step (Sec. 2.3: eq. 14
+// reconstruction with xi = 0, half-step predictor, eq. 13 HLL, eq. 15 update
+// with the source Y, eq. 16 reduction) on block tiles, for large grids.
+//
+// A persistent block walks over tiles of 2 * NTT = 512 cells, thread t owning
+// the cell pair (b + 2t, b + 2t + 1) of the tile that starts at b, and writes
+// the 508 cells [b + 2, b + 510): the two cells at each end are computed only
+// to give the outermost written cells their faces (0.8% redundant work, no
+// state carried from tile to tile).  Per tile:
+//   1. the tile's 4 fields, cells [b - 2, b + 514), are in shared memory
+//      (16-byte cp.async copies, issued one tile ahead into a second buffer);
+//   2. slopes, guard, predictor and face states of the pair (packed f32x2,
+//      sv_pair1d.cuh);
+//   3. the left state of the pair's left face comes from lane - 1 by shuffle
+//      (for lane 0 from the previous warp through shared memory);
+//   4. the HLL fluxes of the pair's left and inner faces (one packed call);
+//   5. the right face of the odd cell is lane + 1's left face (shuffle; for
+//      lane 31 the next warp's lane 0 through shared memory);
+//   6. update, eq. 16 bound of the new states, 8-byte stores.
+// The per-cell arithmetic is that of the sliding warp body in float
+// (sv_step1d.cuh, packed path), operation for operation, so both kernels give
+// bitwise the same states.  The dt epilogue is the shared block fold and
+// last-block finalize.
+#include "sv_internal.h"
+#include "sv_step1d.cuh"
+
+namespace sv {
+
+namespace {
+
+constexpr int NTT = 256;                 // threads per block
+constexpr int TILE = 2 * NTT;            // cells computed per tile
+constexpr int OUT = TILE - 4;            // cells written per tile
+constexpr int SPAN = TILE + 4;           // cells held per tile: [b - 2, b + TILE + 2)
+constexpr int NWT = NTT / 32;
+
+struct TileSmem {
+  float u[2][4][SPAN];                   // double-buffered tile, field-major
+  float wp[NWT][4];                      // lane 31's odd-cell right face state, per warp
+  float fl[NWT][4];                      // lane 0's left face flux, per warp
+};
+
+__device__ __forceinline__ void cp16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// Fill buffer `dst` with tile b's cells [b - 2, b + TILE + 2).  Interior tiles
+// of a grid whose fields start on 16-byte boundaries use 16-byte copies; the
+// others go cell by cell through the boundary mapping (periodic wrap, wall
+// mirror, outflow copy, driven ghost state).  Commits one cp.async group.
+__device__ __forceinline__ void load_tile(float (*dst)[SPAN], const float* Uin, int N, int b,
+                                          const P<float>& k, const KParams& kp, double t) {
+  const int lo = b - 2;
+  if ((N & 3) == 0 && lo >= 0 && lo + SPAN <= N) {
+    // lo = b - 2 is a multiple of 4 (b = OUT * i - 2, OUT = 508)
+    for (int e = threadIdx.x; e < 4 * (SPAN / 4); e += NTT) {
+      const int f = e / (SPAN / 4), q = e - f * (SPAN / 4);
+      cp16(&dst[f][4 * q], Uin + (size_t)f * N + lo + 4 * q);
+    }
+  } else {
+    for (int e = threadIdx.x; e < SPAN; e += NTT) {
+      const int j = lo + e;
+      if (j < 0 && k.bc_lo == BC_DRIVEN) {
+        double u[4];
+        drive_state(kp, ((double)j + 0.5) * kp.h, t, u);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) dst[f][e] = (float)u[f];
+      } else {
+        bool flip;
+        const int i = bc_index(j, N, k.bc_lo, k.bc_hi, flip);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const float v = Uin[(size_t)f * N + i];
+          dst[f][e] = (f == 1 && flip) ? -v : v;
+        }
+      }
+    }
+  }
+  cp_async_commit();
+}
+
+template <int LIM, int SRC, int MINB>
+__global__ void __launch_bounds__(NTT, MINB)
+tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bufB,
+              Ctl* __restrict__ ctl, int N) {
+  using pk::f2;
+  const StepCtl sc = block_step_ctl(ctl);
+  if (!(sc.dt > 0.0)) return;                     // stopped, or t_end reached
+  const float* __restrict__ Uin = sc.cur ? bufB : bufA;
+  float* __restrict__ Uout = sc.cur ? bufA : bufB;
+  const double t = sc.t;
+
+  const P<float> k(kp);
+  const StepDt<float> sd(sc);
+  const f2 dt2 = pk::splat(sd.dt), ndtdx2 = pk::splat(-sd.dtdx);
+  const f2 ndt_2h2 = pk::splat(-sd.dt_2h), dt_22 = pk::splat(sd.dt_2);
+
+  extern __shared__ __align__(16) unsigned char smem_tile[];
+  TileSmem& S = *reinterpret_cast<TileSmem*>(smem_tile);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int src_m = (lane + 31) & 31, src_p = (lane + 1) & 31;
+  const int ntile = (N + OUT - 1) / OUT;
+
+  float smax = 0.0f, akey = -INFINITY;
+  uint32_t flags = 0;
+
+  int tile = blockIdx.x;
+  if (tile < ntile) load_tile(S.u[0], Uin, N, OUT * tile - 2, k, kp, t);
+  for (int it = 0; tile < ntile; ++it, tile += gridDim.x) {
+    const int buf = it & 1;
+    const int b = OUT * tile - 2;
+    cp_async_wait<0>();
+    __syncthreads();                              // tile in place; the other buffer is free
+    if (tile + (int)gridDim.x < ntile)
+      load_tile(S.u[buf ^ 1], Uin, N, OUT * (tile + gridDim.x) - 2, k, kp, t);
+
+    // the pair sits at span offsets 2 + 2t, 3 + 2t
+    const int pos = 2 + 2 * threadIdx.x;
+    f2 X[4], XM[4], A[4], B[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const float* rf = S.u[buf][f];
+      X[f] = *reinterpret_cast<const f2*>(rf + pos);
+      XM[f] = pk::pair(rf[pos - 1], X[f].x);
+      A[f] = pk::sub(X[f], XM[f]);
+      B[f] = pk::sub(pk::pair(X[f].y, rf[pos + 2]), X[f]);
+    }
+    f2 WP[4], WM[4], YE, YEv;
+    pk::predict<LIM, SRC>(k, X, A, B, ndt_2h2, dt_22, WP, WM, YE, YEv);
+
+    if (lane == 31) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) S.wp[w][f] = WP[f].y;
+    }
+    __syncthreads();
+    f2 L[4], F[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const float nb = __shfl_sync(0xffffffffu, WP[f].y, src_m);
+      // thread 0's left face is outside the written cells: any physical state
+      L[f] = pk::pair(lane ? nb : (w ? S.wp[w - 1][f] : (f == 0 || f == 2 ? 1.0f : 0.0f)), WP[f].x);
+    }
+    pk::hll(k, L, WM, XM, X, F);                  // faces b + 2t - 1/2 and b + 2t + 1/2
+
+    if (lane == 0) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) S.fl[w][f] = F[f].x;
+    }
+    __syncthreads();
+    f2 FR[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const float nb = __shfl_sync(0xffffffffu, F[f].x, src_p);
+      FR[f] = pk::pair(F[f].y, lane < 31 ? nb : (w < NWT - 1 ? S.fl[w + 1][f] : 0.0f));
+    }
+    const int j = b + 2 * threadIdx.x;            // global index of the even cell
+    if (threadIdx.x >= 1 && threadIdx.x < NTT - 1 && j < N) {
+      f2 Nw[4];
+      pk::update<SRC>(X, F, FR, YE, YEv, dt2, ndtdx2, Nw);
+      const bool two = j + 1 < N;
+      pk::cfl<SRC>(k, Nw, two ? 3 : 1, smax, akey, flags);
+      if (two && (N & 1) == 0) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) *reinterpret_cast<f2*>(Uout + (size_t)f * N + j) = Nw[f];
+      } else {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          Uout[(size_t)f * N + j] = Nw[f].x;
+          if (two) Uout[(size_t)f * N + j + 1] = Nw[f].y;
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  reduce_and_finalize<float, NTT>(ctl, kp, (double)smax, (double)akey, flags, true);
+}
+
+template <int LIM, int SRC>
+struct KT {
+  static constexpr auto fn = tile1d_kernel<LIM, SRC, 3>;
+};
+
+template <int LIM>
+void* pick_src(int src) {
+  switch (src) {
+    case 0: return (void*)KT<LIM, 0>::fn;
+    case 1: return (void*)KT<LIM, 1>::fn;
+    default: return (void*)KT<LIM, 2>::fn;
+  }
+}
+
+void* pick(const KParams& kp) {
+  const int src = kp.frozen ? 0 : (kp.qi_zero ? 1 : 2);
+  switch (kp.limiter) {
+    case 1: return pick_src<1>(src);
+    case 2: return pick_src<2>(src);
+    default: return pick_src<0>(src);
+  }
+}
+
+}  // namespace
+
+// Sets the kernel's shared-memory limit (host side, outside any capture) and
+// returns the persistent grid size (0 on failure).
+int tile1d_grid(const KParams& kp) {
+  int dev = 0, sms = 0, per = 0;
+  const void* fn = pick(kp);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem)) !=
+      cudaSuccess)
+    return 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, NTT, sizeof(TileSmem)) != cudaSuccess)
+    return 0;
+  if (per < 1) per = 1;
+  return sms * per;
+}
+
+cudaError_t tile1d_launch(const KParams& kp, void* a, void* b, Ctl* ctl, int64_t N, int grid,
+                          cudaStream_t st) {
+  if (N >= (1LL << 31) / 4 || N < kTile1dMinCells || grid < 1) return cudaErrorInvalidValue;
+  int n32 = (int)N;
+  void* args[] = {(void*)&kp, &a, &b, &ctl, &n32};
+  return cudaLaunchKernel(pick(kp), dim3(grid), dim3(NTT), args, sizeof(TileSmem), st);
+}
+
+}  // namespace sv
