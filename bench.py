@@ -34,11 +34,12 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s"
 L2_FLUSH_BYTES = 256 << 20
 
-# DRAM bytes (read + write) of one launch of the 1D FP32 step kernel at N = 2^22,
-# from one ncu capture of the current kernel (74.4 MB read + 16.9 MB written
-# during the launch; the remaining writes are still dirty in L2 when it ends).
-# Only valid for that workload and precision; other lines report null.
-TRAFFIC_1D_FP32_N22 = 91.3e6
+# DRAM bytes (read + write) of one launch of the 1D FP32 step kernel at N = 2^22
+# (the block-tile kernel tile1d_kernel), from one ncu capture of the current
+# kernel (67.2 MB read + 18.9 MB written during the launch; the remaining writes
+# are still dirty in L2 when it ends).  Only valid for that workload and
+# precision; other lines report null.
+TRAFFIC_1D_FP32_N22 = 86.1e6
 
 
 def workload(n_cells: int, gamma: float, Ck: float, S: float):

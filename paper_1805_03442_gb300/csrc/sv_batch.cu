@@ -97,6 +97,7 @@ batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns
   __shared__ uint32_t s_f[NTB / 32];
   __shared__ int s_run, s_stop, s_last, s_log;
   __shared__ double s_dt, s_t;
+  __shared__ R s_step[4];               // dt, dt/h, dt/(2h), dt/2 of the next step
   extern __shared__ __align__(16) unsigned char smemb[];   // per-warp rings
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   R* ring = reinterpret_cast<R*>(smemb) + warp * (ring1d_bytes<R>() / sizeof(R));
@@ -107,7 +108,7 @@ batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns
     const int qi = s_run;
     if (qi >= nruns) break;
     RunDev* rd = runs + order[qi];
-    const KParams kp = rd->kp;
+    const KParams& kp = rd->kp;
     const P<R> k(kp);
     const int n = rd->n, stride = rd->stride, mode = rd->mode, src = rd->src;
     const double t_end = rd->t_end;
@@ -163,6 +164,11 @@ batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns
           s_dt = t_end - t;
           s_last = 1;
         }
+        const StepDt<R> sd(s_dt, kp.h);
+        s_step[0] = sd.dt;
+        s_step[1] = sd.dtdx;
+        s_step[2] = sd.dt_2h;
+        s_step[3] = sd.dt_2;
       }
       __syncthreads();
     }
@@ -177,8 +183,7 @@ batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns
     int64_t steps = 0;
     while (!s_stop) {
       const double dtd = s_dt;
-      const StepDt<R> sd(dtd, kp.h);
-      const R dt = sd.dt, dtdx = sd.dtdx, dt_2h = sd.dt_2h, dt_2 = sd.dt_2;
+      const R dt = s_step[0], dtdx = s_step[1], dt_2h = s_step[2], dt_2 = s_step[3];
       const R* Uin = cur ? B : A;
       R* Uout = cur ? A : B;
       R smax = 0, akey = -INFINITY;
@@ -210,6 +215,11 @@ batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns
           s_dt = t_end - t;
           s_last = 1;
         }
+        const StepDt<R> sd(s_dt, kp.h);
+        s_step[0] = sd.dt;
+        s_step[1] = sd.dtdx;
+        s_step[2] = sd.dt_2h;
+        s_step[3] = sd.dt_2;
         s_log = mode > 0 && log_count < log_cap && (t >= next_log || s_stop);
       }
       __syncthreads();
