@@ -40,7 +40,7 @@ heun1d_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
   step1d_warp<R, PP, LIM, SRC, MODE>(k, Uin, Uout, N, N, c0, c1, lane, sd.dt, sd.dtdx, sd.dt_2h,
                                      sd.dt_2, smax, akey, flags, ring, kp, sc.t, Un);
   if (MODE == MODE_HEUN2)
-    reduce_and_finalize<R, NTH>(ctl, kp, (double)smax, (double)akey, flags, true, false);
+    reduce_and_finalize<R, NTH>(ctl, kp, smax, akey, flags, true, false);
 }
 
 template <typename R, int LIM, int SRC, int MODE>

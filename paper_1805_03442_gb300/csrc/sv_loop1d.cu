@@ -88,7 +88,7 @@ loop1d_kernel(const KParams kp, R* bufA, R* bufB, Ctl* ctl, int N, long long nma
     uint32_t flags = 0;
     step1d_warp<R, PP, LIM, SRC>(k, Uin, Uout, N, N, c0, c1, lane, sd.dt, sd.dtdx, sd.dt_2h,
                                  sd.dt_2, smax, akey, flags, ring, kp, sc.t);
-    const bool last = block_arrive<NTL>(ctl, (double)smax, (double)akey, flags);
+    const bool last = block_arrive<NTL, R>(ctl, smax, akey, flags);
     if (threadIdx.x == 0) {
       bool ok = true;
       if (last) {

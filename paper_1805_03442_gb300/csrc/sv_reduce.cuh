@@ -123,12 +123,14 @@ __device__ void finalize(Ctl* ctl, const KParams& kp, bool advance, bool flip = 
 }
 
 // Block-wide fold of (smax, akey, flags) into the control block, then this
-// block's ticket.  Returns, in every thread, whether this block was the last
-// of the launch to arrive.  Must be called by every thread of the block, after
-// its last store.
-template <int NT>
-__device__ __forceinline__ bool block_arrive(Ctl* ctl, double smax, double akey, uint32_t flags) {
-  __shared__ double s_s[NT / 32], s_a[NT / 32];
+// block's ticket.  The fold runs in the kernel's own type T (float kernels
+// stay off the narrow FP64 pipe; widening to double after the maximum gives
+// the same key as before it).  Returns, in every thread, whether this block
+// was the last of the launch to arrive.  Must be called by every thread of
+// the block, after its last store.
+template <int NT, typename T>
+__device__ __forceinline__ bool block_arrive(Ctl* ctl, T smax, T akey, uint32_t flags) {
+  __shared__ T s_s[NT / 32], s_a[NT / 32];
   __shared__ uint32_t s_f[NT / 32];
   __shared__ bool s_last;
 #pragma unroll
@@ -151,8 +153,8 @@ __device__ __forceinline__ bool block_arrive(Ctl* ctl, double smax, double akey,
       akey = fmax(akey, s_a[i]);
       flags |= s_f[i];
     }
-    atomicMax((unsigned long long*)&ctl->smax_key, (unsigned long long)key_of(smax));
-    atomicMax((unsigned long long*)&ctl->tau_key, (unsigned long long)key_of(akey));
+    atomicMax((unsigned long long*)&ctl->smax_key, (unsigned long long)key_of((double)smax));
+    atomicMax((unsigned long long*)&ctl->tau_key, (unsigned long long)key_of((double)akey));
     if (flags) atomicOr(&ctl->flags, flags);
     __threadfence();
     const uint32_t ticket = atomicAdd(&ctl->ticket, 1u);
@@ -164,10 +166,10 @@ __device__ __forceinline__ bool block_arrive(Ctl* ctl, double smax, double akey,
 
 // block_arrive followed by the last block's finalize.
 template <typename R, int NT>
-__device__ __forceinline__ void reduce_and_finalize(Ctl* ctl, const KParams& kp, double smax,
-                                                    double akey, uint32_t flags, bool advance,
+__device__ __forceinline__ void reduce_and_finalize(Ctl* ctl, const KParams& kp, R smax, R akey,
+                                                    uint32_t flags, bool advance,
                                                     bool flip = true) {
-  const bool last = block_arrive<NT>(ctl, smax, akey, flags);
+  const bool last = block_arrive<NT, R>(ctl, smax, akey, flags);
   if (last && threadIdx.x == 0) finalize<R>(ctl, kp, advance, flip);
 }
 

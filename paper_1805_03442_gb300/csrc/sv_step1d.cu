@@ -40,7 +40,7 @@ step1d_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
 
   step1d_warp<R, PP, LIM, SRC>(k, Uin, Uout, N, N, c0, c1, lane, dt, dtdx, dt_2h, dt_2, smax, akey,
                                flags, ring, kp, sc.t);
-  reduce_and_finalize<R, NT1>(ctl, kp, (double)smax, (double)akey, flags, true);
+  reduce_and_finalize<R, NT1>(ctl, kp, smax, akey, flags, true);
 }
 
 // Kernel variants: arithmetic (float / double / float with double pressure),

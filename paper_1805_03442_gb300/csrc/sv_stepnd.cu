@@ -347,7 +347,7 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
     yEv_prev = yEvh;
   }
   cp_async_wait<0>();
-  reduce_and_finalize<R, NT>(ctl, kp, (double)smax, (double)akey, flags, true);
+  reduce_and_finalize<R, NT>(ctl, kp, smax, akey, flags, true);
 }
 
 // ------------------------------------------------------------------ launch

@@ -173,7 +173,7 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
     }
   }
   cp_async_wait<0>();
-  reduce_and_finalize<float, NTT>(ctl, kp, (double)smax, (double)akey, flags, true);
+  reduce_and_finalize<float, NTT>(ctl, kp, smax, akey, flags, true);
 }
 
 template <int LIM, int SRC>

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(NTU) dt_reduce_kernel(const KParams kp, const 
     cfl_cell<R, PP, 1>(k, rho, kin2, vmag, U[(1 + dim) * ncell + i], U[(2 + dim) * ncell + i],
                        smax, akey, flags);
   }
-  reduce_and_finalize<R, NTU>(ctl, kp, (double)smax, (double)akey, flags, false);
+  reduce_and_finalize<R, NTU>(ctl, kp, smax, akey, flags, false);
 }
 
 static int grid_small(int64_t count) {
