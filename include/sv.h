@@ -165,6 +165,40 @@ int sv_set_launch(sv_solver* s, int mode);
    SV_LAUNCH_PERSISTENT; AUTO resolved). */
 int sv_get_launch(sv_solver* s, int* mode);
 
+/* ------------------------------------------------------------------------
+ * Launch configurations and the autotuner.  A solver's per-step kernel comes
+ * in a few launch configurations that compute bitwise the same states and
+ * differ only in speed:
+ *   1D float MUSCL-Hancock, >= 4096 cells: 512-cell block tiles at a register
+ *     budget of 3 blocks/SM (default) or 2 blocks/SM, or warps sliding over
+ *     64-cell chunks (the kernel of every other 1D solver, its only config);
+ *   2D / 3D: planes per block along the marching axis, 64 / 128 / 256 / 512.
+ * sv_autotune times each configuration on the solver's current state and
+ * keeps the fastest; the state, time and status are restored afterwards.
+ * ------------------------------------------------------------------------ */
+
+/* Number of launch configurations of this solver (>= 1). */
+int sv_num_configs(sv_solver* s, int* count);
+
+/* Current configuration index and its description (desc may be NULL;
+   truncated to cap bytes including the terminating zero). */
+int sv_get_config(sv_solver* s, int* index, char* desc, size_t cap);
+
+/* Description of configuration `index`. */
+int sv_config_desc(sv_solver* s, int index, char* desc, size_t cap);
+
+/* Make configuration `index` current (SV_EINVAL if out of range). */
+int sv_set_config(sv_solver* s, int index);
+
+/* Time every configuration over `steps` per-step launches (after 2 warm-up
+   launches) with CUDA events on the solver's stream, restoring the state and
+   control block after each trial, and make the fastest current.  *best
+   (may be NULL) receives its index; us_per_step (may be NULL, else
+   sv_num_configs entries) the microseconds per step of each configuration,
+   +inf where the trial stopped early (t_end reached or a non-physical
+   state).  Synchronous. */
+int sv_autotune(sv_solver* s, int steps, int* best, double* us_per_step);
+
 /* Advance until t_end, the last step clamped to land on t_end, or until
    max_steps steps.  Synchronous.  Returns SV_EMAXSTEPS if stopped early,
    SV_ENONPHYS / SV_EDT if the run failed (the state of the failing step is
@@ -250,6 +284,13 @@ int sv_batch_mode_log(sv_batch* b, int64_t run, double* t, double* re, double* i
                       int64_t* count);
 
 void sv_batch_free(sv_batch* b);
+
+/* Launch configurations of a batch: the block size per run, 256 (default) or
+   128 threads.  Same results, different speed: smaller blocks keep more runs
+   in flight and idle fewer warps on small runs.  Set before sv_batch_run. */
+int sv_batch_num_configs(sv_batch* b, int* count);
+int sv_batch_set_config(sv_batch* b, int index);
+int sv_batch_get_config(sv_batch* b, int* index, char* desc, size_t cap);
 
 /* ------------------------------------------------------------------------
  * Allocation-free 1D step.  The paper has no counterpart: this is a service

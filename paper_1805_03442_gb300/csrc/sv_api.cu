@@ -11,12 +11,21 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "sv.h"
 #include "sv_internal.h"
 #include "sv_model.cuh"
 
 using namespace sv;
+
+// One launch configuration of a solver's per-step kernel (sv_set_config).
+struct SolverConfig {
+  int kind;        // CFG_TILE, CFG_SLIDE or CFG_ND
+  int param;       // TILE: blocks per SM of the register budget; ND: planes per segment
+  const char* desc;
+};
+enum { CFG_TILE = 0, CFG_SLIDE = 1, CFG_ND = 2 };
 
 struct sv_solver {
   sv_params p;
@@ -37,7 +46,9 @@ struct sv_solver {
   Ctl* host_ctl = nullptr;             // pinned mirror of the control block
   double* host_sums = nullptr;
   int grid = 0;
-  int tile_grid = 0;                   // float 1D MUSCL-Hancock on block tiles (0 = not used)
+  int tile_grid = 0;                   // grid of the block-tile kernel of the current config
+  std::vector<SolverConfig> cfgs;      // launch configurations of the per-step kernel
+  int config = 0;                      // current index into cfgs
   int loop_grid = 0;                   // persistent 1D loop: blocks (0 = not available)
   bool loop_fits = false;              // ... at most one 64-cell chunk per SM
   int launch = SV_LAUNCH_AUTO;
@@ -113,12 +124,13 @@ cudaError_t launch_step(sv_solver* s, cudaStream_t st) {
     return heun1d_launch(s->p.precision, 2, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell, s->grid,
                          st);
   }
-  if (s->dim == 1 && s->tile_grid > 0)
-    return tile1d_launch(s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell, s->tile_grid, st);
-  if (s->dim == 1)
+  const SolverConfig& c = s->cfgs[(size_t)s->config];
+  if (c.kind == CFG_TILE)
+    return tile1d_launch(s->kp, c.param, s->buf[0], s->buf[1], s->ctl, s->ncell, s->tile_grid, st);
+  if (c.kind == CFG_SLIDE)
     return step1d_launch(s->p.precision, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell, s->grid, st);
   return stepnd_launch(s->dim, s->p.precision, s->kp, s->buf[0], s->buf[1], s->ctl, s->g.n,
-                       s->grid, st);
+                       c.param, st);
 }
 
 int ensure_graph(sv_solver* s) {
@@ -150,6 +162,52 @@ int ensure_graph(sv_solver* s) {
 bool use_loop(const sv_solver* s) {
   if (s->loop_grid < 1) return false;
   return s->launch == SV_LAUNCH_PERSISTENT || (s->launch == SV_LAUNCH_AUTO && s->loop_fits);
+}
+
+// Launch configurations a solver can choose from, the default first.
+const char* seg_desc(int seg) {
+  switch (seg) {
+    case 64: return "2D/3D: marching segments of 64 planes per block";
+    case 128: return "2D/3D: marching segments of 128 planes per block";
+    case 256: return "2D/3D: marching segments of 256 planes per block";
+    default: return "2D/3D: marching segments of 512 planes per block";
+  }
+}
+
+void build_configs(sv_solver* s) {
+  s->cfgs.clear();
+  if (s->dim == 1) {
+    if (s->p.method == SV_HANCOCK && s->p.precision == SV_FP32 && s->ncell >= kTile1dMinCells) {
+      s->cfgs.push_back({CFG_TILE, 3,
+                         "1D: 512-cell block tiles, 2 cells per thread, 80 registers, 3 blocks/SM"});
+      s->cfgs.push_back({CFG_TILE, 2, "1D: 512-cell block tiles, 2 cells per thread, 2 blocks/SM"});
+    }
+    s->cfgs.push_back({CFG_SLIDE, 0, "1D: warps sliding over 64-cell chunks, 2 cells per thread"});
+  } else {
+    const int d = stepnd_default_seg(s->dim, s->p.precision);
+    s->cfgs.push_back({CFG_ND, d, seg_desc(d)});
+    for (int seg : {64, 128, 256, 512})
+      if (seg != d) s->cfgs.push_back({CFG_ND, seg, seg_desc(seg)});
+  }
+}
+
+// Make configuration idx current (host side, outside any capture); the
+// captured step graph holds the old kernel, so it is dropped.
+int apply_config(sv_solver* s, int idx) {
+  const SolverConfig& c = s->cfgs[(size_t)idx];
+  int tg = 0;
+  if (c.kind == CFG_TILE) {
+    tg = tile1d_grid(s->kp, c.param);
+    if (tg < 1) return SV_ECUDA;
+  }
+  if (s->graph) {
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return SV_ECUDA;
+    cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+  }
+  s->config = idx;
+  s->tile_grid = tg;
+  return SV_OK;
 }
 
 int issue_steps(sv_solver* s, int64_t n) {
@@ -278,10 +336,9 @@ int sv_init(const sv_params* p, const sv_grid* g, void* cuda_stream, void* devic
                           : stepnd_grid(s->dim, p->precision, s->kp);
     if (s->grid < 1) rc = SV_ECUDA;
   }
-  if (rc == SV_OK && s->dim == 1 && p->method == SV_HANCOCK && p->precision == SV_FP32 &&
-      s->ncell >= kTile1dMinCells) {
-    s->tile_grid = tile1d_grid(s->kp);
-    if (s->tile_grid < 1) rc = SV_ECUDA;
+  if (rc == SV_OK) {
+    build_configs(s);
+    rc = apply_config(s, 0);
   }
   if (rc == SV_OK && s->dim == 1 && p->method == SV_HANCOCK) {
     // 0 where the device has no cooperative launch: the per-step path remains
@@ -383,6 +440,97 @@ int sv_run_to(sv_solver* s, double t_end, int64_t max_steps, int64_t* steps_take
   // clear the target so that later sv_step calls are not clamped
   SV_TRY(set_target_launch(s->ctl, INFINITY, s->h, s->stream));
   return status;
+}
+
+int sv_num_configs(sv_solver* s, int* count) {
+  if (!s || !count) return SV_EINVAL;
+  *count = (int)s->cfgs.size();
+  return SV_OK;
+}
+
+int sv_get_config(sv_solver* s, int* index, char* desc, size_t cap) {
+  if (!s) return SV_EINVAL;
+  if (index) *index = s->config;
+  if (desc && cap > 0) {
+    strncpy(desc, s->cfgs[(size_t)s->config].desc, cap - 1);
+    desc[cap - 1] = 0;
+  }
+  return SV_OK;
+}
+
+int sv_config_desc(sv_solver* s, int index, char* desc, size_t cap) {
+  if (!s || !desc || cap == 0 || index < 0 || index >= (int)s->cfgs.size()) return SV_EINVAL;
+  strncpy(desc, s->cfgs[(size_t)index].desc, cap - 1);
+  desc[cap - 1] = 0;
+  return SV_OK;
+}
+
+int sv_set_config(sv_solver* s, int index) {
+  if (!s || index < 0 || index >= (int)s->cfgs.size()) return SV_EINVAL;
+  return apply_config(s, index);
+}
+
+int sv_autotune(sv_solver* s, int steps, int* best, double* us_per_step) {
+  if (!s || steps < 1) return SV_EINVAL;
+  const int ncfg = (int)s->cfgs.size();
+  const size_t count = (size_t)s->nf * (size_t)s->ncell;
+  // keep the state (exactly: float -> double -> float is lossless) and the
+  // control block; every trial is undone before the next one
+  Ctl saved;
+  SV_TRY(from_state_launch(s->p.precision, s->buf[0], s->buf[1], s->ctl, s->staging,
+                           (int64_t)count, s->stream));
+  SV_TRY(cudaMemcpyAsync(&saved, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
+  SV_TRY(cudaStreamSynchronize(s->stream));
+  auto restore = [&]() -> int {
+    SV_TRY(cudaMemcpyAsync(s->ctl, &saved, sizeof(Ctl), cudaMemcpyHostToDevice, s->stream));
+    SV_TRY(to_state_launch(s->p.precision, s->staging, s->buf[0], s->buf[1], s->ctl,
+                           (int64_t)count, s->stream));
+    SV_TRY(cudaStreamSynchronize(s->stream));
+    return SV_OK;
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return SV_ECUDA;
+  }
+  const int warm = 2;
+  const int start = s->config;
+  int pick = start, rc = SV_OK;
+  double best_us = INFINITY;
+  for (int c = 0; c < ncfg && rc == SV_OK; ++c) {
+    double us = INFINITY;
+    rc = apply_config(s, c);
+    for (int i = 0; i < warm && rc == SV_OK; ++i)
+      if (launch_step(s, s->stream) != cudaSuccess) rc = SV_ECUDA;
+    if (rc == SV_OK && cudaEventRecord(e0, s->stream) != cudaSuccess) rc = SV_ECUDA;
+    for (int i = 0; i < steps && rc == SV_OK; ++i)
+      if (launch_step(s, s->stream) != cudaSuccess) rc = SV_ECUDA;
+    if (rc == SV_OK && (cudaEventRecord(e1, s->stream) != cudaSuccess ||
+                        cudaEventSynchronize(e1) != cudaSuccess))
+      rc = SV_ECUDA;
+    if (rc == SV_OK) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = SV_ECUDA;
+      // a trial whose steps stopped (t_end reached, non-physical state) timed
+      // nothing useful
+      if (rc == SV_OK) rc = read_ctl(s);
+      if (rc == SV_OK && s->host_ctl->flags == 0 && s->host_ctl->nsteps == saved.nsteps + warm + steps)
+        us = 1e3 * (double)ms / steps;
+    }
+    if (us_per_step) us_per_step[c] = us;
+    if (us < best_us) {
+      best_us = us;
+      pick = c;
+    }
+    const int rr = restore();
+    if (rc == SV_OK) rc = rr;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const int ra = apply_config(s, rc == SV_OK ? pick : start);
+  if (rc == SV_OK) rc = ra;
+  if (best) *best = s->config;
+  return rc;
 }
 
 int sv_set_launch(sv_solver* s, int mode) {

@@ -20,246 +20,12 @@
 #include <numeric>
 #include <vector>
 
-#include "sv.h"
-#include "sv_internal.h"
-#include "sv_step1d.cuh"
+#include "sv_batch_kernel.cuh"
 
 namespace sv {
 
-constexpr int NTB = 256;
-
-struct RunDev {
-  KParams kp;            // per-run parameters (h = L / n)
-  int64_t off;           // element offset of the run's block (4 fields x stride)
-  int n, stride, mode, log_count;
-  int src, pad2;         // source variant of the run (as a single solver would pick it)
-  double t, t_end;
-  int64_t steps;
-  uint32_t flags, cur, pad0, pad1;
-};
-
-constexpr uint32_t FLAG_MAXSTEPS = SV_FLAG_MAXSTEPS;
-
-template <typename R>
-__device__ __forceinline__ void block_max(R& smax, R& akey, uint32_t& flags, R* s_a, R* s_b,
-                                          uint32_t* s_f) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-    akey = fmax(akey, __shfl_xor_sync(0xffffffffu, akey, o));
-    flags |= __shfl_xor_sync(0xffffffffu, flags, o);
-  }
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    s_a[w] = smax;
-    s_b[w] = akey;
-    s_f[w] = flags;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (int i = 1; i < NTB / 32; ++i) {
-      smax = fmax(smax, s_a[i]);
-      akey = fmax(akey, s_b[i]);
-      flags |= s_f[i];
-    }
-}
-
-template <typename R>
-__device__ __forceinline__ void block_sum2(R& a, R& b, R* s_a, R* s_b) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-  }
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    s_a[w] = a;
-    s_b[w] = b;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (int i = 1; i < NTB / 32; ++i) {
-      a += s_a[i];
-      b += s_b[i];
-    }
-}
-
-// Every run is stepped with the source variant a single 1D solver with the
-// same parameters would use (none in the frozen limit, pump = sink for zero
-// exponents, general otherwise), chosen per run at run time, so that a batched
-// run and a looped solver run execute the same instructions.
-template <typename R, int PP, int LIM, int MINB>
-__global__ void __launch_bounds__(NTB, MINB)
-batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns,
-             int* __restrict__ queue, R* __restrict__ bufA, R* __restrict__ bufB,
-             double* __restrict__ logs, int log_cap, int64_t max_steps) {
-  __shared__ R s_a[NTB / 32], s_b[NTB / 32];
-  __shared__ uint32_t s_f[NTB / 32];
-  __shared__ int s_run, s_stop, s_last, s_log;
-  __shared__ double s_dt, s_t;
-  __shared__ R s_step[4];               // dt, dt/h, dt/(2h), dt/2 of the next step
-  extern __shared__ __align__(16) unsigned char smemb[];   // per-warp rings
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  R* ring = reinterpret_cast<R*>(smemb) + warp * (ring1d_bytes<R>() / sizeof(R));
-
-  for (;;) {
-    if (threadIdx.x == 0) s_run = atomicAdd(queue, 1);
-    __syncthreads();
-    const int qi = s_run;
-    if (qi >= nruns) break;
-    RunDev* rd = runs + order[qi];
-    const KParams& kp = rd->kp;
-    const P<R> k(kp);
-    const int n = rd->n, stride = rd->stride, mode = rd->mode, src = rd->src;
-    const double t_end = rd->t_end;
-    R* A = bufA + rd->off;
-    R* B = bufB + rd->off;
-    const int nchunk = (n + 63) / 64;
-    const int c0 = warp * nchunk / (NTB / 32), c1 = (warp + 1) * nchunk / (NTB / 32);
-    double* lg = logs + (int64_t)(order[qi]) * log_cap * 3;
-    const double log_dt = log_cap > 1 ? t_end / (double)(log_cap - 1) : INFINITY;
-
-    // logging of a_m at the current state (buffer U)
-    auto log_mode = [&](const R* U, double t, int slot) {
-      R re = 0, im = 0;
-      for (int j = threadIdx.x; j < n; j += NTB) {
-        const R v = U[stride + j] / U[j];
-        R sn, cs;
-        const R ph = (R)(2.0 * mode) * ((R)j + (R)0.5) / (R)n;
-        if constexpr (sizeof(R) == 4) sincospif(ph, &sn, &cs);
-        else sincospi(ph, &sn, &cs);
-        re += v * cs;
-        im -= v * sn;
-      }
-      block_sum2(re, im, s_a, s_b);
-      if (threadIdx.x == 0) {
-        lg[3 * slot + 0] = t;
-        lg[3 * slot + 1] = (double)re / n;
-        lg[3 * slot + 2] = (double)im / n;
-      }
-      __syncthreads();
-    };
-
-    // dt of the initial state (same per-cell bound as every step)
-    {
-      R smax = 0, akey = -INFINITY;
-      uint32_t flags = 0;
-      for (int j = threadIdx.x; j < n; j += NTB) {
-        const R rho = A[j], m = A[stride + j];
-        const R ir = Ar<R>::rcp(rho);
-        const R v = m * ir;
-        cfl_cell<R, PP, 1>(k, rho, m * v, fabs(m * ir), A[2 * stride + j], A[3 * stride + j], smax,
-                           akey, flags);
-      }
-      block_max(smax, akey, flags, s_a, s_b, s_f);
-      if (threadIdx.x == 0) {
-        const double dt = dt_from_maxima<R>(kp, (double)smax, (double)akey, flags);
-        double t = rd->t;
-        rd->flags = flags;
-        s_t = t;
-        s_stop = flags != 0 || !(t < t_end);
-        s_last = 0;
-        s_dt = dt;
-        if (!s_stop && dt >= t_end - t) {
-          s_dt = t_end - t;
-          s_last = 1;
-        }
-        const StepDt<R> sd(s_dt, kp.h);
-        s_step[0] = sd.dt;
-        s_step[1] = sd.dtdx;
-        s_step[2] = sd.dt_2h;
-        s_step[3] = sd.dt_2;
-      }
-      __syncthreads();
-    }
-    int log_count = 0;
-    double next_log = s_t;
-    if (mode > 0 && log_cap > 0) {
-      log_mode(A, s_t, 0);
-      log_count = 1;
-      next_log = s_t + log_dt;
-    }
-    uint32_t cur = 0;
-    int64_t steps = 0;
-    while (!s_stop) {
-      const double dtd = s_dt;
-      const R dt = s_step[0], dtdx = s_step[1], dt_2h = s_step[2], dt_2 = s_step[3];
-      const R* Uin = cur ? B : A;
-      R* Uout = cur ? A : B;
-      R smax = 0, akey = -INFINITY;
-      uint32_t flags = 0;
-      if (src == 0)
-        step1d_warp<R, PP, LIM, 0>(k, Uin, Uout, n, stride, c0, c1, lane, dt, dtdx, dt_2h, dt_2,
-                                   smax, akey, flags, ring, kp, s_t);
-      else if (src == 1)
-        step1d_warp<R, PP, LIM, 1>(k, Uin, Uout, n, stride, c0, c1, lane, dt, dtdx, dt_2h, dt_2,
-                                   smax, akey, flags, ring, kp, s_t);
-      else
-        step1d_warp<R, PP, LIM, 2>(k, Uin, Uout, n, stride, c0, c1, lane, dt, dtdx, dt_2h, dt_2,
-                                   smax, akey, flags, ring, kp, s_t);
-      // the barrier inside block_max also orders this step's stores before the
-      // next step's loads of neighbouring warps' cells
-      block_max(smax, akey, flags, s_a, s_b, s_f);
-      cur ^= 1u;
-      ++steps;
-      if (threadIdx.x == 0) {
-        const double dt_next = dt_from_maxima<R>(kp, (double)smax, (double)akey, flags);
-        const double t = s_last ? t_end : s_t + dtd;
-        s_t = t;
-        if (steps >= max_steps && t < t_end) flags |= FLAG_MAXSTEPS;
-        rd->flags = flags;
-        s_stop = flags != 0 || !(t < t_end);
-        s_last = 0;
-        s_dt = dt_next;
-        if (!s_stop && dt_next >= t_end - t) {
-          s_dt = t_end - t;
-          s_last = 1;
-        }
-        const StepDt<R> sd(s_dt, kp.h);
-        s_step[0] = sd.dt;
-        s_step[1] = sd.dtdx;
-        s_step[2] = sd.dt_2h;
-        s_step[3] = sd.dt_2;
-        s_log = mode > 0 && log_count < log_cap && (t >= next_log || s_stop);
-      }
-      __syncthreads();
-      if (s_log) {
-        log_mode(cur ? B : A, s_t, log_count);
-        ++log_count;
-        while (next_log <= s_t) next_log += log_dt;
-      }
-    }
-    if (threadIdx.x == 0) {
-      rd->t = s_t;
-      rd->steps = steps;
-      rd->cur = cur;
-      rd->log_count = log_count;
-    }
-    __syncthreads();
-  }
-}
-
-template <typename R, int PP, int LIM>
-struct KB {
-  static constexpr int MINB = sizeof(R) == 8 ? 1 : 2;
-  static constexpr auto fn = batch_kernel<R, PP, LIM, MINB>;
-};
-
-template <int LIM>
-static void* bpick_prec(int precision) {
-  switch (precision) {
-    case PREC_FP64: return (void*)KB<double, 0, LIM>::fn;
-    case PREC_FP32_P64: return (void*)KB<float, 1, LIM>::fn;
-    default: return (void*)KB<float, 0, LIM>::fn;
-  }
-}
-static void* bpick(int limiter, int precision) {
-  switch (limiter) {
-    case 1: return bpick_prec<1>(precision);
-    case 2: return bpick_prec<2>(precision);
-    default: return bpick_prec<0>(precision);
-  }
-}
+// Kernels of the two block sizes: 256 threads here, 128 in sv_batch128.cu.
+void* batch_pick256(int limiter, int precision) { return bpick<256>(limiter, precision); }
 
 }  // namespace sv
 
@@ -282,6 +48,8 @@ struct sv_batch {
   std::vector<int64_t> n;
   int64_t total_elems = 0;
   int grid = 0;
+  int nt = 256;                       // threads per run (block size)
+  int config = 0;                     // index into kBatchConfigs
   void* fn = nullptr;
   cudaGraphExec_t graph = nullptr;
   int64_t max_steps = 0;
@@ -364,8 +132,48 @@ int upload(sv_batch* b, const double* host) {
   return cudaStreamSynchronize(b->stream) == cudaSuccess ? SV_OK : SV_ECUDA;
 }
 
-size_t batch_smem(int precision) {
-  return (size_t)(NTB / 32) * (precision == SV_FP64 ? ring1d_bytes<double>() : ring1d_bytes<float>());
+// Launch configurations of the batch kernel (sv_batch_set_config): block size
+// per run.  Smaller blocks keep more runs in flight and idle fewer warps on
+// small runs; larger ones finish each run sooner.
+struct BatchConfig {
+  int nt;
+  const char* desc;
+};
+constexpr BatchConfig kBatchConfigs[] = {
+    {256, "batch: 256 threads (8 warps) per run, 64-cell chunks, 2 cells per thread"},
+    {128, "batch: 128 threads (4 warps) per run, 64-cell chunks, 2 cells per thread"},
+};
+constexpr int kNumBatchConfigs = (int)(sizeof(kBatchConfigs) / sizeof(kBatchConfigs[0]));
+
+size_t batch_smem(int precision, int nt) {
+  return (size_t)(nt / 32) * (precision == SV_FP64 ? ring1d_bytes<double>() : ring1d_bytes<float>());
+}
+
+// Pick the kernel of configuration c, set its shared-memory limit and the
+// persistent grid (host side, outside any capture).
+int apply_config(sv_batch* b, int c) {
+  const int nt = kBatchConfigs[c].nt;
+  void* fn = nt == 128 ? batch_pick128(b->p.limiter, b->p.precision)
+                       : batch_pick256(b->p.limiter, b->p.precision);
+  int dev = 0, sms = 0, per = 0;
+  const size_t smem = batch_smem(b->p.precision, nt);
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, nt, smem) != cudaSuccess)
+    return SV_ECUDA;
+  if (b->graph) {
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return SV_ECUDA;
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->fn = fn;
+  b->nt = nt;
+  b->config = c;
+  b->grid = sms * (per < 1 ? 1 : per);
+  if ((int64_t)b->grid > b->nruns) b->grid = (int)b->nruns;
+  return SV_OK;
 }
 
 cudaError_t launch_batch(sv_batch* b, cudaStream_t st) {
@@ -375,7 +183,8 @@ cudaError_t launch_batch(sv_batch* b, cudaStream_t st) {
   int lc = b->log_cap;
   int64_t ms = b->max_steps;
   void* args[] = {&b->runs, &b->order, &nr, &b->queue, &b->buf[0], &b->buf[1], &b->logs, &lc, &ms};
-  return cudaLaunchKernel(b->fn, dim3(b->grid), dim3(NTB), args, batch_smem(b->p.precision), st);
+  return cudaLaunchKernel(b->fn, dim3(b->grid), dim3(b->nt), args, batch_smem(b->p.precision, b->nt),
+                          st);
 }
 
 int read_runs(sv_batch* b) {
@@ -454,7 +263,6 @@ int sv_batch_init(const sv_params* p, const sv_run* runs, int64_t nruns,
     off += 4 * stride_of(r.n);
   }
   b->total_elems = off;
-  b->fn = bpick(p->limiter, p->precision);
 
   if (device_mem) b->mem = device_mem;
   else {
@@ -481,22 +289,12 @@ int sv_batch_init(const sv_params* p, const sv_run* runs, int64_t nruns,
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
 
   rc = SV_OK;
-  int dev = 0, sms = 0, per = 0;
   if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaFuncSetAttribute(b->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)batch_smem(p->precision)) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, b->fn, NTB, batch_smem(p->precision)) !=
-          cudaSuccess ||
       cudaMemcpyAsync(b->order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice,
                       b->stream) != cudaSuccess)
     rc = SV_ECUDA;
-  if (rc == SV_OK) {
-    b->grid = sms * (per < 1 ? 1 : per);
-    if ((int64_t)b->grid > nruns) b->grid = (int)nruns;
-    rc = upload(b, host_states);
-  }
+  if (rc == SV_OK) rc = apply_config(b, 0);
+  if (rc == SV_OK) rc = upload(b, host_states);
   if (rc != SV_OK) {
     sv_batch_free(b);
     return rc;
@@ -585,6 +383,27 @@ int sv_batch_mode_log(sv_batch* b, int64_t run, double* t, double* re, double* i
       if (re) re[i] = tmp[(size_t)(3 * i + 1)];
       if (im) im[i] = tmp[(size_t)(3 * i + 2)];
     }
+  }
+  return SV_OK;
+}
+
+int sv_batch_num_configs(sv_batch* b, int* count) {
+  if (!b || !count) return SV_EINVAL;
+  *count = kNumBatchConfigs;
+  return SV_OK;
+}
+
+int sv_batch_set_config(sv_batch* b, int index) {
+  if (!b || index < 0 || index >= kNumBatchConfigs) return SV_EINVAL;
+  return apply_config(b, index);
+}
+
+int sv_batch_get_config(sv_batch* b, int* index, char* desc, size_t cap) {
+  if (!b) return SV_EINVAL;
+  if (index) *index = b->config;
+  if (desc && cap > 0) {
+    strncpy(desc, kBatchConfigs[b->config].desc, cap - 1);
+    desc[cap - 1] = 0;
   }
   return SV_OK;
 }

@@ -20,9 +20,10 @@ cudaError_t step1d_launch(int precision, const KParams& kp, void* a, void* b, Ct
 // Float 1D MUSCL-Hancock step on block tiles (sv_tile1d.cu), grids of at
 // least kTile1dMinCells cells
 constexpr int64_t kTile1dMinCells = 4096;
-int tile1d_grid(const KParams& kp);
-cudaError_t tile1d_launch(const KParams& kp, void* a, void* b, Ctl* ctl, int64_t N, int grid,
-                          cudaStream_t st);
+// minb: register budget in blocks per SM (3 or 2)
+int tile1d_grid(const KParams& kp, int minb);
+cudaError_t tile1d_launch(const KParams& kp, int minb, void* a, void* b, Ctl* ctl, int64_t N,
+                          int grid, cudaStream_t st);
 
 // 1D persistent loop of up to nmax steps (sv_loop1d.cu); grid 0 = unavailable
 int loop1d_grid(const KParams& kp, int precision, int64_t N, int* cap);
@@ -34,10 +35,16 @@ int heun1d_grid(const KParams& kp, int precision);
 cudaError_t heun1d_launch(int precision, int stage, const KParams& kp, void* a, void* b, Ctl* ctl,
                           int64_t N, int grid, cudaStream_t st);
 
-// 2D / 3D fused steps (sv_stepnd.cu); n[] cells per axis
+// 2D / 3D fused steps (sv_stepnd.cu); n[] cells per axis; seg = planes per
+// block along the marching axis (0: default)
 int stepnd_grid(int dim, int precision, const KParams& kp);
+int stepnd_default_seg(int dim, int precision);
 cudaError_t stepnd_launch(int dim, int precision, const KParams& kp, void* a, void* b, Ctl* ctl,
-                          const int64_t* n, int grid, cudaStream_t st);
+                          const int64_t* n, int seg, cudaStream_t st);
+
+// Batched sweep kernels of 256 (sv_batch.cu) and 128 (sv_batch128.cu) threads
+void* batch_pick256(int limiter, int precision);
+void* batch_pick128(int limiter, int precision);
 
 // Utility kernels (sv_util.cu)
 cudaError_t ctl_reset_launch(Ctl* ctl, double t, cudaStream_t st);

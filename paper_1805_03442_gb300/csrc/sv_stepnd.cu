@@ -361,10 +361,12 @@ template <> struct Cfg<3, PREC_FP32_P64> { static constexpr int TX = 32, TY = 16
 template <> struct Cfg<3, PREC_FP64> { static constexpr int TX = 32, TY = 8, MINB = 1, SEG = 128; };
 
 // With `n` null only the kernel's shared-memory attribute is set (done once per
-// solver at init, outside any stream capture).
+// solver at init, outside any stream capture).  `seg` = planes per block along
+// the marching axis (0: the default of Cfg); each segment pays a warm-up of
+// two planes, shorter segments give more blocks.
 template <typename R, int PP, int LIM, int SRC, int DIM, int PREC>
 static cudaError_t launch_nd(const KParams& kp, void* a, void* b, Ctl* ctl, const int64_t* n,
-                            cudaStream_t st) {
+                            int seg, cudaStream_t st) {
   using G = Cfg<DIM, PREC>;
   constexpr size_t smem = stepnd_smem<R, DIM, G::TX, G::TY>();
   auto fn = stepnd_kernel<R, PP, LIM, SRC, DIM, G::TX, G::TY, G::MINB>;
@@ -373,7 +375,10 @@ static cudaError_t launch_nd(const KParams& kp, void* a, void* b, Ctl* ctl, cons
   const int tiles_x = (int)((nx + G::TX - 3) / (G::TX - 2));
   const int tiles_y = DIM == 3 ? (int)((ny + G::TY - 3) / (G::TY - 2)) : 1;
   const int64_t M = DIM == 3 ? nz : ny;
-  int nseg = (int)((M + G::SEG - 1) / G::SEG);
+  const int64_t sl = seg > 0 ? seg : G::SEG;
+  int64_t nseg64 = (M + sl - 1) / sl;
+  if (nseg64 > M) nseg64 = M;
+  int nseg = (int)nseg64;
   if (nseg < 1) nseg = 1;
   const int64_t blocks = (int64_t)tiles_x * tiles_y * nseg;
   if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
@@ -384,46 +389,52 @@ static cudaError_t launch_nd(const KParams& kp, void* a, void* b, Ctl* ctl, cons
 
 template <int LIM, int SRC, int DIM>
 static cudaError_t by_prec(int precision, const KParams& kp, void* a, void* b, Ctl* ctl,
-                           const int64_t* n, cudaStream_t st) {
+                           const int64_t* n, int seg, cudaStream_t st) {
   switch (precision) {
-    case PREC_FP64: return launch_nd<double, 0, LIM, SRC, DIM, PREC_FP64>(kp, a, b, ctl, n, st);
-    case PREC_FP32_P64: return launch_nd<float, 1, LIM, SRC, DIM, PREC_FP32_P64>(kp, a, b, ctl, n, st);
-    default: return launch_nd<float, 0, LIM, SRC, DIM, PREC_FP32>(kp, a, b, ctl, n, st);
+    case PREC_FP64: return launch_nd<double, 0, LIM, SRC, DIM, PREC_FP64>(kp, a, b, ctl, n, seg, st);
+    case PREC_FP32_P64: return launch_nd<float, 1, LIM, SRC, DIM, PREC_FP32_P64>(kp, a, b, ctl, n, seg, st);
+    default: return launch_nd<float, 0, LIM, SRC, DIM, PREC_FP32>(kp, a, b, ctl, n, seg, st);
   }
 }
 
 template <int LIM, int DIM>
 static cudaError_t by_src(int precision, const KParams& kp, void* a, void* b, Ctl* ctl,
-                          const int64_t* n, cudaStream_t st) {
-  if (kp.frozen) return by_prec<LIM, 0, DIM>(precision, kp, a, b, ctl, n, st);
-  if (kp.qi_zero) return by_prec<LIM, 1, DIM>(precision, kp, a, b, ctl, n, st);
-  return by_prec<LIM, 2, DIM>(precision, kp, a, b, ctl, n, st);
+                          const int64_t* n, int seg, cudaStream_t st) {
+  if (kp.frozen) return by_prec<LIM, 0, DIM>(precision, kp, a, b, ctl, n, seg, st);
+  if (kp.qi_zero) return by_prec<LIM, 1, DIM>(precision, kp, a, b, ctl, n, seg, st);
+  return by_prec<LIM, 2, DIM>(precision, kp, a, b, ctl, n, seg, st);
 }
 
 template <int DIM>
 static cudaError_t by_lim(int precision, const KParams& kp, void* a, void* b, Ctl* ctl,
-                          const int64_t* n, cudaStream_t st) {
+                          const int64_t* n, int seg, cudaStream_t st) {
   switch (kp.limiter) {
-    case 1: return by_src<1, DIM>(precision, kp, a, b, ctl, n, st);
-    case 2: return by_src<2, DIM>(precision, kp, a, b, ctl, n, st);
-    default: return by_src<0, DIM>(precision, kp, a, b, ctl, n, st);
+    case 1: return by_src<1, DIM>(precision, kp, a, b, ctl, n, seg, st);
+    case 2: return by_src<2, DIM>(precision, kp, a, b, ctl, n, seg, st);
+    default: return by_src<0, DIM>(precision, kp, a, b, ctl, n, seg, st);
   }
+}
+
+// Default planes per block segment along the marching axis.
+int stepnd_default_seg(int dim, int precision) {
+  if (dim == 2) return precision == PREC_FP64 ? Cfg<2, PREC_FP64>::SEG : Cfg<2, PREC_FP32>::SEG;
+  return precision == PREC_FP64 ? Cfg<3, PREC_FP64>::SEG : Cfg<3, PREC_FP32>::SEG;
 }
 
 int stepnd_grid(int dim, int precision, const KParams& kp) {
   cudaError_t e = cudaErrorInvalidValue;
-  if (dim == 2) e = by_lim<2>(precision, kp, nullptr, nullptr, nullptr, nullptr, nullptr);
-  if (dim == 3) e = by_lim<3>(precision, kp, nullptr, nullptr, nullptr, nullptr, nullptr);
+  if (dim == 2) e = by_lim<2>(precision, kp, nullptr, nullptr, nullptr, nullptr, 0, nullptr);
+  if (dim == 3) e = by_lim<3>(precision, kp, nullptr, nullptr, nullptr, nullptr, 0, nullptr);
   return e == cudaSuccess ? 1 : 0;
 }
 
 cudaError_t stepnd_launch(int dim, int precision, const KParams& kp, void* a, void* b, Ctl* ctl,
-                          const int64_t* n, int, cudaStream_t st) {
+                          const int64_t* n, int seg, cudaStream_t st) {
   if (!n) return cudaErrorInvalidValue;
   int64_t ncell = n[0] * n[1] * (dim == 3 ? n[2] : 1);
   if (ncell * (dim + 3) >= (1LL << 31)) return cudaErrorInvalidValue;
-  if (dim == 2) return by_lim<2>(precision, kp, a, b, ctl, n, st);
-  if (dim == 3) return by_lim<3>(precision, kp, a, b, ctl, n, st);
+  if (dim == 2) return by_lim<2>(precision, kp, a, b, ctl, n, seg, st);
+  if (dim == 3) return by_lim<3>(precision, kp, a, b, ctl, n, seg, st);
   return cudaErrorInvalidValue;
 }
 

@@ -176,36 +176,45 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
   reduce_and_finalize<float, NTT>(ctl, kp, smax, akey, flags, true);
 }
 
+// Register budgets: MINB 3 blocks per SM caps the kernel at 80 registers
+// (24 warps per SM), MINB 2 leaves it its natural ~94 (16 warps per SM).
 template <int LIM, int SRC>
 struct KT {
-  static constexpr auto fn = tile1d_kernel<LIM, SRC, 3>;
+  static constexpr auto fn3 = tile1d_kernel<LIM, SRC, 3>;
+  static constexpr auto fn2 = tile1d_kernel<LIM, SRC, 2>;
 };
 
+template <int LIM, int SRC>
+void* pick_minb(int minb) {
+  return minb == 2 ? (void*)KT<LIM, SRC>::fn2 : (void*)KT<LIM, SRC>::fn3;
+}
+
 template <int LIM>
-void* pick_src(int src) {
+void* pick_src(int src, int minb) {
   switch (src) {
-    case 0: return (void*)KT<LIM, 0>::fn;
-    case 1: return (void*)KT<LIM, 1>::fn;
-    default: return (void*)KT<LIM, 2>::fn;
+    case 0: return pick_minb<LIM, 0>(minb);
+    case 1: return pick_minb<LIM, 1>(minb);
+    default: return pick_minb<LIM, 2>(minb);
   }
 }
 
-void* pick(const KParams& kp) {
+void* pick(const KParams& kp, int minb) {
   const int src = kp.frozen ? 0 : (kp.qi_zero ? 1 : 2);
   switch (kp.limiter) {
-    case 1: return pick_src<1>(src);
-    case 2: return pick_src<2>(src);
-    default: return pick_src<0>(src);
+    case 1: return pick_src<1>(src, minb);
+    case 2: return pick_src<2>(src, minb);
+    default: return pick_src<0>(src, minb);
   }
 }
 
 }  // namespace
 
 // Sets the kernel's shared-memory limit (host side, outside any capture) and
-// returns the persistent grid size (0 on failure).
-int tile1d_grid(const KParams& kp) {
+// returns the persistent grid size for the register budget `minb` (blocks per
+// SM: 3 or 2), 0 on failure.
+int tile1d_grid(const KParams& kp, int minb) {
   int dev = 0, sms = 0, per = 0;
-  const void* fn = pick(kp);
+  const void* fn = pick(kp, minb);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem)) !=
       cudaSuccess)
     return 0;
@@ -217,12 +226,12 @@ int tile1d_grid(const KParams& kp) {
   return sms * per;
 }
 
-cudaError_t tile1d_launch(const KParams& kp, void* a, void* b, Ctl* ctl, int64_t N, int grid,
-                          cudaStream_t st) {
+cudaError_t tile1d_launch(const KParams& kp, int minb, void* a, void* b, Ctl* ctl, int64_t N,
+                          int grid, cudaStream_t st) {
   if (N >= (1LL << 31) / 4 || N < kTile1dMinCells || grid < 1) return cudaErrorInvalidValue;
   int n32 = (int)N;
   void* args[] = {(void*)&kp, &a, &b, &ctl, &n32};
-  return cudaLaunchKernel(pick(kp), dim3(grid), dim3(NTT), args, sizeof(TileSmem), st);
+  return cudaLaunchKernel(pick(kp, minb), dim3(grid), dim3(NTT), args, sizeof(TileSmem), st);
 }
 
 }  // namespace sv

@@ -32,7 +32,9 @@ EXPORTS = ("sv_required_bytes", "sv_init", "sv_write_state", "sv_read_state", "s
            "sv_state_device", "sv_free", "sv_strerror", "sv_batch_required_bytes",
            "sv_batch_init", "sv_batch_reset", "sv_batch_run", "sv_batch_sync", "sv_batch_read",
            "sv_batch_mode_log", "sv_batch_free", "sv_step1d_noalloc", "sv_set_drive",
-           "sv_set_launch", "sv_get_launch")
+           "sv_set_launch", "sv_get_launch", "sv_num_configs", "sv_get_config", "sv_config_desc",
+           "sv_set_config", "sv_autotune", "sv_batch_num_configs", "sv_batch_set_config",
+           "sv_batch_get_config")
 
 
 class SvError(RuntimeError):
@@ -136,6 +138,15 @@ def lib() -> ctypes.CDLL:
     L.sv_set_drive.argtypes = [vp, ctypes.POINTER(_Drive)]
     L.sv_set_launch.argtypes = [vp, ctypes.c_int]
     L.sv_get_launch.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.sv_num_configs.argtypes = [vp, ip]
+    L.sv_get_config.argtypes = [vp, ip, ctypes.c_char_p, ctypes.c_size_t]
+    L.sv_config_desc.argtypes = [vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t]
+    L.sv_set_config.argtypes = [vp, ctypes.c_int]
+    L.sv_autotune.argtypes = [vp, ctypes.c_int, ip, dp]
+    L.sv_batch_num_configs.argtypes = [vp, ip]
+    L.sv_batch_set_config.argtypes = [vp, ctypes.c_int]
+    L.sv_batch_get_config.argtypes = [vp, ip, ctypes.c_char_p, ctypes.c_size_t]
     L.sv_step1d_noalloc.argtypes = [ctypes.POINTER(_Params), ctypes.c_int64, ctypes.c_double, vp, vp,
                                     dp, ctypes.POINTER(ctypes.c_uint32), vp]
     _lib = L
@@ -306,6 +317,38 @@ class Solver:
         _check(lib().sv_get_launch(self._h, ctypes.byref(m)), "sv_get_launch")
         return m.value
 
+    # ------------------------------------------------------------ launch configurations
+    def configs(self) -> list[str]:
+        """Descriptions of the solver's launch configurations (same results,
+        different speed)."""
+        n = ctypes.c_int()
+        _check(lib().sv_num_configs(self._h, ctypes.byref(n)), "sv_num_configs")
+        out = []
+        for i in range(n.value):
+            buf = ctypes.create_string_buffer(256)
+            _check(lib().sv_config_desc(self._h, i, buf, 256), "sv_config_desc")
+            out.append(buf.value.decode())
+        return out
+
+    @property
+    def config(self) -> int:
+        i = ctypes.c_int()
+        _check(lib().sv_get_config(self._h, ctypes.byref(i), None, 0), "sv_get_config")
+        return i.value
+
+    def set_config(self, index: int):
+        _check(lib().sv_set_config(self._h, int(index)), "sv_set_config")
+
+    def autotune(self, steps: int = 10) -> tuple[int, list[float]]:
+        """Time every configuration on the current state (restored after each
+        trial) and keep the fastest.  Returns (index, microseconds per step of
+        each configuration)."""
+        n = len(self.configs())
+        us = (ctypes.c_double * n)()
+        best = ctypes.c_int()
+        _check(lib().sv_autotune(self._h, int(steps), ctypes.byref(best), us), "sv_autotune")
+        return best.value, list(us)
+
     def time(self) -> tuple[float, int]:
         t, k = ctypes.c_double(), ctypes.c_int64()
         _check(lib().sv_time(self._h, ctypes.byref(t), ctypes.byref(k)), "sv_time")
@@ -369,6 +412,12 @@ class Batch:
                                    int(max_steps), ctypes.c_void_p(self._stream.cuda_stream),
                                    dev_ptr, self.device_bytes, ctypes.byref(h)), "sv_batch_init")
         self._h = h
+        self._initial = host
+
+    def reset_initial(self):
+        """Upload the initial states given at construction again (times, step
+        counts and flags back to zero)."""
+        _check(lib().sv_batch_reset(self._h, _dp(self._initial)), "sv_batch_reset")
 
     def _concat(self, states) -> np.ndarray:
         parts = []
@@ -398,6 +447,29 @@ class Batch:
     def reset(self, states):
         host = self._concat(states)
         _check(lib().sv_batch_reset(self._h, _dp(host)), "sv_batch_reset")
+
+    def configs(self) -> list[str]:
+        """Descriptions of the batch's launch configurations (block size per run)."""
+        n = ctypes.c_int()
+        _check(lib().sv_batch_num_configs(self._h, ctypes.byref(n)), "sv_batch_num_configs")
+        cur = self.config
+        out = []
+        for i in range(n.value):
+            _check(lib().sv_batch_set_config(self._h, i), "sv_batch_set_config")
+            buf = ctypes.create_string_buffer(256)
+            _check(lib().sv_batch_get_config(self._h, None, buf, 256), "sv_batch_get_config")
+            out.append(buf.value.decode())
+        _check(lib().sv_batch_set_config(self._h, cur), "sv_batch_set_config")
+        return out
+
+    @property
+    def config(self) -> int:
+        i = ctypes.c_int()
+        _check(lib().sv_batch_get_config(self._h, ctypes.byref(i), None, 0), "sv_batch_get_config")
+        return i.value
+
+    def set_config(self, index: int):
+        _check(lib().sv_batch_set_config(self._h, int(index)), "sv_batch_set_config")
 
     def run(self):
         _check(lib().sv_batch_run(self._h), "sv_batch_run")
