@@ -106,6 +106,38 @@ int orc_step_heun(const orc_params* P, int dim, const long* n, double h, double 
 int orc_run_heun(const orc_params* P, int dim, const long* n, double h, double* U,
                  double t0, double t_end, long max_steps, double* t_out, long* steps_out);
 
+/* 2D problems with boundaries, a map of the active medium and driven cells
+   (the paper's two-dimensional active-sector problem, Sec. 3).
+   bc[0], bc[1]: x = 0, x = Lx; bc[2], bc[3]: y = 0, y = Ly; each
+   ORC_BC_PERIODIC, ORC_BC_REFLECT (solid wall: mirrored ghosts with the
+   normal momentum reversed) or ORC_BC_OUTFLOW (zero-gradient ghosts); a
+   non-periodic axis needs n >= 2.
+   Medium: row j (0 <= j < ny) is the active medium of P (relaxation, pump
+   and sink) in the cells act_lo[j] <= i < act_hi[j] and frozen (no
+   relaxation, pump or sink: Y = 0) elsewhere; act_lo == NULL: active
+   everywhere.  The rest state rho = p = 1, v = 0, E_nu = C_k + S is steady in
+   both.  A ghost cell takes the medium of the cell whose state it holds.
+   Driven cells: drv_lo[j] <= i < drv_hi[j] (drv_lo == NULL: none) hold, at
+   every new time level t, rho = 1 + amp sin(omega t), v = 0,
+   p = 1 + gamma amp sin(omega t), E_nu = rho (C_k + S): a pulsating acoustic
+   source (frozen sound speed c0^2 = gamma at rho0 = p0 = 1). */
+typedef struct {
+  const int* act_lo;
+  const int* act_hi;
+  const int* drv_lo;
+  const int* drv_hi;
+  double omega, amp;
+} orc_medium2;
+
+/* One step of the 2D problem (fields rho, rho u, rho v, E, E_nu; U[f*nx*ny +
+   i + nx*j]) from time t with time step dt.  Returns as orc_step, -3 on a
+   bad argument. */
+int orc_step2m(const orc_params* P, long nx, long ny, double h, double dt, const int* bc,
+               const orc_medium2* M, double t, const double* U, double* Unew);
+int orc_run2m(const orc_params* P, long nx, long ny, double h, const int* bc,
+              const orc_medium2* M, double* U, double t0, double t_end, long max_steps,
+              double* t_out, long* steps_out);
+
 /* Number of OpenMP threads the array loops use (1 without OpenMP). */
 int orc_threads(void);
 

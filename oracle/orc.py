@@ -133,8 +133,37 @@ def lib():
         L.orc_run_bc1d.argtypes = [pp, ctypes.c_long, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                    ctypes.POINTER(_CDrive), dp, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_long, dp, lp]
+        mp = ctypes.POINTER(_CMedium2)
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.orc_step2m.argtypes = [pp, ctypes.c_long, ctypes.c_long, ctypes.c_double, ctypes.c_double,
+                                 ip, mp, ctypes.c_double, dp, dp]
+        L.orc_run2m.argtypes = [pp, ctypes.c_long, ctypes.c_long, ctypes.c_double, ip, mp, dp,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_long, dp, lp]
         _lib = L
     return _lib
+
+
+class _CMedium2(ctypes.Structure):
+    _fields_ = [("act_lo", ctypes.POINTER(ctypes.c_int)), ("act_hi", ctypes.POINTER(ctypes.c_int)),
+                ("drv_lo", ctypes.POINTER(ctypes.c_int)), ("drv_hi", ctypes.POINTER(ctypes.c_int)),
+                ("omega", ctypes.c_double), ("amp", ctypes.c_double)]
+
+
+class Medium2:
+    """Map of the active medium and driven cells of a 2D problem: per row j,
+    pump on for act_lo[j] <= i < act_hi[j] (None: everywhere), driven cells
+    drv_lo[j] <= i < drv_hi[j] (None: none), pulsation omega, amplitude amp."""
+
+    def __init__(self, act_lo=None, act_hi=None, drv_lo=None, drv_hi=None, omega=0.0, amp=0.0):
+        conv = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.intc)
+        self.act_lo, self.act_hi = conv(act_lo), conv(act_hi)
+        self.drv_lo, self.drv_hi = conv(drv_lo), conv(drv_hi)
+        self.omega, self.amp = float(omega), float(amp)
+
+    def c(self) -> _CMedium2:
+        ptr = lambda a: None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        return _CMedium2(ptr(self.act_lo), ptr(self.act_hi), ptr(self.drv_lo), ptr(self.drv_hi),
+                         self.omega, self.amp)
 
 
 def _dp(a: np.ndarray):
@@ -255,6 +284,35 @@ def run_driven(P: Params, U: np.ndarray, N: int, h: float, t_end: float, drv: _C
     k = ctypes.c_long()
     rc = lib().orc_run_bc1d(ctypes.byref(P.c()), int(N), h, DRIVEN, bc_hi, ctypes.byref(drv),
                             _dp(U), t0, t_end, max_steps, ctypes.byref(t), ctypes.byref(k))
+    return U, t.value, k.value, rc
+
+
+def _bc4(bc):
+    return (ctypes.c_int * 4)(*[int(b) for b in bc])
+
+
+def step2m(P: Params, U: np.ndarray, nx: int, ny: int, h: float, dt: float, bc,
+           medium: "Medium2 | None" = None, t: float = 0.0):
+    """One 2D step with boundaries bc = (x_lo, x_hi, y_lo, y_hi), the medium
+    map and driven cells of `medium`, from time t.  Returns (Unew, rc)."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    out = np.empty_like(U)
+    m = medium.c() if medium is not None else None
+    rc = lib().orc_step2m(ctypes.byref(P.c()), int(nx), int(ny), h, dt, _bc4(bc),
+                          ctypes.byref(m) if m is not None else None, t, _dp(U), _dp(out))
+    return out, rc
+
+
+def run2m(P: Params, U: np.ndarray, nx: int, ny: int, h: float, t_end: float, bc,
+          medium: "Medium2 | None" = None, t0: float = 0.0, max_steps: int = 1 << 40):
+    """2D run to t_end (last step clamped).  Returns (U, t, steps, rc)."""
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    t = ctypes.c_double()
+    k = ctypes.c_long()
+    m = medium.c() if medium is not None else None
+    rc = lib().orc_run2m(ctypes.byref(P.c()), int(nx), int(ny), h, _bc4(bc),
+                         ctypes.byref(m) if m is not None else None, _dp(U), t0, t_end, max_steps,
+                         ctypes.byref(t), ctypes.byref(k))
     return U, t.value, k.value, rc
 
 

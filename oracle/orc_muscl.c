@@ -440,6 +440,152 @@ int orc_run_bc1d(const orc_params* P, long N, double h, int bc_lo, int bc_hi,
   return rc;
 }
 
+/* ------------------------------------------------- 2D boundaries, medium map, drive */
+
+/* Cell (0..n-1) whose state position j (-2..n+1) holds along an axis of n
+   cells, and whether its normal momentum is reversed (solid wall). */
+static long ghost_map(long j, long n, int bc_lo, int bc_hi, int* flip) {
+  *flip = 0;
+  if (j >= 0 && j < n) return j;
+  const int bc = j < 0 ? bc_lo : bc_hi;
+  if (bc == ORC_BC_PERIODIC) return ((j % n) + n) % n;
+  if (bc == ORC_BC_REFLECT) {
+    *flip = 1;
+    return j < 0 ? -1 - j : 2 * n - 1 - j;
+  }
+  return j < 0 ? 0 : n - 1;   /* outflow: zero gradient */
+}
+
+static int active_cell(const orc_medium2* M, long i, long j) {
+  if (!M || !M->act_lo) return 1;
+  return i >= M->act_lo[j] && i < M->act_hi[j];
+}
+
+static int driven_cell(const orc_medium2* M, long i, long j) {
+  if (!M || !M->drv_lo) return 0;
+  return i >= M->drv_lo[j] && i < M->drv_hi[j];
+}
+
+/* The pulsating source at time t. */
+static void pulse_state(const orc_params* P, const orc_medium2* M, double t, double* u) {
+  const double s = M->amp * sin(M->omega * t);
+  const double rho = 1.0 + s, p = 1.0 + P->gamma * s;
+  const double Ev = rho * (P->Ck + P->S);
+  u[0] = rho;
+  u[1] = 0.0;
+  u[2] = 0.0;
+  u[3] = p / (P->gamma - 1.0) + Ev;
+  u[4] = Ev;
+}
+
+/* The grid is extended by two ghost layers per side; position (a, b) of the
+   extended grid holds cell (map_x(a - 2), map_y(b - 2)) with the momenta of
+   the wall-mirrored axes reversed (so corner ghosts are mirrored in both).
+   Predictors run on positions 1..n+2 of both axes, faces on those that
+   bound a grid cell, updates on the grid cells, each with the functions of
+   the periodic step and the cell's own medium. */
+int orc_step2m(const orc_params* P, long nx, long ny, double h, double dt, const int* bc,
+               const orc_medium2* M, double t, const double* U, double* Unew) {
+  if (!bc || nx < 1 || ny < 1) return -3;
+  for (int k = 0; k < 4; ++k)
+    if (bc[k] < ORC_BC_PERIODIC || bc[k] > ORC_BC_OUTFLOW) return -3;
+  if ((bc[0] != ORC_BC_PERIODIC || bc[1] != ORC_BC_PERIODIC) && nx < 2) return -3;
+  if ((bc[2] != ORC_BC_PERIODIC || bc[3] != ORC_BC_PERIODIC) && ny < 2) return -3;
+  if (M && M->drv_lo && !(M->omega == M->omega)) return -3;
+  const int nf = 5;
+  const long N = nx * ny, ex = nx + 4, ey = ny + 4, NE = ex * ey;
+  const long ne[2] = {ex, ey};
+  grid_t ge = make_grid(2, ne);
+  orc_params Pp = *P;
+  Pp.tau0 = INFINITY;                           /* the passive medium: frozen, Y = 0 */
+  double* Ue = malloc(sizeof(double) * (size_t)nf * (size_t)NE);
+  unsigned char* act = malloc((size_t)NE);
+  double (*dU)[3][NF_MAX] = malloc(sizeof(double[3][NF_MAX]) * (size_t)NE);
+  double (*uh)[NF_MAX] = malloc(sizeof(double[NF_MAX]) * (size_t)NE);
+  double (*Fface)[3][NF_MAX] = malloc(sizeof(double[3][NF_MAX]) * (size_t)NE);
+  if (!Ue || !act || !dU || !uh || !Fface) {
+    free(Ue); free(act); free(dU); free(uh); free(Fface);
+    return -2;
+  }
+  for (long b = 0; b < ey; ++b)
+    for (long a = 0; a < ex; ++a) {
+      int fx, fy;
+      const long i = ghost_map(a - 2, nx, bc[0], bc[1], &fx);
+      const long j = ghost_map(b - 2, ny, bc[2], bc[3], &fy);
+      const long e = a + ex * b, q = i + nx * j;
+      for (int f = 0; f < nf; ++f) Ue[(long)f * NE + e] = U[(long)f * N + q];
+      if (fx) Ue[1 * NE + e] = -Ue[1 * NE + e];
+      if (fy) Ue[2 * NE + e] = -Ue[2 * NE + e];
+      act[e] = (unsigned char)active_cell(M, i, j);
+    }
+
+#pragma omp parallel for schedule(static)
+  for (long b = 1; b <= ny + 2; ++b)
+    for (long a = 1; a <= nx + 2; ++a) {
+      const long e = a + ex * b;
+      predict(act[e] ? P : &Pp, &ge, h, dt, Ue, e, dU[e], uh[e]);
+    }
+
+#pragma omp parallel for schedule(static)
+  for (long b = 1; b <= ny + 1; ++b)
+    for (long a = 1; a <= nx + 1; ++a) {
+      const long e = a + ex * b;
+      if (b >= 2)   /* x face between (a, b) and (a + 1, b) */
+        face_flux(P, &ge, Ue, 0, e, dU[e], uh[e], e + 1, dU[e + 1], uh[e + 1], Fface[e][0]);
+      if (a >= 2)   /* y face between (a, b) and (a, b + 1) */
+        face_flux(P, &ge, Ue, 1, e, dU[e], uh[e], e + ex, dU[e + ex], uh[e + ex], Fface[e][1]);
+    }
+
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+  for (long j = 0; j < ny; ++j)
+    for (long i = 0; i < nx; ++i) {
+      const long e = (i + 2) + ex * (j + 2), q = i + nx * j;
+      double u[NF_MAX], out[NF_MAX], Fp[3][NF_MAX], Fm[3][NF_MAX];
+      gather(&ge, Ue, e, u);
+      memcpy(Fp[0], Fface[e][0], sizeof(double) * NF_MAX);
+      memcpy(Fm[0], Fface[e - 1][0], sizeof(double) * NF_MAX);
+      memcpy(Fp[1], Fface[e][1], sizeof(double) * NF_MAX);
+      memcpy(Fm[1], Fface[e - ex][1], sizeof(double) * NF_MAX);
+      correct(act[e] ? P : &Pp, &ge, h, dt, u, uh[e], Fp, Fm, out);
+      if (driven_cell(M, i, j)) pulse_state(P, M, t + dt, out);
+      for (int f = 0; f < nf; ++f) Unew[(long)f * N + q] = out[f];
+      if (!orc_physical(P, 2, out)) bad = 1;
+    }
+  free(Ue); free(act); free(dU); free(uh); free(Fface);
+  return bad ? -1 : 0;
+}
+
+int orc_run2m(const orc_params* P, long nx, long ny, double h, const int* bc,
+              const orc_medium2* M, double* U, double t0, double t_end, long max_steps,
+              double* t_out, long* steps_out) {
+  const size_t bytes = sizeof(double) * 5 * (size_t)nx * (size_t)ny;
+  double* tmp = malloc(bytes);
+  if (!tmp) return -2;
+  const long n2[2] = {nx, ny};
+  double t = t0;
+  long k = 0;
+  int rc = 0;
+  while (t < t_end && k < max_steps) {
+    double dt = orc_dt(P, 2, n2, h, U);
+    int last = 0;
+    if (dt >= t_end - t) {
+      dt = t_end - t;
+      last = 1;
+    }
+    rc = orc_step2m(P, nx, ny, h, dt, bc, M, t, U, tmp);
+    if (rc == -2 || rc == -3) break;
+    memcpy(U, tmp, bytes);
+    t = last ? t_end : t + dt;
+    ++k;
+    if (rc != 0) break;
+  }
+  free(tmp);
+  *t_out = t;
+  *steps_out = k;
+  return rc;
+}
+
 /* ------------------------------------------------------------ Heun / SSP-RK2 */
 
 /* Spatial operator of the method of lines on a periodic grid:

@@ -205,3 +205,86 @@ def random_field_3d(gamma: float, n: int, L: float, base, amp: float, seed: int,
     v = [c * field() for _ in range(3)]
     # axes (i, j, k) of the FFT grid are mapped to (z, y, x): x fastest
     return prim_to_cons(gamma, rho0 + drho, v, p0 + c * c * drho, np.full(drho.shape, ev0))
+
+
+# ------------------------------------------------------------------ 2D active sector
+
+def row_intervals(mask: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Per row j of a (ny, nx) boolean mask whose true cells are contiguous in
+    every row: int32 arrays (lo, hi) with mask[j, lo[j]:hi[j]] the true cells
+    (lo = hi = 0 for an empty row).  Raises if a row is not one interval."""
+    ny, nx = mask.shape
+    lo = np.zeros(ny, dtype=np.int32)
+    hi = np.zeros(ny, dtype=np.int32)
+    for j in range(ny):
+        idx = np.flatnonzero(mask[j])
+        if idx.size:
+            if idx[-1] - idx[0] + 1 != idx.size:
+                raise ValueError(f"row {j} of the mask is not one interval")
+            lo[j], hi[j] = idx[0], idx[-1] + 1
+    return lo, hi
+
+
+def sector_maps(nx: int, ny: int, h: float, apex, half_angle: float, r_src: float,
+                axis: float = 0.0):
+    """The 2D active-sector geometry as per-row cell intervals: the active
+    medium is the cells whose centre lies within `half_angle` (radians) of the
+    ray from `apex` = (x0, y0) in direction `axis`; the driven source is the
+    cells whose centre lies within `r_src` of the apex.  Returns
+    (act_lo, act_hi, drv_lo, drv_hi), int32 arrays of ny entries."""
+    x = (np.arange(nx) + 0.5) * h
+    y = (np.arange(ny) + 0.5) * h
+    X, Y = np.meshgrid(x, y)
+    dx, dy = X - apex[0], Y - apex[1]
+    along = dx * math.cos(axis) + dy * math.sin(axis)
+    across = -dx * math.sin(axis) + dy * math.cos(axis)
+    active = (along > 0.0) & (np.abs(across) <= math.tan(half_angle) * along)
+    driven = dx * dx + dy * dy <= r_src * r_src
+    return row_intervals(active) + row_intervals(driven)
+
+
+def sector_rest_state(gamma: float, Ck: float, S: float, nx: int, ny: int) -> np.ndarray:
+    """Conserved (5, ny*nx) rest state rho = p = 1, v = 0, specific vibrational
+    energy C_k + S: the steady state of the active medium, and of the frozen
+    medium outside it."""
+    one = np.ones((ny, nx))
+    return prim_to_cons(gamma, one, [0.0 * one, 0.0 * one], one, np.full((ny, nx), Ck + S))
+
+
+@dataclass
+class SectorProblem:
+    """The paper's 2D active-sector problem as set up here (Sec. 3; domain,
+    source and sizes are not given there): a pulsating source at `apex` on the
+    mid-line near the left boundary, the active medium in the 30-degree sector
+    opening towards +x (frozen medium elsewhere), a solid wall at x = Lx (G1)
+    reached by the front near t = 1, free outflow on the other three sides."""
+    nx: int
+    ny: int
+    h: float
+    apex: tuple
+    half_angle: float
+    r_src: float
+    omega: float
+    amp: float
+    bc: tuple
+    maps: tuple
+
+
+def sector_problem(nx: int, wavelength: float = 0.1, amp: float = 1e-3,
+                   gamma: float = 1.4) -> SectorProblem:
+    """Domain [0, Lx] x [0, Ly] with Lx = x0 + c0 (t = 1 to reach the wall),
+    Ly = Lx, x0 = 2 wavelengths; nx cells across, h = Lx / nx; the source a
+    disc of radius wavelength / 4 pulsating at omega = 2 pi c0 / wavelength."""
+    c0 = math.sqrt(gamma)
+    x0 = 2.0 * wavelength
+    Lx = x0 + c0
+    h = Lx / nx
+    ny = nx
+    apex = (x0, 0.5 * ny * h)
+    half = math.radians(15.0)
+    r_src = 0.25 * wavelength
+    maps = sector_maps(nx, ny, h, apex, half, r_src)
+    OUT, WALL = 2, 1
+    return SectorProblem(nx=nx, ny=ny, h=h, apex=apex, half_angle=half, r_src=r_src,
+                         omega=2.0 * math.pi * c0 / wavelength, amp=amp,
+                         bc=(OUT, WALL, OUT, OUT), maps=maps)
