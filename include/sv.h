@@ -92,7 +92,7 @@ typedef struct {
   int method;                   /* SV_HANCOCK (0) or SV_HEUN */
 } sv_params;
 
-/* ---- boundary conditions (1D grids; 2D and 3D grids are periodic) */
+/* ---- boundary conditions (1D and 2D grids; 3D grids are periodic) */
 #define SV_BC_PERIODIC 0
 #define SV_BC_REFLECT  1   /* solid wall: mirrored ghost cells with the velocity reversed */
 #define SV_BC_OUTFLOW  2   /* zero-gradient ghost cells (free outflow) */
@@ -103,8 +103,11 @@ typedef struct {
   int dim;                      /* 1, 2 or 3 */
   int64_t n[3];                 /* cells per axis (unused axes ignored) */
   double L[3];                  /* domain length per axis; L[a]/n[a] must agree */
-  int bc[2];                    /* 1D: SV_BC_* at x = 0 and at x = L[0] (SV_BC_DRIVEN
-                                   only at x = 0); SV_BC_PERIODIC (0) when dim > 1 */
+  int bc[4];                    /* SV_BC_* at x = 0, x = L[0], y = 0, y = L[1].
+                                   1D: bc[0], bc[1] (SV_BC_DRIVEN only at x = 0),
+                                   bc[2], bc[3] ignored.  2D: periodic, wall or
+                                   outflow per side (a non-periodic axis needs >= 2
+                                   cells).  3D: all SV_BC_PERIODIC (0). */
 } sv_grid;
 
 typedef struct sv_solver sv_solver;
@@ -325,6 +328,34 @@ int sv_batch_get_config(sv_batch* b, int* index, char* desc, size_t cap);
    array and race.  n beyond SV_NOALLOC_MAX_CELLS returns SV_ESIZE. */
 int sv_step1d_noalloc(const sv_params* p, int64_t n, double L, const void* U_in, void* U_out,
                       double* dt_used, uint32_t* flags, void* cuda_stream);
+
+/* Medium map and driven cells of a 2D solver (the paper's two-dimensional
+   active-sector problem, Sec. 3: the active medium fills a sector, a source
+   drives acoustic waves, walls and free outflow bound the domain).  All
+   arrays have n[1] entries (one per row j = 0..ny-1) and are copied.
+     active_lo / active_hi: row j is the active medium of the solver's
+       parameters (relaxation, pump and sink) in the cells
+       active_lo[j] <= i < active_hi[j] and frozen (no relaxation, pump or sink)
+       elsewhere; NULL: active everywhere.  The rest state rho = p = 1, v = 0,
+       E_nu = C_k + S is steady in both.  A ghost cell takes the medium of the
+       cell whose state it holds.
+     driven_lo / driven_hi: cells driven_lo[j] <= i < driven_hi[j] hold, at
+       every new time level t, the pulsating source rho = 1 + amp sin(omega t),
+       v = 0, p = 1 + gamma amp sin(omega t), E_nu = rho (C_k + S); NULL: none.
+   0 <= lo <= hi <= n[0] in every row. */
+typedef struct {
+  const int32_t* active_lo;
+  const int32_t* active_hi;
+  const int32_t* driven_lo;
+  const int32_t* driven_hi;
+  double omega, amp;
+} sv_medium2d;
+
+/* Install (or, with every table NULL, remove) the medium map and driven
+   cells of a 2D solver; the library keeps device copies (4 n[1] int32) until
+   sv_free.  SV_EINVAL if the solver is not 2D or a table is out of range.
+   Synchronous. */
+int sv_set_medium2d(sv_solver* s, const sv_medium2d* m);
 
 /* Prescribed wave of an SV_BC_DRIVEN boundary: the ghost cell centred at x < 0
    holds U(x, t) = base + Re(amp e^{i (k x - omega t)}), k = k_re + i k_im,

@@ -44,6 +44,7 @@ struct sv_solver {
   double* partial = nullptr;
   double* sums_out = nullptr;
   Ctl* host_ctl = nullptr;             // pinned mirror of the control block
+  int* medium_dev = nullptr;           // 2D medium map and driven cells: 4 x ny int32
   double* host_sums = nullptr;
   int grid = 0;
   int tile_grid = 0;                   // grid of the block-tile kernel of the current config
@@ -80,11 +81,20 @@ int check_inputs(const sv_params* p, const sv_grid* g) {
     return SV_EINVAL;
   if (p->limiter < SV_MINMOD || p->limiter > SV_MC) return SV_EINVAL;
   if (p->precision < SV_FP32 || p->precision > SV_FP32_P64) return SV_EINVAL;
-  for (int side = 0; side < 2; ++side) {
+  for (int side = 0; side < 2; ++side)
     if (g->bc[side] < SV_BC_PERIODIC || g->bc[side] > SV_BC_DRIVEN) return SV_EINVAL;
-    if (g->dim > 1 && g->bc[side] != SV_BC_PERIODIC) return SV_EINVAL;
-  }
   if (g->bc[1] == SV_BC_DRIVEN) return SV_EINVAL;
+  if (g->dim == 2) {
+    // walls and outflow on any side; the driven boundary is 1D only
+    for (int side = 0; side < 4; ++side)
+      if (g->bc[side] < SV_BC_PERIODIC || g->bc[side] > SV_BC_OUTFLOW) return SV_EINVAL;
+    for (int a = 0; a < 2; ++a)
+      if ((g->bc[2 * a] != SV_BC_PERIODIC || g->bc[2 * a + 1] != SV_BC_PERIODIC) && g->n[a] < 2)
+        return SV_EINVAL;
+  }
+  if (g->dim == 3)
+    for (int side = 0; side < 4; ++side)
+      if (g->bc[side] != SV_BC_PERIODIC) return SV_EINVAL;
   if (p->method != SV_HANCOCK && p->method != SV_HEUN) return SV_EINVAL;
   if (p->method == SV_HEUN &&
       (g->dim != 1 || g->bc[0] != SV_BC_PERIODIC || g->bc[1] != SV_BC_PERIODIC ||
@@ -299,8 +309,13 @@ int sv_init(const sv_params* p, const sv_grid* g, void* cuda_stream, void* devic
   k.cfl = p->cfl;
   k.c_tau = p->c_tau;
   k.limiter = p->limiter;
-  k.bc_lo = g->dim == 1 ? g->bc[0] : SV_BC_PERIODIC;
-  k.bc_hi = g->dim == 1 ? g->bc[1] : SV_BC_PERIODIC;
+  k.bc_lo = g->dim <= 2 ? g->bc[0] : SV_BC_PERIODIC;
+  k.bc_hi = g->dim <= 2 ? g->bc[1] : SV_BC_PERIODIC;
+  k.bc_ylo = g->dim == 2 ? g->bc[2] : SV_BC_PERIODIC;
+  k.bc_yhi = g->dim == 2 ? g->bc[3] : SV_BC_PERIODIC;
+  k.act_lo = k.act_hi = k.pul_lo = k.pul_hi = nullptr;
+  k.pul_omega = k.pul_amp = 0.0;
+  k.pul_ev = p->Ck + p->S;
   {   // a driven boundary holds the uniform equilibrium until sv_set_drive
     const double ev0 = p->Ck + p->S;
     const double base[4] = {1.0, 0.0, 1.0 / (p->gamma - 1.0) + ev0, ev0};
@@ -546,6 +561,44 @@ int sv_get_launch(sv_solver* s, int* mode) {
   return SV_OK;
 }
 
+int sv_set_medium2d(sv_solver* s, const sv_medium2d* m) {
+  if (!s || !m || s->dim != 2) return SV_EINVAL;
+  const int64_t nx = s->g.n[0], ny = s->g.n[1];
+  const int32_t* tab[4] = {m->active_lo, m->active_hi, m->driven_lo, m->driven_hi};
+  if ((tab[0] == nullptr) != (tab[1] == nullptr) || (tab[2] == nullptr) != (tab[3] == nullptr))
+    return SV_EINVAL;
+  for (int t = 0; t < 4; t += 2)
+    if (tab[t])
+      for (int64_t j = 0; j < ny; ++j)
+        if (tab[t][j] < 0 || tab[t][j] > tab[t + 1][j] || tab[t + 1][j] > nx) return SV_EINVAL;
+  if (tab[2] && (!isfinite(m->omega) || !isfinite(m->amp))) return SV_EINVAL;
+  if (!s->medium_dev && (tab[0] || tab[2])) {
+    if (cudaMalloc((void**)&s->medium_dev, sizeof(int) * 4 * (size_t)ny) != cudaSuccess) {
+      s->medium_dev = nullptr;
+      return SV_ENOMEM;
+    }
+  }
+  // the captured graph and running steps use the old tables
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return SV_ECUDA;
+  if (s->graph) {
+    cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+  }
+  int* dst[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (int t = 0; t < 4; ++t) {
+    if (!tab[t]) continue;
+    dst[t] = s->medium_dev + (size_t)t * (size_t)ny;
+    SV_TRY(cudaMemcpy(dst[t], tab[t], sizeof(int) * (size_t)ny, cudaMemcpyHostToDevice));
+  }
+  s->kp.act_lo = dst[0];
+  s->kp.act_hi = dst[1];
+  s->kp.pul_lo = dst[2];
+  s->kp.pul_hi = dst[3];
+  s->kp.pul_omega = tab[2] ? m->omega : 0.0;
+  s->kp.pul_amp = tab[2] ? m->amp : 0.0;
+  return SV_OK;
+}
+
 int sv_set_drive(sv_solver* s, const sv_drive* d) {
   if (!s || !d || s->dim != 1 || s->kp.bc_lo != SV_BC_DRIVEN) return SV_EINVAL;
   if (!isfinite(d->omega) || !isfinite(d->k_re) || !isfinite(d->k_im)) return SV_EINVAL;
@@ -609,6 +662,7 @@ void sv_free(sv_solver* s) {
   if (s->graph) cudaGraphExecDestroy(s->graph);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
   if (s->owns_mem && s->mem) cudaFree(s->mem);
+  if (s->medium_dev) cudaFree(s->medium_dev);
   if (s->host_ctl) cudaFreeHost(s->host_ctl);
   if (s->host_sums) cudaFreeHost(s->host_sums);
   delete s;

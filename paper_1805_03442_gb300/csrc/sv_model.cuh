@@ -31,10 +31,21 @@ struct KParams {
   int limiter;   // 0 minmod, 1 van Leer, 2 MC
   int frozen;    // 1: no source at all (Q = I = 0, 1/tau = 0)
   int qi_zero;   // 1: all Q and I exponents are zero (Q = I = Q0)
-  int bc_lo, bc_hi;   // 1D boundary conditions at x = 0 / x = L (BC_*)
+  int bc_lo, bc_hi;   // boundary conditions at x = 0 / x = Lx (BC_*)
+  int bc_ylo, bc_yhi; // 2D: boundary conditions at y = 0 / y = Ly
   int pad;
   // driven boundary wave: U = base + Re(amp e^{i (k x - omega t)})
   double drv_omega, drv_kre, drv_kim, drv_base[4], drv_are[4], drv_aim[4];
+  // 2D medium map (device arrays of ny entries, null when unused): row j is
+  // active (relaxation, pump, sink) for act_lo[j] <= i < act_hi[j] and frozen
+  // elsewhere; cells drv_lo[j] <= i < drv_hi[j] hold the pulsating source
+  // rho = 1 + pul_amp sin(pul_omega t), v = 0, p = 1 + gamma (rho - 1),
+  // E_nu = rho (C_k + S) at every new time level
+  const int* act_lo;
+  const int* act_hi;
+  const int* pul_lo;
+  const int* pul_hi;
+  double pul_omega, pul_amp, pul_ev;   // pul_ev = C_k + S
   // float copies for the float kernels (kparams_finish): the twelve values
   // above, then log2(1/tau0) (0 in the frozen limit), -tau_rho, -tau_T
   float f[16];

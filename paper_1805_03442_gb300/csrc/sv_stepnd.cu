@@ -74,9 +74,11 @@ struct Nd {
     return fmin(fmin(a[0], pa), fmin(b[0], pb)) > (R)0;
   }
 
-  static __device__ __forceinline__ void source(const P<R>& k, const V& u, R& yE, R& yEv) {
+  // Y of a cell of the active medium; a frozen cell (active = false) has none.
+  static __device__ __forceinline__ void source(const P<R>& k, const V& u, R& yE, R& yEv,
+                                                bool active = true) {
     yE = yEv = (R)0;
-    if (SRC == 0) return;
+    if (SRC == 0 || !active) return;
     R ir, p, v[DIM];
     prim(k, u, ir, v, p);
     Src<R, SRC>::eval(k, u[0], p * ir, u[2 + DIM], yE, yEv);
@@ -112,6 +114,37 @@ struct Nd {
   }
 };
 
+// Cell whose state position j of an axis of n cells holds: periodic wrap,
+// wall mirror (flip: the normal momentum is reversed) or outflow copy.
+// Positions further out than the two ghost layers are clamped into the grid;
+// their values reach no updated cell.
+__device__ __forceinline__ int64_t map_axis(int64_t j, int64_t n, int bc_lo, int bc_hi,
+                                            bool& flip) {
+  flip = false;
+  if (j >= 0 && j < n) return j;
+  const int bc = j < 0 ? bc_lo : bc_hi;
+  if (bc == BC_PERIODIC) return wrap(j, n);
+  if (bc == BC_REFLECT) {
+    flip = true;
+    const int64_t m = j < 0 ? -1 - j : 2 * n - 1 - j;
+    return m < 0 ? 0 : (m >= n ? n - 1 : m);
+  }
+  return j < 0 ? 0 : n - 1;
+}
+
+// The pulsating source of the 2D problem at time t (double, like its
+// definition), in the kernel's type.
+template <typename R, int NF>
+__device__ __forceinline__ void pulse_state(const KParams& kp, double t, R (&u)[NF]) {
+  const double s = kp.pul_amp * sin(kp.pul_omega * t);
+  const double rho = 1.0 + s, p = 1.0 + kp.gamma * s, Ev = rho * kp.pul_ev;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) u[f] = (R)0;
+  u[0] = (R)rho;
+  u[NF - 2] = (R)(p / kp.g1 + Ev);
+  u[NF - 1] = (R)Ev;
+}
+
 // Planes per thread ring (a power of two; four planes are in flight).
 constexpr int kPlaneRing = 8;
 
@@ -129,7 +162,10 @@ constexpr size_t stepnd_smem() {
 }
 
 // DIM 2: TY must be 1; marching axis y.  DIM 3: marching axis z.
-template <typename R, int PP, int LIM, int SRC, int DIM, int TX, int TY, int MINB>
+// BND: a 2D grid with walls or outflow on some side, or a medium map / driven
+// cells; without it every axis is periodic (the compiled-out general path
+// costs the periodic kernel 8%).
+template <typename R, int PP, int LIM, int SRC, int DIM, int TX, int TY, int MINB, bool BND>
 __global__ void __launch_bounds__(TX * TY, MINB)
 stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl* __restrict__ ctl,
               int64_t nx, int64_t ny, int64_t nz, int tiles_x, int tiles_y, int nseg) {
@@ -172,11 +208,29 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
   const int64_t q0 = seg * M / nseg, q1 = (seg + 1) * M / nseg;
   const bool interior = tx >= 1 && tx <= TX - 2 && gx < nx &&
                         (DIM == 2 || (ty >= 1 && ty <= TY - 2 && gy < ny));
-  const int64_t wx = wrap(gx, nx), wy = DIM == 3 ? wrap(gy, ny) : 0;
+  // 2D boundaries: x sides kp.bc_lo / bc_hi, y sides (the marching axis)
+  // kp.bc_ylo / bc_yhi; 3D is periodic.  Ghost positions load the mapped cell;
+  // the reversed momenta of wall ghosts are applied when the planes are read.
+  static_assert(!BND || DIM == 2, "boundaries and media are 2D only");
+  bool fx_own = false, fx_rx = false;
+  const int64_t wx = BND ? map_axis(gx, nx, kp.bc_lo, kp.bc_hi, fx_own) : wrap(gx, nx);
+  const int64_t wy = DIM == 3 ? wrap(gy, ny) : 0;
   const int64_t col = DIM == 3 ? wy * nx + wx : wx;          // index within a plane
   // second-ring positions loaded by the halo threads
   const bool ringx = (tx == 0) || (tx == TX - 1);
-  const int64_t col_rx = (DIM == 3 ? wy * nx : 0) + wrap(gx + (tx == 0 ? -1 : 1), nx);
+  const int64_t col_rx = (DIM == 3 ? wy * nx : 0) +
+                         (BND ? map_axis(gx + (tx == 0 ? -1 : 1), nx, kp.bc_lo, kp.bc_hi, fx_rx)
+                              : wrap(gx + (tx == 0 ? -1 : 1), nx));
+  // plane of the marching axis holding position p, and whether it is a wall ghost
+  auto plane_of = [&](int64_t p, bool& fy) -> int64_t {
+    if (!BND) {
+      fy = false;
+      return wrap(p, M);
+    }
+    return map_axis(p, M, kp.bc_ylo, kp.bc_yhi, fy);
+  };
+  const bool medium = BND && kp.act_lo != nullptr;
+  const bool pulses = BND && kp.pul_lo != nullptr;
   const bool ringy = DIM == 3 && ((ty == 0) || (ty == TY - 1));
   const int64_t col_ry = DIM == 3 ? wrap(gy + (ty == 0 ? -1 : 1), ny) * nx + wx : 0;
   const int oy = DIM == 3 ? ty + 1 : 0;
@@ -192,7 +246,8 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
   auto issue = [&](int64_t p) {
     const int sl = (int)(p & (D - 1));
     if (p <= q1 + 1) {
-      const int64_t o = wrap(p, M) * plane;
+      bool fy;
+      const int64_t o = plane_of(p, fy) * plane;
 #pragma unroll
       for (int f = 0; f < NF; ++f) cp_async<sizeof(R)>(&sR[sl][f][tid], Uin + f * ncell + o + col);
       if (p <= q1) {
@@ -211,7 +266,10 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
   R Wm_prev[NF], D_prev[NF], H_prev[NF], yE_prev = 0, yEv_prev = 0;
 #pragma unroll
   for (int f = 0; f < NF; ++f) Wm_prev[f] = D_prev[f] = H_prev[f] = (R)0;
-  auto pidx = [&](int64_t q) { return wrap(q, M) * plane; };
+  auto pidx = [&](int64_t q) {
+    bool fy;
+    return plane_of(q, fy) * plane;
+  };
   for (int64_t p = q0 - 2; p <= q0 + D - 4; ++p) issue(p);    // D - 1 planes ahead
 
   for (int64_t q = q0 - 1; q <= q1; ++q) {
@@ -219,15 +277,38 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
     //    landed; publish plane q
     cp_async_wait<D - 4>();
     const int sm = (int)((q - 1) & (D - 1)), s0 = (int)(q & (D - 1)), sp = (int)((q + 1) & (D - 1));
+    bool fym, fy0, fyp;
+    const int64_t jq = plane_of(q, fy0);
+    plane_of(q - 1, fym);
+    plane_of(q + 1, fyp);
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       Um1[f] = sR[sm][f][tid];
       Uq[f] = sR[s0][f][tid];
       Up1[f] = sR[sp][f][tid];
+    }
+    if (BND) {
+      if (fx_own) {
+        Um1[1] = -Um1[1];
+        Uq[1] = -Uq[1];
+        Up1[1] = -Up1[1];
+      }
+      if (fym) Um1[2] = -Um1[2];
+      if (fy0) Uq[2] = -Uq[2];
+      if (fyp) Up1[2] = -Up1[2];
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
       sU[f][oy][tx + 1] = Uq[f];
-      if (ringx) sU[f][oy][tx == 0 ? 0 : TX + 1] = sH[s0][f][hx];
+      if (ringx) {
+        R v = sH[s0][f][hx];
+        if (BND && ((f == 1 && fx_rx) || (f == 2 && fy0))) v = -v;
+        sU[f][oy][tx == 0 ? 0 : TX + 1] = v;
+      }
       if (DIM == 3 && ringy) sU[f][ty == 0 ? 0 : SY - 1][tx + 1] = sH[s0][f][hy];
     }
+    // medium of this cell (the mapped cell of a ghost): active or frozen
+    const bool active = !medium || (wx >= __ldg(kp.act_lo + jq) && wx < __ldg(kp.act_hi + jq));
     issue(q + D - 2);    // reuses the slot of plane q-2 (read one barrier ago)
     __syncthreads();
 
@@ -258,14 +339,14 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
       }
     }
     R yE, yEv;
-    C::source(k, Uq, yE, yEv);
+    C::source(k, Uq, yE, yEv, active);
     R uh[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) uh[f] = Uq[f] - dt_2h * div[f];
     uh[1 + DIM] += dt_2 * yE;
     uh[2 + DIM] += dt_2 * yEv;
     R yEh, yEvh;
-    C::source(k, uh, yEh, yEvh);
+    C::source(k, uh, yEh, yEvh, active);
 
     // c. transverse faces: publish +states, take the left neighbour's
 #pragma unroll
@@ -321,6 +402,9 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
       for (int f = 0; f < NF; ++f) un[f] = Um1[f] - dtdx * (D_prev[f] + Hq[f] - H_prev[f]);
       un[1 + DIM] += dt * yE_prev;
       un[2 + DIM] += dt * yEv_prev;
+      // a driven cell holds the pulsating source at the new time level
+      if (pulses && gx >= __ldg(kp.pul_lo + (q - 1)) && gx < __ldg(kp.pul_hi + (q - 1)))
+        pulse_state<R, NF>(kp, sc.t + sc.dt, un);
       const int64_t o = pidx(q - 1) + col;
 #pragma unroll
       for (int f = 0; f < NF; ++f) Uout[f * ncell + o] = un[f];
@@ -369,8 +453,18 @@ static cudaError_t launch_nd(const KParams& kp, void* a, void* b, Ctl* ctl, cons
                             int seg, cudaStream_t st) {
   using G = Cfg<DIM, PREC>;
   constexpr size_t smem = stepnd_smem<R, DIM, G::TX, G::TY>();
-  auto fn = stepnd_kernel<R, PP, LIM, SRC, DIM, G::TX, G::TY, G::MINB>;
-  if (!n) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const bool bnd = DIM == 2 && (kp.bc_lo != BC_PERIODIC || kp.bc_hi != BC_PERIODIC ||
+                                kp.bc_ylo != BC_PERIODIC || kp.bc_yhi != BC_PERIODIC ||
+                                kp.act_lo != nullptr || kp.pul_lo != nullptr);
+  auto fn = bnd ? stepnd_kernel<R, PP, LIM, SRC, DIM, G::TX, G::TY, G::MINB, DIM == 2>
+                : stepnd_kernel<R, PP, LIM, SRC, DIM, G::TX, G::TY, G::MINB, false>;
+  if (!n) {
+    cudaError_t e = cudaFuncSetAttribute(stepnd_kernel<R, PP, LIM, SRC, DIM, G::TX, G::TY, G::MINB, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess || DIM != 2) return e;
+    return cudaFuncSetAttribute(stepnd_kernel<R, PP, LIM, SRC, DIM, G::TX, G::TY, G::MINB, DIM == 2>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
   const int64_t nx = n[0], ny = n[1], nz = DIM == 3 ? n[2] : 1;
   const int tiles_x = (int)((nx + G::TX - 3) / (G::TX - 2));
   const int tiles_y = DIM == 3 ? (int)((ny + G::TY - 3) / (G::TY - 2)) : 1;

@@ -34,7 +34,7 @@ EXPORTS = ("sv_required_bytes", "sv_init", "sv_write_state", "sv_read_state", "s
            "sv_batch_mode_log", "sv_batch_free", "sv_step1d_noalloc", "sv_set_drive",
            "sv_set_launch", "sv_get_launch", "sv_num_configs", "sv_get_config", "sv_config_desc",
            "sv_set_config", "sv_autotune", "sv_batch_num_configs", "sv_batch_set_config",
-           "sv_batch_get_config")
+           "sv_batch_get_config", "sv_set_medium2d")
 
 
 class SvError(RuntimeError):
@@ -65,7 +65,15 @@ class _Drive(ctypes.Structure):
 
 class _Grid(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("L", ctypes.c_double * 3),
-                ("bc", ctypes.c_int * 2)]
+                ("bc", ctypes.c_int * 4)]
+
+
+class _Medium2d(ctypes.Structure):
+    _fields_ = [("active_lo", ctypes.POINTER(ctypes.c_int32)),
+                ("active_hi", ctypes.POINTER(ctypes.c_int32)),
+                ("driven_lo", ctypes.POINTER(ctypes.c_int32)),
+                ("driven_hi", ctypes.POINTER(ctypes.c_int32)),
+                ("omega", ctypes.c_double), ("amp", ctypes.c_double)]
 
 
 @dataclass
@@ -137,6 +145,7 @@ def lib() -> ctypes.CDLL:
     L.sv_batch_free.restype = None
     L.sv_set_drive.argtypes = [vp, ctypes.POINTER(_Drive)]
     L.sv_set_launch.argtypes = [vp, ctypes.c_int]
+    L.sv_set_medium2d.argtypes = [vp, ctypes.POINTER(_Medium2d)]
     L.sv_get_launch.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     ip = ctypes.POINTER(ctypes.c_int)
     L.sv_num_configs.argtypes = [vp, ip]
@@ -171,6 +180,8 @@ def _dp(a: np.ndarray):
 
 
 def grid(n, L=None, bc=(BC_PERIODIC, BC_PERIODIC)) -> _Grid:
+    """sv_grid for cells per axis n, lengths L (default: h = 1 / n[0]) and
+    boundary conditions bc = (x_lo, x_hi) or (x_lo, x_hi, y_lo, y_hi)."""
     n = tuple(int(x) for x in (n if hasattr(n, "__len__") else (n,)))
     if L is None:
         L = tuple(float(x) / n[0] for x in n)          # h = 1 / n[0]
@@ -180,7 +191,9 @@ def grid(n, L=None, bc=(BC_PERIODIC, BC_PERIODIC)) -> _Grid:
     for a in range(3):
         g.n[a] = n[a] if a < len(n) else 1
         g.L[a] = L[a] if a < len(L) else 1.0
-    g.bc[0], g.bc[1] = int(bc[0]), int(bc[1])
+    bc = tuple(int(b) for b in bc) + (BC_PERIODIC,) * (4 - len(bc))
+    for i in range(4):
+        g.bc[i] = bc[i]
     return g
 
 
@@ -305,6 +318,24 @@ class Solver:
             d.amp_re[f] = float(complex(amp[f]).real)
             d.amp_im[f] = float(complex(amp[f]).imag)
         _check(lib().sv_set_drive(self._h, ctypes.byref(d)), "sv_set_drive")
+
+    def set_medium2d(self, active_lo=None, active_hi=None, driven_lo=None, driven_hi=None,
+                     omega: float = 0.0, amp: float = 0.0):
+        """2D medium map (per row j: active medium for active_lo[j] <= i <
+        active_hi[j], frozen elsewhere; None: active everywhere) and driven
+        cells (per row: driven_lo[j] <= i < driven_hi[j] hold the pulsating
+        source of amplitude amp and angular frequency omega; None: none)."""
+        keep = []
+
+        def ptr(a):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.int32)
+            keep.append(a)
+            return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        m = _Medium2d(ptr(active_lo), ptr(active_hi), ptr(driven_lo), ptr(driven_hi),
+                      float(omega), float(amp))
+        _check(lib().sv_set_medium2d(self._h, ctypes.byref(m)), "sv_set_medium2d")
 
     def set_launch(self, mode: int):
         """LAUNCH_AUTO, LAUNCH_PER_STEP or LAUNCH_PERSISTENT (1D MUSCL-Hancock)."""
