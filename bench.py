@@ -479,6 +479,71 @@ def run_wc(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sector(args):
+    """The paper's 2D active-sector problem (Sec. 3) as set up in the inputs
+    module: a pulsating source (wavelength 0.1) at the apex of a 30-degree
+    sector of active medium (S = 1, tau0 = 0.0135; frozen outside), solid wall
+    at x = Lx reached by the front near t = 1, free outflow on the other
+    sides; args.side cells across (default 2048, ~148 cells per wavelength),
+    run to t = 1.2 (time to solution; amplitude in and outside the sector)."""
+    import torch
+    from paper_1805_03442_gb300 import inputs, sv
+    from paper_1805_03442_gb300.build import build
+    build()
+    nx = args.side or 2048
+    prec = {"fp32": sv.FP32, "fp64": sv.FP64, "fp32_p64": sv.FP32_P64}[args.precision]
+    pb = inputs.sector_problem(nx)
+    P = sv.Params(precision=prec, S=1.0, tau0=0.0135)
+    U0 = inputs.sector_rest_state(P.gamma, P.Ck, P.S, pb.nx, pb.ny)
+    lo, hi, dlo, dhi = pb.maps
+    stream = torch.cuda.Stream()
+    n = (pb.nx, pb.ny)
+    s = sv.Solver(P, n, (pb.nx * pb.h, pb.ny * pb.h), stream=stream, bc=pb.bc)
+    s.set_medium2d(lo, hi, dlo, dhi, pb.omega, pb.amp)
+    from paper_1805_03442_gb300 import tune
+    tuned = tune.tune_solver(s, tune.solver_key(P, n) + "/bnd", tune.device_name())
+    s.write_state(U0)
+    s.run_to(0.01)                     # warm-up (graph capture, clocks)
+    s.write_state(U0)
+    torch.cuda.synchronize()
+    t_end = 1.2
+    with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t0 = time.perf_counter()
+        rc, steps = s.run_to(t_end, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    U, t = s.read_state()
+    status = s.status()
+    s.close()
+    # wave amplitude on the arc 0.8 < r < 1.0 from the source: inside the sector
+    # (|angle| < 10 deg) and outside it (40-90 deg off the axis)
+    rho = U[0].reshape(pb.ny, pb.nx) - 1.0
+    X, Y = np.meshgrid((np.arange(pb.nx) + 0.5) * pb.h - pb.apex[0],
+                       (np.arange(pb.ny) + 0.5) * pb.h - pb.apex[1])
+    r, ang = np.hypot(X, Y), np.degrees(np.abs(np.arctan2(Y, X)))
+    arc = (r > 0.8) & (r < 1.0)
+    amp_in = float(np.abs(rho[arc & (ang < 10)]).max())
+    amp_out = float(np.abs(rho[arc & (ang > 40) & (ang < 90)]).max())
+    cells = pb.nx * pb.ny
+    line = {"metric": "cell-updates/s", "value": cells * steps / wall, "unit": "cell-updates/s",
+            "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": 1e3 * wall / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp64": "f64", "fp32_p64": "f32"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": f"2D active sector, {pb.nx}x{pb.ny} cells, walls/outflow, "
+                                   f"pulsating source lambda 0.1, S=1, tau0=0.0135, t_end {t_end}",
+                       "cells": cells, "l2": "not flushed: whole run timed",
+                       "launch_config": tuned["config"]},
+            "time_to_solution_s": wall, "gpu_event_s": e0.elapsed_time(e1) * 1e-3,
+            "status": rc, "status_flags": status, "sim_time": t,
+            "amplitude_in_sector": amp_in, "amplitude_outside": amp_out,
+            "gpu_launches": steps, "clocks": getattr(clk, "result", None)}
+    print(json.dumps(line), flush=True)
+
+
 def run_driven(args):
     """The forced-source problem of the paper's Sec. 3: a wave of wavelength
     ~0.1 driven into the active medium (S = 0.5, tau0 = 0.0135) at x = 0, free
@@ -535,7 +600,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_p64"])
     ap.add_argument("--n", type=int, default=1 << 22, help="cells of the 1d workload")
-    ap.add_argument("--workload", default="1d", choices=sorted(WORKLOADS) + ["sweep", "wc", "driven"])
+    ap.add_argument("--workload", default="1d",
+                    choices=sorted(WORKLOADS) + ["sweep", "wc", "driven", "sector"])
     ap.add_argument("--side", type=int, default=0,
                     help="cells per axis of the 2d / 3d workloads (default 8192 / 512)")
     ap.add_argument("--runs", type=int, default=4096, help="runs of the sweep workload")
@@ -549,6 +615,8 @@ def main():
         run_sweep(args)
     elif args.workload == "wc":
         run_wc(args)
+    elif args.workload == "sector":
+        run_sector(args)
     elif args.workload == "driven":
         run_driven(args)
     else:

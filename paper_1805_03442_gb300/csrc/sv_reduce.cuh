@@ -34,6 +34,16 @@ template <> struct TauKey<double> {
   static __device__ __forceinline__ double tau_min(const KParams&, double a) { return -a; }
 };
 
+// |v| from v.v for the eq. 16 bound of 2D / 3D states.  In float,
+// x * rsqrt(x) of a subnormal v.v (the far tail of a wave still spreading into
+// gas at rest) flushes the rsqrt argument to zero and gives +inf; a speed
+// below 1e-19 cannot change max(2|v|, |v| + c) in float, so it counts as 0.
+template <typename R>
+__device__ __forceinline__ R speed_of(R v2) {
+  if (std::is_same<R, float>::value) return v2 >= (R)1.17549435e-38 ? Ar<R>::sqrt_pos(v2) : (R)0;
+  return v2 > (R)0 ? Ar<R>::sqrt_pos(v2) : (R)0;
+}
+
 // Signal speed, tau key and physicality of one updated state (dim-generic),
 // folded into per-thread maxima of the kernel's own type.
 // `kin2` = rho |v|^2, `vmag` = |v|.  SRC 0 (frozen) has no tau bound.

@@ -413,7 +413,7 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
       R v2 = 0;
 #pragma unroll
       for (int a = 0; a < DIM; ++a) v2 += v[a] * v[a];
-      const R vmag = v2 > (R)0 ? Ar<R>::sqrt_pos(v2) : (R)0;
+      const R vmag = speed_of<R>(v2);
       R kin2 = 0;
 #pragma unroll
       for (int a = 0; a < DIM; ++a) kin2 += un[1 + a] * v[a];

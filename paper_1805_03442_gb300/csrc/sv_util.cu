@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(NTU) dt_reduce_kernel(const KParams kp, const 
       kin2 += m * v;
       v2 += v * v;
     }
-    const R vmag = dim == 1 ? fabs(U[ncell + i] * ir) : (v2 > (R)0 ? Ar<R>::sqrt_pos(v2) : (R)0);
+    const R vmag = dim == 1 ? fabs(U[ncell + i] * ir) : speed_of<R>(v2);
     cfl_cell<R, PP, 1>(k, rho, kin2, vmag, U[(1 + dim) * ncell + i], U[(2 + dim) * ncell + i],
                        smax, akey, flags);
   }

@@ -109,11 +109,33 @@ def test_fp32_sector_problem_close_to_oracle(sv):
         s.step(60)
         U, t = s.read_state()
         k = s.time()[1]
+        assert s.status() == 0 and k == 60
     ref, tr, kr, rcr = O.run2m(Po, U0, pb.nx, pb.ny, pb.h, t, pb.bc, M)
     assert rcr == 0 and abs(kr - k) <= 1
     amp = np.max(np.abs(ref[0] - 1.0))
     assert amp > 1e-4
     assert np.max(np.abs(U[0] - ref[0])) <= 2e-3 * amp + 1e-6
+
+
+@pytest.mark.parametrize("prec", ["FP32", "FP64"])
+def test_subnormal_speeds_do_not_stop_the_run(sv, prec):
+    """Gas at rest with velocities whose squares are subnormal in float (the
+    far tail of a wave spreading into still gas): the eq. 16 bound is that of
+    the gas at rest, and stepping goes on."""
+    n = (64, 48)
+    P = sv.Params(precision=getattr(sv, prec))
+    rest = inputs.sector_rest_state(1.4, P.Ck, P.S, *n)
+    tiny = rest.copy()
+    tiny[1, ::7] = 3e-22                  # (3e-22)^2 = 9e-44 < FLT_MIN
+    tiny[2, ::5] = -2e-21
+    dts = []
+    for U in (rest, tiny):
+        with sv.Solver(P, n, None, bc=(OUT, WALL, OUT, OUT)) as s:
+            s.write_state(U)
+            dts.append(s.dt())
+            s.step(30)
+            assert s.status() == 0 and s.time()[1] == 30
+    assert dts[1] == dts[0]
 
 
 def test_medium_map_everywhere_and_nowhere(sv):
