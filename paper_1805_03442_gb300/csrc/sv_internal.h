@@ -41,6 +41,11 @@ int stepnd_grid(int dim, int precision, const KParams& kp);
 int stepnd_default_seg(int dim, int precision);
 cudaError_t stepnd_launch(int dim, int precision, const KParams& kp, void* a, void* b, Ctl* ctl,
                           const int64_t* n, int seg, cudaStream_t st);
+// The float (all-float pressure) 2D / 3D step marching plane pairs
+// (sv_stepnd_pair.cu); n == nullptr sets the kernels' shared-memory limits
+int stepnd_pair_default_seg(int dim);
+cudaError_t stepnd_pair_launch(int dim, const KParams& kp, void* a, void* b, Ctl* ctl,
+                               const int64_t* n, int seg, cudaStream_t st);
 
 // Batched sweep kernels of 256 (sv_batch.cu) and 128 (sv_batch128.cu) threads
 void* batch_pick256(int limiter, int precision);

@@ -25,6 +25,7 @@
 // planes in shared memory with cp.async, four planes ahead of the one being
 // computed; copies are coalesced along x.
 #include "sv_internal.h"
+#include "sv_ndbnd.cuh"
 #include "sv_step1d.cuh"      // cp.async helpers
 
 namespace sv {
@@ -113,37 +114,6 @@ struct Nd {
     for (int f = 0; f < NF; ++f) F[f] = wl * FL[f] + wr * FR[f] + wd * (Rr[f] - L[f]);
   }
 };
-
-// Cell whose state position j of an axis of n cells holds: periodic wrap,
-// wall mirror (flip: the normal momentum is reversed) or outflow copy.
-// Positions further out than the two ghost layers are clamped into the grid;
-// their values reach no updated cell.
-__device__ __forceinline__ int64_t map_axis(int64_t j, int64_t n, int bc_lo, int bc_hi,
-                                            bool& flip) {
-  flip = false;
-  if (j >= 0 && j < n) return j;
-  const int bc = j < 0 ? bc_lo : bc_hi;
-  if (bc == BC_PERIODIC) return wrap(j, n);
-  if (bc == BC_REFLECT) {
-    flip = true;
-    const int64_t m = j < 0 ? -1 - j : 2 * n - 1 - j;
-    return m < 0 ? 0 : (m >= n ? n - 1 : m);
-  }
-  return j < 0 ? 0 : n - 1;
-}
-
-// The pulsating source of the 2D problem at time t (double, like its
-// definition), in the kernel's type.
-template <typename R, int NF>
-__device__ __forceinline__ void pulse_state(const KParams& kp, double t, R (&u)[NF]) {
-  const double s = kp.pul_amp * sin(kp.pul_omega * t);
-  const double rho = 1.0 + s, p = 1.0 + kp.gamma * s, Ev = rho * kp.pul_ev;
-#pragma unroll
-  for (int f = 0; f < NF; ++f) u[f] = (R)0;
-  u[0] = (R)rho;
-  u[NF - 2] = (R)(p / kp.g1 + Ev);
-  u[NF - 1] = (R)Ev;
-}
 
 // Planes per thread ring (a power of two; four planes are in flight).
 constexpr int kPlaneRing = 8;
@@ -487,7 +457,11 @@ static cudaError_t by_prec(int precision, const KParams& kp, void* a, void* b, C
   switch (precision) {
     case PREC_FP64: return launch_nd<double, 0, LIM, SRC, DIM, PREC_FP64>(kp, a, b, ctl, n, seg, st);
     case PREC_FP32_P64: return launch_nd<float, 1, LIM, SRC, DIM, PREC_FP32_P64>(kp, a, b, ctl, n, seg, st);
-    default: return launch_nd<float, 0, LIM, SRC, DIM, PREC_FP32>(kp, a, b, ctl, n, seg, st);
+    default:
+      // 2D: packed plane pairs; 3D keeps one cell per thread (the pair kernel
+      // needs 242 registers there, one block per SM, and runs 17% slower)
+      if (DIM == 2) return stepnd_pair_launch(DIM, kp, a, b, ctl, n, seg, st);
+      return launch_nd<float, 0, LIM, SRC, DIM, PREC_FP32>(kp, a, b, ctl, n, seg, st);
   }
 }
 
@@ -511,7 +485,8 @@ static cudaError_t by_lim(int precision, const KParams& kp, void* a, void* b, Ct
 
 // Default planes per block segment along the marching axis.
 int stepnd_default_seg(int dim, int precision) {
-  if (dim == 2) return precision == PREC_FP64 ? Cfg<2, PREC_FP64>::SEG : Cfg<2, PREC_FP32>::SEG;
+  if (precision == PREC_FP32 && dim == 2) return stepnd_pair_default_seg(dim);
+  if (dim == 2) return precision == PREC_FP64 ? Cfg<2, PREC_FP64>::SEG : Cfg<2, PREC_FP32_P64>::SEG;
   return precision == PREC_FP64 ? Cfg<3, PREC_FP64>::SEG : Cfg<3, PREC_FP32>::SEG;
 }
 
