@@ -173,8 +173,9 @@ int sv_get_launch(sv_solver* s, int* mode);
  * in a few launch configurations that compute bitwise the same states and
  * differ only in speed:
  *   1D float MUSCL-Hancock, >= 4096 cells: 512-cell block tiles at a register
- *     budget of 3 blocks/SM (default) or 2 blocks/SM, or warps sliding over
- *     64-cell chunks (the kernel of every other 1D solver, its only config);
+ *     budget of 3 blocks/SM (default) or 2 blocks/SM, 1024-cell tiles with two
+ *     cell pairs per thread, or warps sliding over 64-cell chunks (the kernel
+ *     of every other 1D solver, its only config);
  *   2D / 3D: planes per block along the marching axis, 64 / 128 / 256 / 512.
  * sv_autotune times each configuration on the solver's current state and
  * keeps the fastest; the state, time and status are restored afterwards.

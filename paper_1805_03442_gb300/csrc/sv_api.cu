@@ -22,7 +22,7 @@ using namespace sv;
 // One launch configuration of a solver's per-step kernel (sv_set_config).
 struct SolverConfig {
   int kind;        // CFG_TILE, CFG_SLIDE or CFG_ND
-  int param;       // TILE: blocks per SM of the register budget; ND: planes per segment
+  int param;       // TILE: 10 x cell pairs per thread + blocks per SM; ND: planes per segment
   const char* desc;
 };
 enum { CFG_TILE = 0, CFG_SLIDE = 1, CFG_ND = 2 };
@@ -188,9 +188,10 @@ void build_configs(sv_solver* s) {
   s->cfgs.clear();
   if (s->dim == 1) {
     if (s->p.method == SV_HANCOCK && s->p.precision == SV_FP32 && s->ncell >= kTile1dMinCells) {
-      s->cfgs.push_back({CFG_TILE, 3,
+      s->cfgs.push_back({CFG_TILE, 13,
                          "1D: 512-cell block tiles, 2 cells per thread, 80 registers, 3 blocks/SM"});
-      s->cfgs.push_back({CFG_TILE, 2, "1D: 512-cell block tiles, 2 cells per thread, 2 blocks/SM"});
+      s->cfgs.push_back({CFG_TILE, 12, "1D: 512-cell block tiles, 2 cells per thread, 2 blocks/SM"});
+      s->cfgs.push_back({CFG_TILE, 22, "1D: 1024-cell block tiles, 4 cells per thread, 2 blocks/SM"});
     }
     s->cfgs.push_back({CFG_SLIDE, 0, "1D: warps sliding over 64-cell chunks, 2 cells per thread"});
   } else {

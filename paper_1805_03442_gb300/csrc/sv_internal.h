@@ -20,9 +20,10 @@ cudaError_t step1d_launch(int precision, const KParams& kp, void* a, void* b, Ct
 // Float 1D MUSCL-Hancock step on block tiles (sv_tile1d.cu), grids of at
 // least kTile1dMinCells cells
 constexpr int64_t kTile1dMinCells = 4096;
-// minb: register budget in blocks per SM (3 or 2)
-int tile1d_grid(const KParams& kp, int minb);
-cudaError_t tile1d_launch(const KParams& kp, int minb, void* a, void* b, Ctl* ctl, int64_t N,
+// var = 10 * (cell pairs per thread) + (blocks per SM of the register budget):
+// 13, 12 or 22
+int tile1d_grid(const KParams& kp, int var);
+cudaError_t tile1d_launch(const KParams& kp, int var, void* a, void* b, Ctl* ctl, int64_t N,
                           int grid, cudaStream_t st);
 
 // 1D persistent loop of up to nmax steps (sv_loop1d.cu); grid 0 = unavailable

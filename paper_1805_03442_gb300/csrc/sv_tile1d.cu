@@ -29,15 +29,20 @@ namespace sv {
 namespace {
 
 constexpr int NTT = 256;                 // threads per block
-constexpr int TILE = 2 * NTT;            // cells computed per tile
-constexpr int OUT = TILE - 4;            // cells written per tile
-constexpr int SPAN = TILE + 4;           // cells held per tile: [b - 2, b + TILE + 2)
 constexpr int NWT = NTT / 32;
 
-struct TileSmem {
-  float u[2][4][SPAN];                   // double-buffered tile, field-major
-  float wp[NWT][4];                      // lane 31's odd-cell right face state, per warp
-  float fl[NWT][4];                      // lane 0's left face flux, per warp
+// A tile of NPT cell pairs per thread: 2 NPT NTT cells computed, the two at
+// each end only for their neighbours' faces.
+template <int NPT> struct Tile {
+  static constexpr int CELLS = 2 * NPT * NTT;   // cells computed per tile
+  static constexpr int OUT = CELLS - 4;         // cells written per tile
+  static constexpr int SPAN = CELLS + 4;        // cells held: [b - 2, b + CELLS + 2)
+};
+
+template <int NPT> struct TileSmem {
+  float u[2][4][Tile<NPT>::SPAN];        // double-buffered tile, field-major
+  float wp[NWT][4];                      // lane 31's last right face state, per warp
+  float fl[NWT][4];                      // lane 0's first left face flux, per warp
 };
 
 __device__ __forceinline__ void cp16(void* smem, const void* gmem) {
@@ -45,15 +50,16 @@ __device__ __forceinline__ void cp16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
-// Fill buffer `dst` with tile b's cells [b - 2, b + TILE + 2).  Interior tiles
+// Fill buffer `dst` with tile b's cells [b - 2, b + SPAN - 2).  Interior tiles
 // of a grid whose fields start on 16-byte boundaries use 16-byte copies; the
 // others go cell by cell through the boundary mapping (periodic wrap, wall
 // mirror, outflow copy, driven ghost state).  Commits one cp.async group.
+template <int SPAN>
 __device__ __forceinline__ void load_tile(float (*dst)[SPAN], const float* Uin, int N, int b,
                                           const P<float>& k, const KParams& kp, double t) {
   const int lo = b - 2;
   if ((N & 3) == 0 && lo >= 0 && lo + SPAN <= N) {
-    // lo = b - 2 is a multiple of 4 (b = OUT * i - 2, OUT = 508)
+    // lo = b - 2 is a multiple of 4 (b = OUT i - 2 with OUT a multiple of 4)
     for (int e = threadIdx.x; e < 4 * (SPAN / 4); e += NTT) {
       const int f = e / (SPAN / 4), q = e - f * (SPAN / 4);
       cp16(&dst[f][4 * q], Uin + (size_t)f * N + lo + 4 * q);
@@ -80,11 +86,12 @@ __device__ __forceinline__ void load_tile(float (*dst)[SPAN], const float* Uin, 
   cp_async_commit();
 }
 
-template <int LIM, int SRC, int MINB>
+template <int LIM, int SRC, int MINB, int NPT>
 __global__ void __launch_bounds__(NTT, MINB)
 tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bufB,
               Ctl* __restrict__ ctl, int N) {
   using pk::f2;
+  constexpr int CELLS = Tile<NPT>::CELLS, OUT = Tile<NPT>::OUT, SPAN = Tile<NPT>::SPAN;
   const StepCtl sc = block_step_ctl(ctl);
   if (!(sc.dt > 0.0)) return;                     // stopped, or t_end reached
   const float* __restrict__ Uin = sc.cur ? bufB : bufA;
@@ -97,7 +104,7 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
   const f2 ndt_2h2 = pk::splat(-sd.dt_2h), dt_22 = pk::splat(sd.dt_2);
 
   extern __shared__ __align__(16) unsigned char smem_tile[];
-  TileSmem& S = *reinterpret_cast<TileSmem*>(smem_tile);
+  TileSmem<NPT>& S = *reinterpret_cast<TileSmem<NPT>*>(smem_tile);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int src_m = (lane + 31) & 31, src_p = (lane + 1) & 31;
   const int ntile = (N + OUT - 1) / OUT;
@@ -106,68 +113,85 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
   uint32_t flags = 0;
 
   int tile = blockIdx.x;
-  if (tile < ntile) load_tile(S.u[0], Uin, N, OUT * tile - 2, k, kp, t);
+  if (tile < ntile) load_tile<SPAN>(S.u[0], Uin, N, OUT * tile - 2, k, kp, t);
   for (int it = 0; tile < ntile; ++it, tile += gridDim.x) {
     const int buf = it & 1;
     const int b = OUT * tile - 2;
     cp_async_wait<0>();
     __syncthreads();                              // tile in place; the other buffer is free
     if (tile + (int)gridDim.x < ntile)
-      load_tile(S.u[buf ^ 1], Uin, N, OUT * (tile + gridDim.x) - 2, k, kp, t);
+      load_tile<SPAN>(S.u[buf ^ 1], Uin, N, OUT * (tile + gridDim.x) - 2, k, kp, t);
 
-    // the pair sits at span offsets 2 + 2t, 3 + 2t
-    const int pos = 2 + 2 * threadIdx.x;
-    f2 X[4], XM[4], A[4], B[4];
+    // pair p of the thread sits at span offsets 2 + 2 (NPT t + p) and the next
+    f2 X[NPT][4], XM[NPT][4], WP[NPT][4], WM[NPT][4], YE[NPT], YEv[NPT];
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      const float* rf = S.u[buf][f];
-      X[f] = *reinterpret_cast<const f2*>(rf + pos);
-      XM[f] = pk::pair(rf[pos - 1], X[f].x);
-      A[f] = pk::sub(X[f], XM[f]);
-      B[f] = pk::sub(pk::pair(X[f].y, rf[pos + 2]), X[f]);
+    for (int p = 0; p < NPT; ++p) {
+      const int pos = 2 + 2 * (NPT * (int)threadIdx.x + p);
+      f2 A[4], B[4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const float* rf = S.u[buf][f];
+        X[p][f] = *reinterpret_cast<const f2*>(rf + pos);
+        XM[p][f] = pk::pair(rf[pos - 1], X[p][f].x);
+        A[f] = pk::sub(X[p][f], XM[p][f]);
+        B[f] = pk::sub(pk::pair(X[p][f].y, rf[pos + 2]), X[p][f]);
+      }
+      pk::predict<LIM, SRC>(k, X[p], A, B, ndt_2h2, dt_22, WP[p], WM[p], YE[p], YEv[p]);
     }
-    f2 WP[4], WM[4], YE, YEv;
-    pk::predict<LIM, SRC>(k, X, A, B, ndt_2h2, dt_22, WP, WM, YE, YEv);
 
     if (lane == 31) {
 #pragma unroll
-      for (int f = 0; f < 4; ++f) S.wp[w][f] = WP[f].y;
+      for (int f = 0; f < 4; ++f) S.wp[w][f] = WP[NPT - 1][f].y;
     }
     __syncthreads();
-    f2 L[4], F[4];
+    // left state of the first pair's left face: lane - 1's last pair
+    float nb[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-      const float nb = __shfl_sync(0xffffffffu, WP[f].y, src_m);
-      // thread 0's left face is outside the written cells: any physical state
-      L[f] = pk::pair(lane ? nb : (w ? S.wp[w - 1][f] : (f == 0 || f == 2 ? 1.0f : 0.0f)), WP[f].x);
+      const float v = __shfl_sync(0xffffffffu, WP[NPT - 1][f].y, src_m);
+      // thread 0's first left face is outside the written cells: any physical state
+      nb[f] = lane ? v : (w ? S.wp[w - 1][f] : (f == 0 || f == 2 ? 1.0f : 0.0f));
     }
-    pk::hll(k, L, WM, XM, X, F);                  // faces b + 2t - 1/2 and b + 2t + 1/2
+    f2 F[NPT][4];
+#pragma unroll
+    for (int p = 0; p < NPT; ++p) {
+      f2 L[4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) L[f] = pk::pair(p ? WP[p - 1][f].y : nb[f], WP[p][f].x);
+      pk::hll(k, L, WM[p], XM[p], X[p], F[p]);    // the pair's left and inner faces
+    }
 
     if (lane == 0) {
 #pragma unroll
-      for (int f = 0; f < 4; ++f) S.fl[w][f] = F[f].x;
+      for (int f = 0; f < 4; ++f) S.fl[w][f] = F[0][f].x;
     }
     __syncthreads();
-    f2 FR[4];
+    // right face of the last pair's odd cell: lane + 1's first left face
+    float nf[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-      const float nb = __shfl_sync(0xffffffffu, F[f].x, src_p);
-      FR[f] = pk::pair(F[f].y, lane < 31 ? nb : (w < NWT - 1 ? S.fl[w + 1][f] : 0.0f));
+      const float v = __shfl_sync(0xffffffffu, F[0][f].x, src_p);
+      nf[f] = lane < 31 ? v : (w < NWT - 1 ? S.fl[w + 1][f] : 0.0f);
     }
-    const int j = b + 2 * threadIdx.x;            // global index of the even cell
-    if (threadIdx.x >= 1 && threadIdx.x < NTT - 1 && j < N) {
-      f2 Nw[4];
-      pk::update<SRC>(X, F, FR, YE, YEv, dt2, ndtdx2, Nw);
-      const bool two = j + 1 < N;
-      pk::cfl<SRC>(k, Nw, two ? 3 : 1, smax, akey, flags);
-      if (two && (N & 1) == 0) {
 #pragma unroll
-        for (int f = 0; f < 4; ++f) *reinterpret_cast<f2*>(Uout + (size_t)f * N + j) = Nw[f];
-      } else {
+    for (int p = 0; p < NPT; ++p) {
+      const int j = b + 2 * (NPT * (int)threadIdx.x + p);   // global index of the even cell
+      if (j >= b + 2 && j < b + CELLS - 2 && j < N) {
+        f2 FR[4], Nw[4];
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          Uout[(size_t)f * N + j] = Nw[f].x;
-          if (two) Uout[(size_t)f * N + j + 1] = Nw[f].y;
+        for (int f = 0; f < 4; ++f) FR[f] = pk::pair(F[p][f].y, p < NPT - 1 ? F[p + 1][f].x : nf[f]);
+        pk::update<SRC>(X[p], F[p], FR, YE[p], YEv[p], dt2, ndtdx2, Nw);
+        const bool two = j + 1 < N;
+        pk::cfl<SRC>(k, Nw, two ? 3 : 1, smax, akey, flags);
+        if (two && (N & 1) == 0) {
+#pragma unroll
+          for (int f = 0; f < 4; ++f) *reinterpret_cast<f2*>(Uout + (size_t)f * N + j) = Nw[f];
+        } else {
+#pragma unroll
+          for (int f = 0; f < 4; ++f) {
+            Uout[(size_t)f * N + j] = Nw[f].x;
+            if (two) Uout[(size_t)f * N + j + 1] = Nw[f].y;
+          }
         }
       }
     }
@@ -176,62 +200,68 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
   reduce_and_finalize<float, NTT>(ctl, kp, smax, akey, flags, true);
 }
 
-// Register budgets: MINB 3 blocks per SM caps the kernel at 80 registers
-// (24 warps per SM), MINB 2 leaves it its natural ~94 (16 warps per SM).
+// Variants (tile1d_grid / tile1d_launch `var` = 10 NPT + MINB): one cell pair
+// per thread at a register budget of 3 blocks per SM (80 registers, 24 warps
+// per SM) or 2 (its natural ~94 registers), or two pairs per thread (1024-cell
+// tiles: half the barriers and exchanges per cell, two independent chains)
+// at 2 blocks per SM.
 template <int LIM, int SRC>
 struct KT {
-  static constexpr auto fn3 = tile1d_kernel<LIM, SRC, 3>;
-  static constexpr auto fn2 = tile1d_kernel<LIM, SRC, 2>;
+  static constexpr auto fn13 = tile1d_kernel<LIM, SRC, 3, 1>;
+  static constexpr auto fn12 = tile1d_kernel<LIM, SRC, 2, 1>;
+  static constexpr auto fn22 = tile1d_kernel<LIM, SRC, 2, 2>;
 };
 
 template <int LIM, int SRC>
-void* pick_minb(int minb) {
-  return minb == 2 ? (void*)KT<LIM, SRC>::fn2 : (void*)KT<LIM, SRC>::fn3;
+void* pick_var(int var) {
+  if (var == 12) return (void*)KT<LIM, SRC>::fn12;
+  if (var == 22) return (void*)KT<LIM, SRC>::fn22;
+  return (void*)KT<LIM, SRC>::fn13;
 }
 
 template <int LIM>
-void* pick_src(int src, int minb) {
+void* pick_src(int src, int var) {
   switch (src) {
-    case 0: return pick_minb<LIM, 0>(minb);
-    case 1: return pick_minb<LIM, 1>(minb);
-    default: return pick_minb<LIM, 2>(minb);
+    case 0: return pick_var<LIM, 0>(var);
+    case 1: return pick_var<LIM, 1>(var);
+    default: return pick_var<LIM, 2>(var);
   }
 }
 
-void* pick(const KParams& kp, int minb) {
+void* pick(const KParams& kp, int var) {
   const int src = kp.frozen ? 0 : (kp.qi_zero ? 1 : 2);
   switch (kp.limiter) {
-    case 1: return pick_src<1>(src, minb);
-    case 2: return pick_src<2>(src, minb);
-    default: return pick_src<0>(src, minb);
+    case 1: return pick_src<1>(src, var);
+    case 2: return pick_src<2>(src, var);
+    default: return pick_src<0>(src, var);
   }
 }
+
+size_t smem_of(int var) { return var == 22 ? sizeof(TileSmem<2>) : sizeof(TileSmem<1>); }
 
 }  // namespace
 
 // Sets the kernel's shared-memory limit (host side, outside any capture) and
-// returns the persistent grid size for the register budget `minb` (blocks per
-// SM: 3 or 2), 0 on failure.
-int tile1d_grid(const KParams& kp, int minb) {
+// returns the persistent grid size of variant `var` (13, 12 or 22), 0 on failure.
+int tile1d_grid(const KParams& kp, int var) {
   int dev = 0, sms = 0, per = 0;
-  const void* fn = pick(kp, minb);
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem)) !=
-      cudaSuccess)
+  const void* fn = pick(kp, var);
+  const size_t smem = smem_of(var);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, NTT, sizeof(TileSmem)) != cudaSuccess)
-    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, NTT, smem) != cudaSuccess) return 0;
   if (per < 1) per = 1;
   return sms * per;
 }
 
-cudaError_t tile1d_launch(const KParams& kp, int minb, void* a, void* b, Ctl* ctl, int64_t N,
+cudaError_t tile1d_launch(const KParams& kp, int var, void* a, void* b, Ctl* ctl, int64_t N,
                           int grid, cudaStream_t st) {
   if (N >= (1LL << 31) / 4 || N < kTile1dMinCells || grid < 1) return cudaErrorInvalidValue;
   int n32 = (int)N;
   void* args[] = {(void*)&kp, &a, &b, &ctl, &n32};
-  return cudaLaunchKernel(pick(kp, minb), dim3(grid), dim3(NTT), args, sizeof(TileSmem), st);
+  return cudaLaunchKernel(pick(kp, var), dim3(grid), dim3(NTT), args, smem_of(var), st);
 }
 
 }  // namespace sv

@@ -48,7 +48,8 @@ def assert_all_equal(out):
 def test_1d_float_configs_bitwise(sv, N):
     P = sv.Params(precision=sv.FP32)
     descs, out = run_each_config(sv, P, (N,), wave_1d(N, seed=N), 30)
-    assert len(descs) == 3 and "block tiles" in descs[0] and "sliding" in descs[2]
+    assert len(descs) == 4 and "block tiles" in descs[0] and "4 cells per thread" in descs[2]
+    assert "sliding" in descs[3]
     assert_all_equal(out)
 
 
