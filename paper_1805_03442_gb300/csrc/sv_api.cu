@@ -423,7 +423,7 @@ int sv_step(sv_solver* s, int64_t nsteps) {
 
 int sv_run_to(sv_solver* s, double t_end, int64_t max_steps, int64_t* steps_taken) {
   if (!s || max_steps < 0 || isnan(t_end)) return SV_EINVAL;
-  SV_TRY(set_target_launch(s->ctl, t_end, s->h, s->stream));
+  SV_TRY(set_target_launch(s->p.precision, s->ctl, t_end, s->kp, s->stream));
   int rc = read_ctl(s);
   if (rc != SV_OK) return rc;
   const int64_t n0 = s->host_ctl->nsteps;
@@ -454,7 +454,7 @@ int sv_run_to(sv_solver* s, double t_end, int64_t max_steps, int64_t* steps_take
   (void)issued;
   if (steps_taken) *steps_taken = s->host_ctl->nsteps - n0;
   // clear the target so that later sv_step calls are not clamped
-  SV_TRY(set_target_launch(s->ctl, INFINITY, s->h, s->stream));
+  SV_TRY(set_target_launch(s->p.precision, s->ctl, INFINITY, s->kp, s->stream));
   return status;
 }
 

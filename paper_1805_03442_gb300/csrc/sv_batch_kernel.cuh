@@ -134,7 +134,7 @@ batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns
       }
       block_max<NTB>(smax, akey, flags, s_a, s_b, s_f);
       if (threadIdx.x == 0) {
-        const double dt = dt_from_maxima<R>(kp, (double)smax, (double)akey, flags);
+        const double dt = dt_from_maxima(kp, smax, akey, flags);
         double t = rd->t;
         rd->flags = flags;
         s_t = t;
@@ -145,7 +145,7 @@ batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns
           s_dt = t_end - t;
           s_last = 1;
         }
-        const StepDt<R> sd(s_dt, kp.h);
+        const StepDt<R> sd(s_dt, kp);
         s_step[0] = sd.dt;
         s_step[1] = sd.dtdx;
         s_step[2] = sd.dt_2h;
@@ -184,7 +184,7 @@ batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns
       cur ^= 1u;
       ++steps;
       if (threadIdx.x == 0) {
-        const double dt_next = dt_from_maxima<R>(kp, (double)smax, (double)akey, flags);
+        const double dt_next = dt_from_maxima(kp, smax, akey, flags);
         const double t = s_last ? t_end : s_t + dtd;
         s_t = t;
         if (steps >= max_steps && t < t_end) flags |= FLAG_MAXSTEPS;
@@ -196,7 +196,7 @@ batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns
           s_dt = t_end - t;
           s_last = 1;
         }
-        const StepDt<R> sd(s_dt, kp.h);
+        const StepDt<R> sd(s_dt, kp);
         s_step[0] = sd.dt;
         s_step[1] = sd.dtdx;
         s_step[2] = sd.dt_2h;

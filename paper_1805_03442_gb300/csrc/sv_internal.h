@@ -56,7 +56,8 @@ void* batch_pick128(int limiter, int precision);
 cudaError_t ctl_reset_launch(Ctl* ctl, double t, cudaStream_t st);
 cudaError_t dt_reduce_launch(int precision, int dim, const KParams& kp, const void* a,
                              const void* b, Ctl* ctl, int64_t ncell, cudaStream_t st);
-cudaError_t set_target_launch(Ctl* ctl, double t_end, double h, cudaStream_t st);
+cudaError_t set_target_launch(int precision, Ctl* ctl, double t_end, const KParams& kp,
+                              cudaStream_t st);
 cudaError_t to_state_launch(int precision, const double* src, void* a, void* b, Ctl* ctl,
                             int64_t count, cudaStream_t st);
 cudaError_t from_state_launch(int precision, const void* a, const void* b, const Ctl* ctl,

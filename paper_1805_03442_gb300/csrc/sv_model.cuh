@@ -49,6 +49,9 @@ struct KParams {
   // float copies for the float kernels (kparams_finish): the twelve values
   // above, then log2(1/tau0) (0 in the frozen limit), -tau_rho, -tau_T
   float f[16];
+  // float constants of the dt rule of the float solvers: cfl h, 1/h, 1/(2h),
+  // c_tau tau0 (0 in the frozen limit)
+  float fdt[4];
 };
 
 // Fill the float copies once on the host, so float kernels convert nothing.
@@ -60,6 +63,10 @@ inline void kparams_finish(KParams& k) {
   k.f[13] = (float)(-k.tau_rho);
   k.f[14] = (float)(-k.tau_T);
   k.f[15] = 0.0f;
+  k.fdt[0] = (float)(k.cfl * k.h);
+  k.fdt[1] = (float)(1.0 / k.h);
+  k.fdt[2] = (float)(0.5 / k.h);
+  k.fdt[3] = k.frozen ? 0.0f : (float)(k.c_tau * k.tau0);
 }
 
 // Device control block: time, step size and the reductions of one solver.
@@ -185,20 +192,22 @@ __device__ __forceinline__ StepCtl block_step_ctl(const Ctl* ctl) {
 }
 
 // The dt-derived factors of the next step in the kernel's arithmetic type.
+// Float solvers form them in float from the float dt (a product by the
+// stored 1/h and 1/(2h): no FP64 divide on the step's serial path).
 template <typename R> struct StepDt;
 template <> struct StepDt<double> {
   double dt, dtdx, dt_2h, dt_2;
   __device__ __forceinline__ explicit StepDt(const StepCtl& c)
       : dt(c.dt), dtdx(c.dtdx), dt_2h(c.dt_2h), dt_2(c.dt_2) {}
-  __device__ __forceinline__ StepDt(double d, double h)
-      : dt(d), dtdx(d / h), dt_2h(d / (2.0 * h)), dt_2(0.5 * d) {}
+  __device__ __forceinline__ StepDt(double d, const KParams& kp)
+      : dt(d), dtdx(d / kp.h), dt_2h(d / (2.0 * kp.h)), dt_2(0.5 * d) {}
 };
 template <> struct StepDt<float> {
   float dt, dtdx, dt_2h, dt_2;
   __device__ __forceinline__ explicit StepDt(const StepCtl& c)
       : dt(c.fdt), dtdx(c.fdtdx), dt_2h(c.fdt_2h), dt_2(c.fdt_2) {}
-  __device__ __forceinline__ StepDt(double d, double h)
-      : dt((float)d), dtdx((float)(d / h)), dt_2h((float)(d / (2.0 * h))), dt_2((float)(0.5 * d)) {}
+  __device__ __forceinline__ StepDt(double d, const KParams& kp)
+      : dt((float)d), dtdx(dt * kp.fdt[1]), dt_2h(dt * kp.fdt[2]), dt_2(0.5f * dt) {}
 };
 
 // ---------------------------------------------------------------- eq. 5

@@ -23,15 +23,11 @@ template <> struct TauKey<float> {
   static __device__ __forceinline__ float of(const P<float>& k, float rho, float T) {
     return -fmaf(k.tau_rho, Ar<float>::lg2(rho), k.tau_T * Ar<float>::lg2(T));
   }
-  static __device__ __forceinline__ double tau_min(const KParams& kp, double a) {
-    return kp.tau0 * exp2(-a);
-  }
 };
 template <> struct TauKey<double> {
   static __device__ __forceinline__ double of(const P<double>& k, double rho, double T) {
     return -(k.tau0 * pow(rho, k.tau_rho) * pow(T, k.tau_T));
   }
-  static __device__ __forceinline__ double tau_min(const KParams&, double a) { return -a; }
 };
 
 // |v| from v.v for the eq. 16 bound of 2D / 3D states.  In float,
@@ -62,30 +58,50 @@ __device__ __forceinline__ void cfl_cell(const P<R>& k, R rho, R kin2, R vmag, R
 }
 
 // eq. 16 times cfl from the maximal signal speed, capped by c_tau * min tau;
-// raises FLAG_DT if the result is not a positive finite number.
-template <typename R>
+// raises FLAG_DT if the result is not a positive finite number.  One thread
+// per step evaluates it on the step's serial path, in the solver's own type:
+// float solvers stay off the narrow FP64 pipe, whose divide and exp2 take
+// microseconds of latency on one thread.
 __device__ __forceinline__ double dt_from_maxima(const KParams& kp, double smax, double akey,
                                                  uint32_t& flags) {
   double dt = kp.cfl * kp.h / smax;
   if (!kp.frozen) {
-    const double taumin = TauKey<R>::tau_min(kp, akey);
-    if (kp.c_tau * taumin < dt) dt = kp.c_tau * taumin;
+    const double cap = kp.c_tau * -akey;          // akey = -min tau
+    if (cap < dt) dt = cap;
   }
   if (!(dt > 0.0) || !isfinite(dt)) flags |= FLAG_DT;
   return dt;
 }
+__device__ __forceinline__ double dt_from_maxima(const KParams& kp, float smax, float akey,
+                                                 uint32_t& flags) {
+  float dt = __fdiv_rn(kp.fdt[0], smax);
+  if (!kp.frozen) {
+    const float cap = kp.fdt[3] * Ar<float>::ex2(-akey);   // c_tau tau0 2^-a = c_tau min tau
+    if (cap < dt) dt = cap;
+  }
+  if (!(dt > 0.0f) || !isfinite(dt)) flags |= FLAG_DT;
+  return (double)dt;
+}
 
-// Store the next step's dt and its derived factors (double and float).
-__device__ __forceinline__ void set_step_dt(Ctl* ctl, double dt, double h) {
-  const double dtdx = dt / h, dt_2h = dt / (2.0 * h), dt_2 = 0.5 * dt;
+// Store the next step's dt and its derived factors (StepDt of the solver's
+// type; the other type's copies are conversions of those).
+template <typename R>
+__device__ __forceinline__ void set_step_dt(Ctl* ctl, double dt, const KParams& kp) {
+  const StepDt<R> s(dt, kp);
   ctl->dt = dt;
-  ctl->dtdx = dtdx;
-  ctl->dt_2h = dt_2h;
-  ctl->dt_2 = dt_2;
-  ctl->fdt = (float)dt;
-  ctl->fdtdx = (float)dtdx;
-  ctl->fdt_2h = (float)dt_2h;
-  ctl->fdt_2 = (float)dt_2;
+  ctl->dtdx = (double)s.dtdx;
+  ctl->dt_2h = (double)s.dt_2h;
+  ctl->dt_2 = (double)s.dt_2;
+  ctl->fdt = (float)s.dt;
+  ctl->fdtdx = (float)s.dtdx;
+  ctl->fdt_2h = (float)s.dt_2h;
+  ctl->fdt_2 = (float)s.dt_2;
+}
+
+// A zero step (no step pending).
+__device__ __forceinline__ void clear_step_dt(Ctl* ctl) {
+  ctl->dt = ctl->dtdx = ctl->dt_2h = ctl->dt_2 = 0.0;
+  ctl->fdt = ctl->fdtdx = ctl->fdt_2h = ctl->fdt_2 = 0.0f;
 }
 
 // Read a control field written by other blocks in this launch or by the
@@ -105,7 +121,7 @@ __device__ void finalize(Ctl* ctl, const KParams& kp, bool advance, bool flip = 
   const double akey = key_to_double(atomicExch((unsigned long long*)&ctl->tau_key,
                                                (unsigned long long)key_of(-INFINITY)));
   uint32_t flags = atomicOr(&ctl->flags, 0u);
-  const double dt = dt_from_maxima<R>(kp, smax, akey, flags);
+  const double dt = dt_from_maxima(kp, (R)smax, (R)akey, flags);
   double t = vload(&ctl->t);
   const double t_end = vload(&ctl->t_end);
   if (advance) {
@@ -125,7 +141,7 @@ __device__ void finalize(Ctl* ctl, const KParams& kp, bool advance, bool flip = 
   }
   ctl->t = t;
   ctl->dt_cfl = dt;
-  set_step_dt(ctl, dtn, kp.h);
+  set_step_dt<R>(ctl, dtn, kp);
   ctl->last = last;
   ctl->flags = flags;
   __threadfence();

@@ -10,7 +10,7 @@ constexpr int NTU = 256;
 
 __global__ void ctl_reset_kernel(Ctl* ctl, double t) {
   ctl->t = t;
-  set_step_dt(ctl, 0.0, 1.0);
+  clear_step_dt(ctl);
   ctl->dt_cfl = 0.0;
   ctl->t_end = INFINITY;
   ctl->nsteps = 0;
@@ -29,7 +29,8 @@ cudaError_t ctl_reset_launch(Ctl* ctl, double t, cudaStream_t st) {
 
 // Sets the target time and re-clamps the pending dt (same rule as the
 // step finalize: the step that would reach or pass t_end lands on it).
-__global__ void set_target_kernel(Ctl* ctl, double t_end, double h) {
+template <typename R>
+__global__ void set_target_kernel(Ctl* ctl, double t_end, const KParams kp) {
   const double t = ctl->t, dt = ctl->dt_cfl;
   ctl->t_end = t_end;
   uint32_t last = 0;
@@ -40,12 +41,16 @@ __global__ void set_target_kernel(Ctl* ctl, double t_end, double h) {
     dtn = t_end - t;
     last = 1;
   }
-  set_step_dt(ctl, dtn, h);
+  set_step_dt<R>(ctl, dtn, kp);
   ctl->last = last;
 }
 
-cudaError_t set_target_launch(Ctl* ctl, double t_end, double h, cudaStream_t st) {
-  set_target_kernel<<<1, 1, 0, st>>>(ctl, t_end, h);
+cudaError_t set_target_launch(int precision, Ctl* ctl, double t_end, const KParams& kp,
+                              cudaStream_t st) {
+  if (precision == PREC_FP64)
+    set_target_kernel<double><<<1, 1, 0, st>>>(ctl, t_end, kp);
+  else
+    set_target_kernel<float><<<1, 1, 0, st>>>(ctl, t_end, kp);
   return cudaGetLastError();
 }
 
