@@ -10,7 +10,7 @@ fused kernel).  The state (64 MiB per buffer) fits in L2, so L2 is flushed by a
 events on the solver's stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision fp32|fp64|fp32_p64] [--n CELLS]
+                  [--precision fp32|fp64|fp32_p64|fp32_pc] [--n CELLS]
 
 Under torchrun (N > 1) every rank runs an independent replica (the 1D problem
 is not sharded: "replicas only"); value = all ranks' cell-updates / max time.
@@ -35,11 +35,16 @@ METRIC = "cell-updates/s"
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM bytes (read + write) of one launch of the 1D FP32 step kernel at N = 2^22
-# (the block-tile kernel tile1d_kernel), from one ncu capture of the current
-# kernel (67.2 MB read + 18.9 MB written during the launch; the remaining writes
-# are still dirty in L2 when it ends).  Only valid for that workload and
-# precision; other lines report null.
-TRAFFIC_1D_FP32_N22 = 86.1e6
+# (the 512-cell block-tile configuration of tile1d_kernel), from one ncu capture
+# of the current kernel (67.2 MB read + 19.1 MB written during the launch; the
+# remaining writes are still dirty in L2 when it ends).  Only valid for that
+# workload, precision and launch configuration; other lines report null.
+TRAFFIC_1D_FP32_N22 = 86.2e6
+
+# --precision names -> sv_params.precision (SV_FP32, SV_FP64, SV_FP32_P64,
+# SV_FP32_PC of include/sv.h) and the arithmetic type reported as "dtype"
+PRECISIONS = {"fp32": 0, "fp64": 1, "fp32_p64": 2, "fp32_pc": 3}
+DTYPES = {"fp32": "f32", "fp64": "f64", "fp32_p64": "f32", "fp32_pc": "f32"}
 
 
 def workload(n_cells: int, gamma: float, Ck: float, S: float):
@@ -52,15 +57,18 @@ def workload(n_cells: int, gamma: float, Ck: float, S: float):
     return U0, h, L
 
 
-# Workloads: name -> (grid, params, description).  The 1D line is the default.
+# Workloads: name -> (grid, params, description, steps of the per-field error run
+# against FP64).  The 1D line is the default.
 WORKLOADS = {
-    "1d": dict(dims=lambda a: (a.n,), params=dict(tau0=0.08, S=1.0, cfl=0.4),
+    "1d": dict(dims=lambda a: (a.n,), params=dict(tau0=0.08, S=1.0, cfl=0.4), err_steps=200,
                desc="1D periodic MUSCL-Hancock step, N={cells} cells, h=1/1024, 64 random-phase "
                     "acoustic modes (k^-1, 1e-3), S=1, tau0=0.08, CFL 0.4"),
     "2d": dict(dims=lambda a: (a.side or 8192,) * 2, params=dict(tau0=0.01, S=1.0, cfl=0.4),
+               err_steps=50,
                desc="2D periodic unsplit MUSCL-Hancock step, {side}x{side}, plane wave (7,4) at 29.7 deg "
                     "amplitude 1e-3 + white noise 1e-5, S=1, tau0=0.01, CFL 0.4"),
     "3d": dict(dims=lambda a: (a.side or 512,) * 3, params=dict(tau0=0.08, S=1.0, cfl=0.3),
+               err_steps=20,
                desc="3D periodic unsplit MUSCL-Hancock step, {side}^3, isotropic k^-2 random density/"
                     "velocity perturbations amplitude 1e-3, S=1, tau0=0.08, CFL 0.3"),
 }
@@ -237,7 +245,7 @@ def run_ours(args):
         build()
     if dist is not None:
         dist.barrier()
-    prec = {"fp32": sv.FP32, "fp64": sv.FP64, "fp32_p64": sv.FP32_P64}[args.precision]
+    prec = PRECISIONS[args.precision]
     esize = 8 if prec == sv.FP64 else 4
     W = WORKLOADS[args.workload]
     P = sv.Params(precision=prec, **W["params"])
@@ -298,6 +306,9 @@ def run_ours(args):
 
     if rank != 0:
         return
+    err = None
+    if prec != sv.FP64 and args.err_steps >= 0:
+        err = precision_error(sv, P, dims, L, U0, args.err_steps or W["err_steps"])
     pk = peaks()
     step_s = tot / args.steps
     alg_bytes = 2 * nf * esize * ncell             # read + write every conserved field once
@@ -307,7 +318,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "fp64": "f64", "fp32_p64": "f32"}[args.precision],
+        "dtype": DTYPES[args.precision],
         "data": "synthetic",
         "config": {"workload": W["desc"].format(cells=ncell, side=dims[0]), "cells": ncell,
                    "precision": args.precision,
@@ -318,7 +329,9 @@ def run_ours(args):
                      "peak_src": f"{pk['src']} hbm_gbs (burst copy)", "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"],
                      "traffic": (TRAFFIC_1D_FP32_N22 if (args.workload == "1d" and ncell == 1 << 22
-                                                         and args.precision == "fp32") else None),
+                                                         and args.precision == "fp32"
+                                                         and "512-cell" in tuned["config"])
+                                 else None),
                      "alg_bytes_per_launch": alg_bytes},
         "e2e": {"value": ws * ncell * e2e_steps / e2e_t, "unit": METRIC,
                 "h2d_bytes_per_step": int(host_in.numel() * 8),
@@ -327,9 +340,49 @@ def run_ours(args):
         "clocks": getattr(clk, "result", None),
         "status_flags": status, "sim_time": t_sim,
     }
+    if err is not None:
+        line["error_vs_fp64"] = err
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, args, budget_s=args.cpu_budget)
     print(json.dumps(line), flush=True)
+
+
+def precision_error(sv, P, dims, L, U0, steps: int) -> dict:
+    """Per-field error of a float policy against the FP64 kernels (which match
+    the FP64 oracle to 1e-12) on the benchmark's own workload: the float run
+    takes `steps` steps of its own dt, the FP64 run is advanced to the same
+    time (its last step clamped onto it), and rho, v, p, E_nu are compared cell
+    by cell.  Absolute errors: L1 = mean over cells, Linf = maximum (v: every
+    component)."""
+    import dataclasses
+    with sv.Solver(P, dims, L) as s:
+        s.write_state(U0)
+        s.step(steps)
+        Uf, t = s.read_state()
+        st = s.status()
+    P64 = dataclasses.replace(P, precision=sv.FP64)
+    with sv.Solver(P64, dims, L) as s:
+        s.write_state(U0)
+        rc, k = s.run_to(t, check=False)
+        Ud, _ = s.read_state()
+    dim = len(dims)
+
+    def fields(U):
+        U = U.reshape(dim + 3, -1)
+        rho = U[0]
+        v = np.stack([U[1 + a] / rho for a in range(dim)])
+        kin = sum(U[1 + a] * v[a] for a in range(dim))
+        return {"rho": rho, "v": v, "p": (P.gamma - 1.0) * (U[1 + dim] - 0.5 * kin - U[2 + dim]),
+                "E_nu": U[2 + dim]}
+
+    ff, fd = fields(Uf), fields(Ud)
+    del Uf, Ud
+    out = {}
+    for name in ff:
+        d = np.abs(ff[name] - fd[name])
+        out[name] = {"l1": float(np.mean(d)), "linf": float(np.max(d))}
+    return {"reference": "FP64 kernels", "steps": steps, "fp64_steps": int(k), "t": t,
+            "status": [int(st), int(rc)], "norm": "absolute, L1 = mean over cells", "fields": out}
 
 
 def sweep_inputs(nruns: int, seed: int = 2026):
@@ -446,7 +499,7 @@ def run_wc(args):
     from paper_1805_03442_gb300.build import build
     build()
     N = args.n if args.n != 1 << 22 else 100000
-    prec = {"fp32": sv.FP32, "fp64": sv.FP64, "fp32_p64": sv.FP32_P64}[args.precision]
+    prec = PRECISIONS[args.precision]
     P = sv.Params(precision=prec, tau0=math.inf, S=0.0)
     x = inputs.cell_centres(N, 1.0)
     p = np.where(x < 0.1, 1000.0, np.where(x <= 0.9, 0.01, 100.0))
@@ -470,7 +523,7 @@ def run_wc(args):
     line = {"metric": "cell-updates/s", "value": N * steps / wall, "unit": "cell-updates/s",
             "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": 1e3 * wall / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "fp64": "f64", "fp32_p64": "f32"}[args.precision],
+            "dtype": DTYPES[args.precision],
             "data": "synthetic",
             "config": {"workload": f"colliding shock waves, N={N} cells, solid walls, t_end 0.038",
                        "cells": N, "l2": "not flushed: whole run timed (3.2 MB state)"},
@@ -491,7 +544,7 @@ def run_sector(args):
     from paper_1805_03442_gb300.build import build
     build()
     nx = args.side or 2048
-    prec = {"fp32": sv.FP32, "fp64": sv.FP64, "fp32_p64": sv.FP32_P64}[args.precision]
+    prec = PRECISIONS[args.precision]
     pb = inputs.sector_problem(nx)
     P = sv.Params(precision=prec, S=1.0, tau0=0.0135)
     U0 = inputs.sector_rest_state(P.gamma, P.Ck, P.S, pb.nx, pb.ny)
@@ -531,7 +584,7 @@ def run_sector(args):
     line = {"metric": "cell-updates/s", "value": cells * steps / wall, "unit": "cell-updates/s",
             "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": 1e3 * wall / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "fp64": "f64", "fp32_p64": "f32"}[args.precision],
+            "dtype": DTYPES[args.precision],
             "data": "synthetic",
             "config": {"workload": f"2D active sector, {pb.nx}x{pb.ny} cells, walls/outflow, "
                                    f"pulsating source lambda 0.1, S=1, tau0=0.0135, t_end {t_end}",
@@ -556,7 +609,7 @@ def run_driven(args):
     from paper_1805_03442_gb300.build import build
     build()
     N = args.n if args.n != 1 << 22 else 1 << 16
-    prec = {"fp32": sv.FP32, "fp64": sv.FP64, "fp32_p64": sv.FP32_P64}[args.precision]
+    prec = PRECISIONS[args.precision]
     P = sv.Params(precision=prec, S=0.5, tau0=0.0135)
     rho0, p0, ev0 = inputs.equilibrium_primitive(P.Ck, P.S)
     base = inputs.prim_to_cons(P.gamma, np.array([rho0]), [np.array([0.0])], np.array([p0]),
@@ -582,7 +635,7 @@ def run_driven(args):
     line = {"metric": "cell-updates/s", "value": N * steps / wall, "unit": "cell-updates/s",
             "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": 1e3 * wall / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "fp64": "f64", "fp32_p64": "f32"}[args.precision],
+            "dtype": DTYPES[args.precision],
             "data": "synthetic",
             "config": {"workload": f"forced-source wave, N={N} cells, driven x=0, outflow x=1, "
                                    "S=0.5, tau0=0.0135, t_end 1", "cells": N,
@@ -598,7 +651,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_p64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_p64", "fp32_pc"])
     ap.add_argument("--n", type=int, default=1 << 22, help="cells of the 1d workload")
     ap.add_argument("--workload", default="1d",
                     choices=sorted(WORKLOADS) + ["sweep", "wc", "driven", "sector"])
@@ -608,6 +661,9 @@ def main():
     ap.add_argument("--subset", type=int, default=64, help="looped comparison subset of the sweep")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--err-steps", type=int, default=0,
+                    help="steps of the per-field error run against FP64 (0: workload default, "
+                         "-1: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

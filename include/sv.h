@@ -70,6 +70,10 @@ extern "C" {
 #define SV_FP32     0   /* float state and arithmetic */
 #define SV_FP64     1   /* double state and arithmetic */
 #define SV_FP32_P64 2   /* float state, pressure recovery of eq. 5 in double */
+#define SV_FP32_PC  3   /* float state, pressure recovery of eq. 5 in compensated float:
+                           the exact E - rho v^2/2 - E_nu of the float operands (two
+                           error-free float sums), times gamma - 1, rounded once; the
+                           same p as SV_FP32_P64 to within its last bit, at float speed */
 
 /* ---- time integration */
 #define SV_HANCOCK  0   /* MUSCL-Hancock: half-step predictor + corrector (eqs. 14-15) */
@@ -88,7 +92,7 @@ typedef struct {
   double cfl;                   /* factor on the eq. 16 bound, e.g. 0.4 */
   double c_tau;                 /* dt <= c_tau * min tau (explicit source), e.g. 0.5 */
   int limiter;                  /* SV_MINMOD, SV_VANLEER, SV_MC */
-  int precision;                /* SV_FP32, SV_FP64, SV_FP32_P64 */
+  int precision;                /* SV_FP32, SV_FP64, SV_FP32_P64, SV_FP32_PC */
   int method;                   /* SV_HANCOCK (0) or SV_HEUN */
 } sv_params;
 
@@ -313,7 +317,7 @@ int sv_batch_get_config(sv_batch* b, int* index, char* desc, size_t cap);
 
 /* One MUSCL-Hancock step of a 1D periodic grid of n cells (length L) from the
    caller's device buffer U_in to the caller's device buffer U_out (each
-   4 * n elements of float for SV_FP32 / SV_FP32_P64 or double for SV_FP64,
+   4 * n elements of float for SV_FP32 / SV_FP32_P64 / SV_FP32_PC or double for SV_FP64,
    field-major rho, rho v, E, E_nu; they must not overlap), with dt from
    eq. 16 (capped by c_tau * min tau) on U_in.  Same kernels and results as
    sv_step on a solver holding U_in.  Allocates nothing and calls no

@@ -80,7 +80,7 @@ int check_inputs(const sv_params* p, const sv_grid* g) {
   if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->c_tau > 0.0) || !(p->tau0 > 0.0))
     return SV_EINVAL;
   if (p->limiter < SV_MINMOD || p->limiter > SV_MC) return SV_EINVAL;
-  if (p->precision < SV_FP32 || p->precision > SV_FP32_P64) return SV_EINVAL;
+  if (p->precision < SV_FP32 || p->precision > SV_FP32_PC) return SV_EINVAL;
   for (int side = 0; side < 2; ++side)
     if (g->bc[side] < SV_BC_PERIODIC || g->bc[side] > SV_BC_DRIVEN) return SV_EINVAL;
   if (g->bc[1] == SV_BC_DRIVEN) return SV_EINVAL;
@@ -98,7 +98,7 @@ int check_inputs(const sv_params* p, const sv_grid* g) {
   if (p->method != SV_HANCOCK && p->method != SV_HEUN) return SV_EINVAL;
   if (p->method == SV_HEUN &&
       (g->dim != 1 || g->bc[0] != SV_BC_PERIODIC || g->bc[1] != SV_BC_PERIODIC ||
-       p->precision == SV_FP32_P64))
+       p->precision == SV_FP32_P64 || p->precision == SV_FP32_PC))
     return SV_EINVAL;
   if (g->dim == 1 && (g->bc[0] != SV_BC_PERIODIC || g->bc[1] != SV_BC_PERIODIC) && g->n[0] < 2)
     return SV_EINVAL;

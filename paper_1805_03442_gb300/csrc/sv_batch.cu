@@ -70,7 +70,7 @@ int check_batch(const sv_params* p, const sv_run* r, int64_t nruns, int log_cap)
   if (!p || !r || nruns < 1 || nruns > (1 << 30) || log_cap < 0) return SV_EINVAL;
   if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->c_tau > 0.0)) return SV_EINVAL;
   if (p->limiter < SV_MINMOD || p->limiter > SV_MC) return SV_EINVAL;
-  if (p->precision < SV_FP32 || p->precision > SV_FP32_P64) return SV_EINVAL;
+  if (p->precision < SV_FP32 || p->precision > SV_FP32_PC) return SV_EINVAL;
   if (p->method != SV_HANCOCK) return SV_EINVAL;
   for (int64_t i = 0; i < nruns; ++i) {
     if (r[i].n < 1 || r[i].n > (1 << 24) || !(r[i].L > 0.0) || !(r[i].tau0 > 0.0) ||

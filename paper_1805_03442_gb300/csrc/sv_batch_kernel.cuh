@@ -232,6 +232,7 @@ void* bpick_prec(int precision) {
   switch (precision) {
     case PREC_FP64: return (void*)KB<NTB, double, 0, LIM>::fn;
     case PREC_FP32_P64: return (void*)KB<NTB, float, 1, LIM>::fn;
+    case PREC_FP32_PC: return (void*)KB<NTB, float, 2, LIM>::fn;
     default: return (void*)KB<NTB, float, 0, LIM>::fn;
   }
 }

@@ -10,7 +10,7 @@ namespace sv {
 struct KParams;
 struct Ctl;
 
-enum { PREC_FP32 = 0, PREC_FP64 = 1, PREC_FP32_P64 = 2 };
+enum { PREC_FP32 = 0, PREC_FP64 = 1, PREC_FP32_P64 = 2, PREC_FP32_PC = 3 };
 
 // 1D fused step (sv_step1d.cu)
 int step1d_grid(const KParams& kp, int precision);

@@ -47,7 +47,8 @@ struct KParams {
   const int* pul_hi;
   double pul_omega, pul_amp, pul_ev;   // pul_ev = C_k + S
   // float copies for the float kernels (kparams_finish): the twelve values
-  // above, then log2(1/tau0) (0 in the frozen limit), -tau_rho, -tau_T
+  // above, then log2(1/tau0) (0 in the frozen limit), -tau_rho, -tau_T, and
+  // the low part of g1 (g1 - (float)g1, for the compensated pressure)
   float f[16];
   // float constants of the dt rule of the float solvers: cfl h, 1/h, 1/(2h),
   // c_tau tau0 (0 in the frozen limit)
@@ -62,7 +63,7 @@ inline void kparams_finish(KParams& k) {
   k.f[12] = k.inv_tau0 > 0.0 ? (float)log2(k.inv_tau0) : 0.0f;
   k.f[13] = (float)(-k.tau_rho);
   k.f[14] = (float)(-k.tau_T);
-  k.f[15] = 0.0f;
+  k.f[15] = (float)(k.g1 - (double)k.f[1]);
   k.fdt[0] = (float)(k.cfl * k.h);
   k.fdt[1] = (float)(1.0 / k.h);
   k.fdt[2] = (float)(0.5 / k.h);
@@ -150,11 +151,12 @@ template <> struct P<float> {
   float gamma, g1, Ck, Q0, inv_tau0, tau0;
   float tau_rho, tau_T, Q_rho, Q_T, I_rho, I_T;
   float l2_inv_tau0, ntau_rho, ntau_T;   // log2(1/tau0), -tau_rho, -tau_T
+  float g1lo;                            // g1 - (float)g1
   int limiter, frozen, qi_zero, bc_lo, bc_hi;
   __device__ __forceinline__ explicit P(const KParams& k)
       : gamma(k.f[0]), g1(k.f[1]), Ck(k.f[2]), Q0(k.f[3]), inv_tau0(k.f[5]), tau0(k.f[4]),
         tau_rho(k.f[6]), tau_T(k.f[7]), Q_rho(k.f[8]), Q_T(k.f[9]), I_rho(k.f[10]),
-        I_T(k.f[11]), l2_inv_tau0(k.f[12]), ntau_rho(k.f[13]), ntau_T(k.f[14]),
+        I_T(k.f[11]), l2_inv_tau0(k.f[12]), ntau_rho(k.f[13]), ntau_T(k.f[14]), g1lo(k.f[15]),
         limiter(k.limiter), frozen(k.frozen), qi_zero(k.qi_zero), bc_lo(k.bc_lo),
         bc_hi(k.bc_hi) {}
 };
@@ -213,14 +215,30 @@ template <> struct StepDt<float> {
 // ---------------------------------------------------------------- eq. 5
 
 // Pressure policies of the float kernels: PP = 0 all-float, PP = 1 the
-// subtraction of eq. 5 carried out in double.
+// subtraction of eq. 5 carried out in double, PP = 2 the same subtraction in
+// compensated float: E - kin2/2 - E_nu of the float operands is formed exactly
+// as an unevaluated sum t + e by two of Dekker's fast two-sums (exact when
+// |E| >= E_nu and E - E_nu >= kin2/2, i.e. for every state with p >= 0), then
+// multiplied by g1 held as two floats (g1 + g1lo) with one final rounding.  The
+// result is the double policy's p to within its last bit, at the cost of eleven
+// float operations (three for PP = 0) instead of a trip through GB300's narrow
+// FP64 pipe.
 template <typename R, int PP>
 __device__ __forceinline__ R pressure(const P<R>& k, R kin2, R E, R Ev) {
   // kin2 = rho |v|^2 (twice the kinetic energy density)
-  if (PP == 1) {
+  if constexpr (PP == 1) {
     return (R)((double)k.g1 * ((double)E - 0.5 * (double)kin2 - (double)Ev));
+  } else if constexpr (PP == 2) {
+    static_assert(std::is_same<R, float>::value, "compensated pressure is a float policy");
+    const float h = 0.5f * kin2;
+    const float s = __fsub_rn(E, Ev);
+    const float e1 = __fsub_rn(__fsub_rn(E, s), Ev);
+    const float t = __fsub_rn(s, h);
+    const float e2 = __fsub_rn(__fsub_rn(s, t), h);
+    return __fmaf_rn(k.g1, t, __fmaf_rn(k.g1lo, t, __fmul_rn(k.g1, __fadd_rn(e1, e2))));
+  } else {
+    return k.g1 * (E - (R)0.5 * kin2 - Ev);
   }
-  return k.g1 * (E - (R)0.5 * kin2 - Ev);
 }
 
 // ---------------------------------------------------------------- limiter

@@ -58,7 +58,7 @@ extern "C" int sv_step1d_noalloc(const sv_params* p, int64_t n, double L, const 
   if (n < 1 || !(L > 0.0)) return SV_EINVAL;
   if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->c_tau > 0.0) || !(p->tau0 > 0.0) ||
       p->limiter < SV_MINMOD || p->limiter > SV_MC || p->precision < SV_FP32 ||
-      p->precision > SV_FP32_P64 || p->method != SV_HANCOCK)
+      p->precision > SV_FP32_PC || p->method != SV_HANCOCK)
     return SV_EINVAL;
   void* scratch = nullptr;
   int rc = scratch_address(&scratch);

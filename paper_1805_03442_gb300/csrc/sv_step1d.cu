@@ -43,7 +43,8 @@ step1d_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
   reduce_and_finalize<R, NT1>(ctl, kp, smax, akey, flags, true);
 }
 
-// Kernel variants: arithmetic (float / double / float with double pressure),
+// Kernel variants: arithmetic (float / double / float with double or
+// compensated-float pressure),
 // limiter and source kind are compile-time; one of them is chosen per solver.
 template <typename R, int PP, int LIM, int SRC>
 struct K1 {
@@ -56,6 +57,7 @@ static void* pick_prec(int precision) {
   switch (precision) {
     case PREC_FP64: return (void*)K1<double, 0, LIM, SRC>::fn;
     case PREC_FP32_P64: return (void*)K1<float, 1, LIM, SRC>::fn;
+    case PREC_FP32_PC: return (void*)K1<float, 2, LIM, SRC>::fn;
     default: return (void*)K1<float, 0, LIM, SRC>::fn;
   }
 }

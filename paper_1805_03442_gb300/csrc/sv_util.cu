@@ -101,6 +101,10 @@ cudaError_t dt_reduce_launch(int precision, int dim, const KParams& kp, const vo
       dt_reduce_kernel<float, 1><<<g, NTU, 0, st>>>(kp, (const float*)a, (const float*)b, ctl,
                                                     dim, ncell);
       break;
+    case PREC_FP32_PC:
+      dt_reduce_kernel<float, 2><<<g, NTU, 0, st>>>(kp, (const float*)a, (const float*)b, ctl,
+                                                    dim, ncell);
+      break;
     default:
       dt_reduce_kernel<float, 0><<<g, NTU, 0, st>>>(kp, (const float*)a, (const float*)b, ctl,
                                                     dim, ncell);

@@ -80,7 +80,7 @@ def test_fp64_other_limiters(sv, limiter):
     assert rel_linf(U, ref) <= 1e-12
 
 
-@pytest.mark.parametrize("precision", ["FP32", "FP32_P64"])
+@pytest.mark.parametrize("precision", ["FP32", "FP32_P64", "FP32_PC"])
 @pytest.mark.parametrize("N", [5, 33, 1000, 4099])
 def test_fp32_one_step(sv, precision, N):
     P = sv.Params(precision=getattr(sv, precision), tau0=0.3)

@@ -72,7 +72,7 @@ def test_fp64_other_limiters(sv, n, limiter):
     assert rel_linf(U, _oracle_steps(Po, U0, n, h, dts)) <= 1e-12
 
 
-@pytest.mark.parametrize("precision", ["FP32", "FP32_P64"])
+@pytest.mark.parametrize("precision", ["FP32", "FP32_P64", "FP32_PC"])
 @pytest.mark.parametrize("n", [(37, 29), (513, 260), (33, 17, 9), (65, 40, 20)])
 def test_fp32_one_step(sv, precision, n):
     P = sv.Params(precision=getattr(sv, precision), tau0=0.3)

@@ -1,0 +1,116 @@
+"""Pressure recovery policies of the float kernels (eq. 5), through the C ABI.
+
+p = (gamma - 1)(E - rho v^2/2 - E_nu) cancels when E_nu dominates E.  The
+float state is the same for the three float policies; they differ in how the
+subtraction is carried out: SV_FP32 in float (three roundings), SV_FP32_P64 in
+double, SV_FP32_PC in compensated float (exact difference, one rounding).
+
+The eq. 16 time step of a state at rest exposes p directly: dt = cfl h /
+(|v| + sqrt(gamma p / rho)), with no stored intermediate state in between.  The
+state below (E_nu = 1000, p = 1) is the one of a scan over rho v in which the
+float subtraction loses the most: E - rho v^2/2 rounds at the ulp of 1002.5,
+2^-14, so float p comes out as 1.0 against 0.99998779296875 exactly (1.2e-5),
+while a correctly rounded p is exact to 6e-8."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_util import need_gpu, oracle_params
+from oracle import orc as O
+
+pytestmark = pytest.mark.gpu
+
+FLOAT_POLICIES = ["FP32", "FP32_P64", "FP32_PC"]
+
+
+@pytest.fixture(scope="module")
+def sv():
+    return need_gpu()
+
+
+def _cancelling_state(N):
+    """rho = 1, rho v = 5/128, E_nu = 1000, E the float nearest p = 1 + kinetic + E_nu."""
+    m = np.float32(5.0 / 128.0)
+    E = np.float32(2.5 + 0.5 * float(m) ** 2 + 1000.0)
+    U = np.empty((4, N))
+    U[0], U[1], U[2], U[3] = 1.0, float(m), float(E), 1000.0
+    return U
+
+
+def _dt_of(sv, prec, U, N, h):
+    P = sv.Params(precision=getattr(sv, prec), tau0=math.inf, S=0.0)
+    with sv.Solver(P, (N,), (N * h,)) as s:
+        s.write_state(U)
+        assert s.status() == 0
+        return s.dt(), P
+
+
+def test_dt_exposes_pressure_policy(sv):
+    N, h = 64, 1.0 / 64
+    U = _cancelling_state(N)
+    dts = {}
+    for prec in FLOAT_POLICIES:
+        dts[prec], P = _dt_of(sv, prec, U, N, h)
+    ref = O.dt_cfl(oracle_params(P), U, N, h)
+    # the exact pressure of the float state, and the float-arithmetic one
+    p_exact = 0.4 * (U[2, 0] - 0.5 * U[1, 0] ** 2 - U[3, 0])
+    assert p_exact == pytest.approx(0.99998779296875, rel=1e-15)
+    rel = {k: abs(v - ref) / ref for k, v in dts.items()}
+    # double and compensated float: only the approximate sqrt / reciprocal remain
+    assert rel["FP32_P64"] <= 1.5e-6
+    assert rel["FP32_PC"] <= 1.5e-6
+    # same pressure bits -> same dt bits
+    assert dts["FP32_PC"] == dts["FP32_P64"]
+    # float subtraction: p = 1.0, c too large by 6.1e-6, dt too small by ~5.9e-6
+    assert 4e-6 <= rel["FP32"] <= 8e-6
+    assert dts["FP32"] < ref
+
+
+def _frozen_states(N, seed, ev_per_mass):
+    rng = np.random.default_rng(seed)
+    x = (np.arange(N) + 0.5) / N
+    rho = 1.0 + 0.05 * np.sin(2 * np.pi * x + rng.uniform(0, 2 * np.pi))
+    v = 0.05 * np.sin(4 * np.pi * x + rng.uniform(0, 2 * np.pi))
+    p = 1.0 + 0.05 * np.sin(2 * np.pi * x + rng.uniform(0, 2 * np.pi))
+    Ev = ev_per_mass * rho
+    U = np.stack([rho, rho * v, p / 0.4 + 0.5 * rho * v * v + Ev, Ev])
+    return U.astype(np.float32).astype(np.float64)
+
+
+def _run(sv, prec, U0, N, h, nsteps):
+    P = sv.Params(precision=getattr(sv, prec), tau0=math.inf, S=0.0)
+    with sv.Solver(P, (N,), (N * h,)) as s:
+        s.write_state(U0)
+        dts = []
+        for _ in range(nsteps):
+            dts.append(s.dt())
+            s.step(1)
+        U, _ = s.read_state()
+        assert s.status() == 0
+    return U, dts, P
+
+
+def test_compensated_and_double_pressure_same_accuracy(sv):
+    """Ten steps of a state whose E_nu is 1000 times its pressure.  The
+    compensated policy rounds g1 (t + e) with g1 held to ~2^-48, the double one
+    with g1 in double; they differ only where the exact p lies that close to a
+    float midpoint (7e-5 of the evaluations for such states, whose E and E_nu
+    sit on a coarse 2^-14 grid).  Each such last-bit difference moves E by an
+    ulp of 1000, which the cancellation turns into 2e-5 of p, so the two runs
+    drift apart at the level of the float state itself; what they share is the
+    accuracy: the same error against the FP64 oracle, field by field."""
+    N, steps = 4099, 10
+    h = 1.0 / N
+    U0 = _frozen_states(N, seed=N, ev_per_mass=1000.0)
+    err = {}
+    for prec in ["FP32_P64", "FP32_PC"]:
+        U, dts, P = _run(sv, prec, U0, N, h, steps)
+        ref = U0.copy()
+        for dt in dts:
+            ref, rc = O.step(oracle_params(P), ref, N, h, dt)
+            assert rc == 0
+        err[prec] = np.sqrt(np.mean((U - ref) ** 2, axis=1))
+    for f in range(4):
+        a, b = err["FP32_P64"][f], err["FP32_PC"][f]
+        assert b <= 1.25 * a + 1e-12 and a <= 1.25 * b + 1e-12, (f, a, b)
