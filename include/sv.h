@@ -156,8 +156,8 @@ int sv_step(sv_solver* s, int64_t nsteps);
      Every barrier wait gives up after about 2 s with SV_FLAG_STALL, which
      sv_run_to reports as SV_ESTALL.
    SV_LAUNCH_AUTO (default): persistent for 1D MUSCL-Hancock grids of at most
-     one 64-cell chunk per SM (9728 cells on a GB300), where a step is short
-     enough for the gap between launches to matter; per-step launches
+     one 64-cell chunk per two SMs (4864 cells on a GB300), where a step is
+     short enough for the gap between launches to matter; per-step launches
      otherwise. */
 #define SV_LAUNCH_AUTO       0
 #define SV_LAUNCH_PER_STEP   1

@@ -165,10 +165,10 @@ int ensure_graph(sv_solver* s) {
 }
 
 // The persistent loop serves 1D MUSCL-Hancock solvers: always when asked for,
-// by default on grids of at most one 64-cell chunk per SM, where a step is
-// short enough for the gap between launches to matter (measured on a GB300:
-// 11-12 us instead of 14-15 us per float step up to 5000 cells, equal or
-// slightly slower from 2e4 cells on).
+// by default on grids of at most one 64-cell chunk per two SMs, where a step
+// is short enough for the gap between launches to matter (measured on a
+// GB300 with the float finalize: 7.8 instead of 10.1 us per float step at 200
+// cells, equal at 1600-5000 cells, 25-33% slower from 2e4 cells on).
 bool use_loop(const sv_solver* s) {
   if (s->loop_grid < 1) return false;
   return s->launch == SV_LAUNCH_PERSISTENT || (s->launch == SV_LAUNCH_AUTO && s->loop_fits);
@@ -362,7 +362,7 @@ int sv_init(const sv_params* p, const sv_grid* g, void* cuda_stream, void* devic
     s->loop_grid = loop1d_grid(s->kp, p->precision, s->ncell, &cap);
     if (cudaGetDevice(&dev) == cudaSuccess)
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    s->loop_fits = s->loop_grid > 0 && (s->ncell + 63) / 64 <= (int64_t)sms;
+    s->loop_fits = s->loop_grid > 0 && 2 * ((s->ncell + 63) / 64) <= (int64_t)sms;
   }
   if (rc == SV_OK) {
     // uniform equilibrium start: rho = p = 1, v = 0, E_nu = C_k + S

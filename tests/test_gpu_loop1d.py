@@ -144,6 +144,8 @@ def test_auto_mode(sv):
     P = sv.Params(precision=sv.FP32)
     with sv.Solver(P, (1000,), (1.0,)) as s:
         assert s.launch == sv.LAUNCH_PERSISTENT
+    with sv.Solver(P, (8000,), (1.0,)) as s:
+        assert s.launch == sv.LAUNCH_PER_STEP
     with sv.Solver(P, (20000,), (1.0,)) as s:
         assert s.launch == sv.LAUNCH_PER_STEP
     with sv.Solver(P, (1 << 22,), (1.0,)) as s:
