@@ -136,7 +136,8 @@ cudaError_t launch_step(sv_solver* s, cudaStream_t st) {
   }
   const SolverConfig& c = s->cfgs[(size_t)s->config];
   if (c.kind == CFG_TILE)
-    return tile1d_launch(s->kp, c.param, s->buf[0], s->buf[1], s->ctl, s->ncell, s->tile_grid, st);
+    return tile1d_launch(s->kp, s->p.precision, c.param, s->buf[0], s->buf[1], s->ctl, s->ncell,
+                         s->tile_grid, st);
   if (c.kind == CFG_SLIDE)
     return step1d_launch(s->p.precision, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell, s->grid, st);
   return stepnd_launch(s->dim, s->p.precision, s->kp, s->buf[0], s->buf[1], s->ctl, s->g.n,
@@ -187,7 +188,8 @@ const char* seg_desc(int seg) {
 void build_configs(sv_solver* s) {
   s->cfgs.clear();
   if (s->dim == 1) {
-    if (s->p.method == SV_HANCOCK && s->p.precision == SV_FP32 && s->ncell >= kTile1dMinCells) {
+    if (s->p.method == SV_HANCOCK && (s->p.precision == SV_FP32 || s->p.precision == SV_FP32_PC) &&
+        s->ncell >= kTile1dMinCells) {
       s->cfgs.push_back({CFG_TILE, 13,
                          "1D: 512-cell block tiles, 2 cells per thread, 80 registers, 3 blocks/SM"});
       s->cfgs.push_back({CFG_TILE, 12, "1D: 512-cell block tiles, 2 cells per thread, 2 blocks/SM"});
@@ -208,7 +210,7 @@ int apply_config(sv_solver* s, int idx) {
   const SolverConfig& c = s->cfgs[(size_t)idx];
   int tg = 0;
   if (c.kind == CFG_TILE) {
-    tg = tile1d_grid(s->kp, c.param);
+    tg = tile1d_grid(s->kp, s->p.precision, c.param);
     if (tg < 1) return SV_ECUDA;
   }
   if (s->graph) {

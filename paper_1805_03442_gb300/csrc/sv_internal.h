@@ -18,13 +18,13 @@ cudaError_t step1d_launch(int precision, const KParams& kp, void* a, void* b, Ct
                           int grid, cudaStream_t st);
 
 // Float 1D MUSCL-Hancock step on block tiles (sv_tile1d.cu), grids of at
-// least kTile1dMinCells cells
+// least kTile1dMinCells cells; precision PREC_FP32 or PREC_FP32_PC
 constexpr int64_t kTile1dMinCells = 4096;
 // var = 10 * (cell pairs per thread) + (blocks per SM of the register budget):
 // 13, 12 or 22
-int tile1d_grid(const KParams& kp, int var);
-cudaError_t tile1d_launch(const KParams& kp, int var, void* a, void* b, Ctl* ctl, int64_t N,
-                          int grid, cudaStream_t st);
+int tile1d_grid(const KParams& kp, int precision, int var);
+cudaError_t tile1d_launch(const KParams& kp, int precision, int var, void* a, void* b, Ctl* ctl,
+                          int64_t N, int grid, cudaStream_t st);
 
 // 1D persistent loop of up to nmax steps (sv_loop1d.cu); grid 0 = unavailable
 int loop1d_grid(const KParams& kp, int precision, int64_t N, int* cap);
@@ -42,10 +42,10 @@ int stepnd_grid(int dim, int precision, const KParams& kp);
 int stepnd_default_seg(int dim, int precision);
 cudaError_t stepnd_launch(int dim, int precision, const KParams& kp, void* a, void* b, Ctl* ctl,
                           const int64_t* n, int seg, cudaStream_t st);
-// The float (all-float pressure) 2D / 3D step marching plane pairs
-// (sv_stepnd_pair.cu); n == nullptr sets the kernels' shared-memory limits
+// The float 2D step marching plane pairs (sv_stepnd_pair.cu), precision
+// PREC_FP32 or PREC_FP32_PC; n == nullptr sets the kernels' shared-memory limits
 int stepnd_pair_default_seg(int dim);
-cudaError_t stepnd_pair_launch(int dim, const KParams& kp, void* a, void* b, Ctl* ctl,
+cudaError_t stepnd_pair_launch(int dim, int precision, const KParams& kp, void* a, void* b, Ctl* ctl,
                                const int64_t* n, int seg, cudaStream_t st);
 
 // Batched sweep kernels of 256 (sv_batch.cu) and 128 (sv_batch128.cu) threads

@@ -236,6 +236,12 @@ __device__ __forceinline__ R pressure(const P<R>& k, R kin2, R E, R Ev) {
     const float t = __fsub_rn(s, h);
     const float e2 = __fsub_rn(__fsub_rn(s, t), h);
     return __fmaf_rn(k.g1, t, __fmaf_rn(k.g1lo, t, __fmul_rn(k.g1, __fadd_rn(e1, e2))));
+  } else if constexpr (std::is_same<R, float>::value) {
+    // The cancelling pair first: E - E_nu is exact whenever E_nu >= E / 2
+    // (Sterbenz), which is where the cancellation bites, so p stays within
+    // ~1.4 ulp of the exact value of the float operands however large E_nu
+    // is (the order E - kin2/2 - E_nu loses log2(E / p) bits there).
+    return k.g1 * fmaf(kin2, -0.5f, E - Ev);
   } else {
     return k.g1 * (E - (R)0.5 * kin2 - Ev);
   }

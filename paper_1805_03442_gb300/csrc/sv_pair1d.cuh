@@ -47,16 +47,36 @@ __device__ __forceinline__ float slope(float a, float b) {
   return limit<LIM, float>(a, b);
 }
 
+// eq. 5 of two states, rho |v|^2 = kin2 given: PP = 0 in float (E - E_nu
+// first, as pressure<float, 0>), PP = 2 in compensated float (the
+// pressure<float, 2> policy); component by component, each packed add,
+// subtract and fused multiply-add rounds as the scalar one.
+template <int PP>
+__device__ __forceinline__ f2 pressure(const P<float>& k, f2 kin2, f2 E, f2 Ev) {
+  static_assert(PP == 0 || PP == 2, "packed pressure policies: float or compensated float");
+  if constexpr (PP == 2) {
+    const f2 h = mul(splat(0.5f), kin2);
+    const f2 s = sub(E, Ev);
+    const f2 e1 = sub(sub(E, s), Ev);
+    const f2 t = sub(s, h);
+    const f2 e2 = sub(sub(s, t), h);
+    return fma(splat(k.g1), t, fma(splat(k.g1lo), t, mul(splat(k.g1), add(e1, e2))));
+  } else {
+    return mul(splat(k.g1), fma(kin2, splat(-0.5f), sub(E, Ev)));
+  }
+}
+
 // Primitive recovery (eq. 5, eq. 7) of two states: 1/rho, v, rho v^2, p.
 struct Prim {
   f2 ir, v, kin2, p;
 };
+template <int PP>
 __device__ __forceinline__ Prim prim(const P<float>& k, const f2 (&u)[4]) {
   Prim q;
   q.ir = rcp(u[0]);
   q.v = mul(u[1], q.ir);
   q.kin2 = mul(u[1], q.v);
-  q.p = mul(splat(k.g1), sub(fma(q.kin2, splat(-0.5f), u[2]), u[3]));
+  q.p = pressure<PP>(k, q.kin2, u[2], u[3]);
   return q;
 }
 
@@ -84,7 +104,7 @@ __device__ __forceinline__ void source(const P<float>& k, f2 rho, f2 T, f2 Ev, f
 // Slopes, positivity guard, half-step predictor and face states of the two
 // cells X from their one-sided differences A (left) and B (right); as
 // predict() of the scalar body.
-template <int LIM, int SRC>
+template <int PP, int LIM, int SRC>
 __device__ __forceinline__ void predict(const P<float>& k, const f2 (&X)[4], const f2 (&A)[4],
                                         const f2 (&B)[4], f2 ndt_2h, f2 dt_2, f2 (&WP)[4],
                                         f2 (&WM)[4], f2& yEh, f2& yEvh) {
@@ -95,7 +115,7 @@ __device__ __forceinline__ void predict(const P<float>& k, const f2 (&X)[4], con
     a[f] = fma(splat(0.5f), d[f], X[f]);
     b[f] = fma(splat(-0.5f), d[f], X[f]);
   }
-  const Prim pa = prim(k, a), pb = prim(k, b);
+  const Prim pa = prim<PP>(k, a), pb = prim<PP>(k, b);
   f2 dF[4];
   dF[0] = sub(a[1], b[1]);
   dF[1] = sub(add(pa.kin2, pa.p), add(pb.kin2, pb.p));
@@ -113,7 +133,7 @@ __device__ __forceinline__ void predict(const P<float>& k, const f2 (&X)[4], con
   }
   f2 yE = splat(0.0f), yEv = splat(0.0f);
   if (SRC != 0) {
-    const Prim pu = prim(k, X);
+    const Prim pu = prim<PP>(k, X);
     source<SRC>(k, X[0], mul(pu.p, pu.ir), X[3], yE, yEv);
   }
   f2 uh[4];
@@ -129,7 +149,7 @@ __device__ __forceinline__ void predict(const P<float>& k, const f2 (&X)[4], con
   }
   yEh = yEvh = splat(0.0f);
   if (SRC != 0) {
-    const Prim ph = prim(k, uh);
+    const Prim ph = prim<PP>(k, uh);
     source<SRC>(k, uh[0], mul(ph.p, ph.ir), uh[3], yEh, yEvh);
   }
 }
@@ -138,9 +158,10 @@ __device__ __forceinline__ void predict(const P<float>& k, const f2 (&X)[4], con
 // non-physical state uses the cell values (fl, fr) instead.  Written with
 // -S_L >= 0 so that every weight is non-negative:
 //   F = (S_R F_L + (-S_L) F_R + (-S_L) S_R (L - R)) / (S_R - S_L).
+template <int PP>
 __device__ __forceinline__ void hll(const P<float>& k, f2 (&L)[4], f2 (&R)[4], const f2 (&fl)[4],
                                     const f2 (&fr)[4], f2 (&F)[4]) {
-  Prim pl = prim(k, L), pr = prim(k, R);
+  Prim pl = prim<PP>(k, L), pr = prim<PP>(k, R);
   const bool g0 = fminf(fminf(L[0].x, pl.p.x), fminf(R[0].x, pr.p.x)) > 0.0f;
   const bool g1 = fminf(fminf(L[0].y, pl.p.y), fminf(R[0].y, pr.p.y)) > 0.0f;
   if (!(g0 && g1)) {
@@ -149,8 +170,8 @@ __device__ __forceinline__ void hll(const P<float>& k, f2 (&L)[4], f2 (&R)[4], c
       if (!g0) { L[f].x = fl[f].x; R[f].x = fr[f].x; }
       if (!g1) { L[f].y = fl[f].y; R[f].y = fr[f].y; }
     }
-    pl = prim(k, L);
-    pr = prim(k, R);
+    pl = prim<PP>(k, L);
+    pr = prim<PP>(k, R);
   }
   const f2 gam = splat(k.gamma);
   const f2 cL = sqrt_pos(mul(mul(gam, pl.p), pl.ir));
@@ -182,10 +203,10 @@ __device__ __forceinline__ void update(const f2 (&Q)[4], const f2 (&Fl)[4], cons
 
 // eq. 16 signal speed and tau key of updated states N, folded into the
 // lane's maxima for the cells whose mask bit is set (bit 0: .x, bit 1: .y).
-template <int SRC>
+template <int PP, int SRC>
 __device__ __forceinline__ void cfl(const P<float>& k, const f2 (&N)[4], int mask, float& smax,
                                     float& akey, uint32_t& flags) {
-  const Prim q = prim(k, N);
+  const Prim q = prim<PP>(k, N);
   const f2 c = sqrt_pos(mul(mul(splat(k.gamma), q.p), q.ir));
   f2 key = splat(-INFINITY);
   if (SRC != 0) {

@@ -29,8 +29,9 @@ struct Prim {
   f2 ir, v[DIM], kin2, p;
 };
 
-// Primitive recovery (eq. 5, eq. 7) of two states.
-template <int DIM>
+// Primitive recovery (eq. 5, eq. 7) of two states; PP the pressure policy
+// (pk::pressure: 0 float, 2 compensated float).
+template <int DIM, int PP>
 __device__ __forceinline__ Prim<DIM> prim(const P<float>& k, const f2 (&u)[DIM + 3]) {
   Prim<DIM> q;
   q.ir = rcp(u[0]);
@@ -39,7 +40,7 @@ __device__ __forceinline__ Prim<DIM> prim(const P<float>& k, const f2 (&u)[DIM +
   q.kin2 = mul(u[1], q.v[0]);
 #pragma unroll
   for (int a = 1; a < DIM; ++a) q.kin2 = fma(u[1 + a], q.v[a], q.kin2);
-  q.p = mul(splat(k.g1), sub(fma(q.kin2, splat(-0.5f), u[1 + DIM]), u[2 + DIM]));
+  q.p = pk::pressure<PP>(k, q.kin2, u[1 + DIM], u[2 + DIM]);
   return q;
 }
 
@@ -55,7 +56,7 @@ __device__ __forceinline__ void flux(const f2 (&u)[DIM + 3], const Prim<DIM>& q,
 
 // F(u + d/2) - F(u - d/2) along axis A; ok0 / ok1 stay true while both
 // extrapolated states of that cell are physical.
-template <int DIM, int A>
+template <int DIM, int PP, int A>
 __device__ __forceinline__ void dflux(const P<float>& k, const f2 (&u)[DIM + 3], const f2 (&d)[DIM + 3],
                                       f2 (&dF)[DIM + 3], bool& ok0, bool& ok1) {
   constexpr int NF = DIM + 3;
@@ -65,7 +66,7 @@ __device__ __forceinline__ void dflux(const P<float>& k, const f2 (&u)[DIM + 3],
     a[f] = fma(splat(0.5f), d[f], u[f]);
     b[f] = fma(splat(-0.5f), d[f], u[f]);
   }
-  const Prim<DIM> pa = prim<DIM>(k, a), pb = prim<DIM>(k, b);
+  const Prim<DIM> pa = prim<DIM, PP>(k, a), pb = prim<DIM, PP>(k, b);
   f2 Fa[NF], Fb[NF];
   flux<DIM, A>(a, pa, Fa);
   flux<DIM, A>(b, pb, Fb);
@@ -76,22 +77,22 @@ __device__ __forceinline__ void dflux(const P<float>& k, const f2 (&u)[DIM + 3],
 }
 
 // Components E and E_nu of Y (eq. 6 closures) of two states.
-template <int DIM, int SRC>
+template <int DIM, int PP, int SRC>
 __device__ __forceinline__ void source(const P<float>& k, const f2 (&u)[DIM + 3], f2& yE, f2& yEv) {
   yE = yEv = splat(0.0f);
   if (SRC == 0) return;
-  const Prim<DIM> q = prim<DIM>(k, u);
+  const Prim<DIM> q = prim<DIM, PP>(k, u);
   pk::source<SRC>(k, u[0], mul(q.p, q.ir), u[2 + DIM], yE, yEv);
 }
 
 // eq. 13 along axis A at two faces with left states L and right states R; a
 // face with a non-physical state uses the cell values (fl, fr).  Weights as in
 // pk::hll (all non-negative).
-template <int DIM, int A>
+template <int DIM, int PP, int A>
 __device__ __forceinline__ void hll(const P<float>& k, f2 (&L)[DIM + 3], f2 (&R)[DIM + 3],
                                     const f2 (&fl)[DIM + 3], const f2 (&fr)[DIM + 3], f2 (&F)[DIM + 3]) {
   constexpr int NF = DIM + 3;
-  Prim<DIM> pl = prim<DIM>(k, L), pr = prim<DIM>(k, R);
+  Prim<DIM> pl = prim<DIM, PP>(k, L), pr = prim<DIM, PP>(k, R);
   const bool g0 = fminf(fminf(L[0].x, pl.p.x), fminf(R[0].x, pr.p.x)) > 0.0f;
   const bool g1 = fminf(fminf(L[0].y, pl.p.y), fminf(R[0].y, pr.p.y)) > 0.0f;
   if (!(g0 && g1)) {
@@ -100,8 +101,8 @@ __device__ __forceinline__ void hll(const P<float>& k, f2 (&L)[DIM + 3], f2 (&R)
       if (!g0) { L[f].x = fl[f].x; R[f].x = fr[f].x; }
       if (!g1) { L[f].y = fl[f].y; R[f].y = fr[f].y; }
     }
-    pl = prim<DIM>(k, L);
-    pr = prim<DIM>(k, R);
+    pl = prim<DIM, PP>(k, L);
+    pr = prim<DIM, PP>(k, R);
   }
   const f2 gam = splat(k.gamma);
   const f2 cL = pk::sqrt_pos(mul(mul(gam, pl.p), pl.ir));
@@ -121,10 +122,10 @@ __device__ __forceinline__ void hll(const P<float>& k, f2 (&L)[DIM + 3], f2 (&R)
 
 // eq. 16 signal speed and tau key of two updated states, folded for the cells
 // whose mask bit is set (bit 0: .x, bit 1: .y).
-template <int DIM, int SRC>
+template <int DIM, int PP, int SRC>
 __device__ __forceinline__ void cfl(const P<float>& k, const f2 (&N)[DIM + 3], int mask, float& smax,
                                     float& akey, uint32_t& flags) {
-  const Prim<DIM> q = prim<DIM>(k, N);
+  const Prim<DIM> q = prim<DIM, PP>(k, N);
   const f2 c = pk::sqrt_pos(mul(mul(splat(k.gamma), q.p), q.ir));
   f2 v2 = mul(q.v[0], q.v[0]);
 #pragma unroll

@@ -407,9 +407,7 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
 // ------------------------------------------------------------------ launch
 
 template <int DIM, int PREC> struct Cfg;
-template <> struct Cfg<2, PREC_FP32> { static constexpr int TX = 256, TY = 1, MINB = 2, SEG = 256; };
 template <> struct Cfg<2, PREC_FP32_P64> { static constexpr int TX = 256, TY = 1, MINB = 2, SEG = 256; };
-template <> struct Cfg<2, PREC_FP32_PC> { static constexpr int TX = 256, TY = 1, MINB = 2, SEG = 256; };
 template <> struct Cfg<2, PREC_FP64> { static constexpr int TX = 128, TY = 1, MINB = 2, SEG = 256; };
 template <> struct Cfg<3, PREC_FP32> { static constexpr int TX = 32, TY = 16, MINB = 1, SEG = 128; };
 template <> struct Cfg<3, PREC_FP32_P64> { static constexpr int TX = 32, TY = 16, MINB = 1, SEG = 128; };
@@ -459,11 +457,13 @@ static cudaError_t by_prec(int precision, const KParams& kp, void* a, void* b, C
   switch (precision) {
     case PREC_FP64: return launch_nd<double, 0, LIM, SRC, DIM, PREC_FP64>(kp, a, b, ctl, n, seg, st);
     case PREC_FP32_P64: return launch_nd<float, 1, LIM, SRC, DIM, PREC_FP32_P64>(kp, a, b, ctl, n, seg, st);
-    case PREC_FP32_PC: return launch_nd<float, 2, LIM, SRC, DIM, PREC_FP32_PC>(kp, a, b, ctl, n, seg, st);
     default:
-      // 2D: packed plane pairs; 3D keeps one cell per thread (the pair kernel
-      // needs 242 registers there, one block per SM, and runs 17% slower)
-      if constexpr (DIM == 2) return stepnd_pair_launch(DIM, kp, a, b, ctl, n, seg, st);
+      // float and compensated-float pressure: in 2D packed plane pairs; 3D
+      // keeps one cell per thread (the pair kernel needs 242 registers there,
+      // one block per SM, and runs 17% slower)
+      if constexpr (DIM == 2) return stepnd_pair_launch(DIM, precision, kp, a, b, ctl, n, seg, st);
+      else if (precision == PREC_FP32_PC)
+        return launch_nd<float, 2, LIM, SRC, DIM, PREC_FP32_PC>(kp, a, b, ctl, n, seg, st);
       else return launch_nd<float, 0, LIM, SRC, DIM, PREC_FP32>(kp, a, b, ctl, n, seg, st);
   }
 }
@@ -488,7 +488,8 @@ static cudaError_t by_lim(int precision, const KParams& kp, void* a, void* b, Ct
 
 // Default planes per block segment along the marching axis.
 int stepnd_default_seg(int dim, int precision) {
-  if (precision == PREC_FP32 && dim == 2) return stepnd_pair_default_seg(dim);
+  if ((precision == PREC_FP32 || precision == PREC_FP32_PC) && dim == 2)
+    return stepnd_pair_default_seg(dim);
   if (dim == 2) return precision == PREC_FP64 ? Cfg<2, PREC_FP64>::SEG : Cfg<2, PREC_FP32_P64>::SEG;
   if (precision == PREC_FP32_PC) return Cfg<3, PREC_FP32_PC>::SEG;
   return precision == PREC_FP64 ? Cfg<3, PREC_FP64>::SEG : Cfg<3, PREC_FP32>::SEG;

@@ -52,7 +52,7 @@ constexpr size_t pair_smem() {
                           (size_t)kPairRing * NF * PairHalo<DIM, TX, TY>::N);
 }
 
-template <int LIM, int SRC, int DIM, int TX, int TY, int MINB, bool BND>
+template <int PP, int LIM, int SRC, int DIM, int TX, int TY, int MINB, bool BND>
 __global__ void __launch_bounds__(TX * TY, MINB)
 stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bufB,
                    Ctl* __restrict__ ctl, int64_t nx, int64_t ny, int64_t nz, int tiles_x,
@@ -230,12 +230,12 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
     }
     f2 div[NF], dF[NF];
     bool ok0 = true, ok1 = true;
-    pkn::dflux<DIM, 0>(k, X, d[0], div, ok0, ok1);
-    pkn::dflux<DIM, 1>(k, X, d[1], dF, ok0, ok1);
+    pkn::dflux<DIM, PP, 0>(k, X, d[0], div, ok0, ok1);
+    pkn::dflux<DIM, PP, 1>(k, X, d[1], dF, ok0, ok1);
 #pragma unroll
     for (int f = 0; f < NF; ++f) div[f] = pk::add(div[f], dF[f]);
     if (DIM == 3) {
-      pkn::dflux<DIM, DIM == 3 ? 2 : 1>(k, X, d[AM], dF, ok0, ok1);
+      pkn::dflux<DIM, PP, DIM == 3 ? 2 : 1>(k, X, d[AM], dF, ok0, ok1);
 #pragma unroll
       for (int f = 0; f < NF; ++f) div[f] = pk::add(div[f], dF[f]);
     }
@@ -257,7 +257,7 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
     // the cells' media (2D map: frozen cells have no source)
     const bool act0 = active(j0), act1 = active(j1);
     f2 yE, yEv;
-    pkn::source<DIM, SRC>(k, X, yE, yEv);
+    pkn::source<DIM, PP, SRC>(k, X, yE, yEv);
     if (!act0) yE.x = yEv.x = 0.0f;
     if (!act1) yE.y = yEv.y = 0.0f;
     f2 uh[NF];
@@ -266,7 +266,7 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
     if (SRC == 2) uh[1 + DIM] = pk::fma(dt_22, yE, uh[1 + DIM]);
     if (SRC != 0) uh[2 + DIM] = pk::fma(dt_22, yEv, uh[2 + DIM]);
     f2 yEh, yEvh;
-    pkn::source<DIM, SRC>(k, uh, yEh, yEvh);
+    pkn::source<DIM, PP, SRC>(k, uh, yEh, yEvh);
     if (!act0) yEh.x = yEvh.x = 0.0f;
     if (!act1) yEh.y = yEvh.y = 0.0f;
 
@@ -288,7 +288,7 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
         Rr[f] = pk::fma(nhalf, d[0][f], uh[f]);
         fl[f] = pk::pair(sU[0][f][oy][tx], sU[1][f][oy][tx]);
       }
-      pkn::hll<DIM, 0>(k, L, Rr, fl, X, Fx);
+      pkn::hll<DIM, PP, 0>(k, L, Rr, fl, X, Fx);
       if (DIM == 3) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
@@ -296,7 +296,7 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
           Rr[f] = pk::fma(nhalf, d[1][f], uh[f]);
           fl[f] = pk::pair(sU[0][f][oy > 0 ? oy - 1 : oy][tx + 1], sU[1][f][oy > 0 ? oy - 1 : oy][tx + 1]);
         }
-        pkn::hll<DIM, DIM == 3 ? 1 : 0>(k, L, Rr, fl, X, Fy);
+        pkn::hll<DIM, PP, DIM == 3 ? 1 : 0>(k, L, Rr, fl, X, Fy);
       }
     }
 #pragma unroll
@@ -328,7 +328,7 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
         fl[f] = pk::pair(um[f], u0[f]);
         wpm_next[f] = wp.y;
       }
-      pkn::hll<DIM, AM>(k, L, Rr, fl, X, Hq);
+      pkn::hll<DIM, PP, AM>(k, L, Rr, fl, X, Hq);
     }
 
     // f. update of planes q-2 and q-1 (interior planes: no ghosts)
@@ -365,7 +365,7 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
         Uout[f * ncell + oa] = Nw[f].x;
         if (two) Uout[f * ncell + ob] = Nw[f].y;
       }
-      pkn::cfl<DIM, SRC>(k, Nw, two ? 3 : 1, smax, akey, flags);
+      pkn::cfl<DIM, PP, SRC>(k, Nw, two ? 3 : 1, smax, akey, flags);
     }
 
 #pragma unroll
@@ -386,23 +386,23 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
 template <int DIM> struct PairCfg;
 template <> struct PairCfg<2> { static constexpr int TX = 128, TY = 1, MINB = 3, SEG = 128; };
 
-template <int LIM, int SRC, int DIM>
+template <int PP, int LIM, int SRC, int DIM>
 cudaError_t launch_pair(const KParams& kp, void* a, void* b, Ctl* ctl, const int64_t* n, int seg,
                         cudaStream_t st) {
   using G = PairCfg<DIM>;
   constexpr size_t smem = pair_smem<DIM, G::TX, G::TY>();
   if (!n) {
-    cudaError_t e = cudaFuncSetAttribute(stepnd_pair_kernel<LIM, SRC, DIM, G::TX, G::TY, G::MINB, false>,
+    cudaError_t e = cudaFuncSetAttribute(stepnd_pair_kernel<PP, LIM, SRC, DIM, G::TX, G::TY, G::MINB, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess || DIM != 2) return e;
-    return cudaFuncSetAttribute(stepnd_pair_kernel<LIM, SRC, DIM, G::TX, G::TY, G::MINB, DIM == 2>,
+    return cudaFuncSetAttribute(stepnd_pair_kernel<PP, LIM, SRC, DIM, G::TX, G::TY, G::MINB, DIM == 2>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
   const bool bnd = DIM == 2 && (kp.bc_lo != BC_PERIODIC || kp.bc_hi != BC_PERIODIC ||
                                 kp.bc_ylo != BC_PERIODIC || kp.bc_yhi != BC_PERIODIC ||
                                 kp.act_lo != nullptr || kp.pul_lo != nullptr);
-  auto fn = bnd ? stepnd_pair_kernel<LIM, SRC, DIM, G::TX, G::TY, G::MINB, DIM == 2>
-                : stepnd_pair_kernel<LIM, SRC, DIM, G::TX, G::TY, G::MINB, false>;
+  auto fn = bnd ? stepnd_pair_kernel<PP, LIM, SRC, DIM, G::TX, G::TY, G::MINB, DIM == 2>
+                : stepnd_pair_kernel<PP, LIM, SRC, DIM, G::TX, G::TY, G::MINB, false>;
   const int64_t nx = n[0], ny = n[1], nz = DIM == 3 ? n[2] : 1;
   const int tiles_x = (int)((nx + G::TX - 3) / (G::TX - 2));
   const int tiles_y = DIM == 3 ? (int)((ny + G::TY - 3) / (G::TY - 2)) : 1;
@@ -418,15 +418,15 @@ cudaError_t launch_pair(const KParams& kp, void* a, void* b, Ctl* ctl, const int
   return cudaGetLastError();
 }
 
-template <int DIM>
+template <int PP, int DIM>
 cudaError_t pair_by_kind(const KParams& kp, void* a, void* b, Ctl* ctl, const int64_t* n, int seg,
                          cudaStream_t st) {
   const int src = kp.frozen ? 0 : (kp.qi_zero ? 1 : 2);
 #define SV_PAIR_SRC(LIM)                                                   \
   switch (src) {                                                           \
-    case 0: return launch_pair<LIM, 0, DIM>(kp, a, b, ctl, n, seg, st);    \
-    case 1: return launch_pair<LIM, 1, DIM>(kp, a, b, ctl, n, seg, st);    \
-    default: return launch_pair<LIM, 2, DIM>(kp, a, b, ctl, n, seg, st);   \
+    case 0: return launch_pair<PP, LIM, 0, DIM>(kp, a, b, ctl, n, seg, st);    \
+    case 1: return launch_pair<PP, LIM, 1, DIM>(kp, a, b, ctl, n, seg, st);    \
+    default: return launch_pair<PP, LIM, 2, DIM>(kp, a, b, ctl, n, seg, st);   \
   }
   switch (kp.limiter) {
     case 1: SV_PAIR_SRC(1)
@@ -443,9 +443,11 @@ int stepnd_pair_default_seg(int) { return PairCfg<2>::SEG; }
 // n == nullptr: set the kernels' shared-memory limits (host side, at set-up).
 // 2D only: in 3D the pair kernel needs 242 registers (one 8-warp block per SM)
 // and loses to one cell per thread.
-cudaError_t stepnd_pair_launch(int dim, const KParams& kp, void* a, void* b, Ctl* ctl,
+cudaError_t stepnd_pair_launch(int dim, int precision, const KParams& kp, void* a, void* b, Ctl* ctl,
                                const int64_t* n, int seg, cudaStream_t st) {
-  if (dim == 2) return pair_by_kind<2>(kp, a, b, ctl, n, seg, st);
+  if (dim == 2)
+    return precision == PREC_FP32_PC ? pair_by_kind<2, 2>(kp, a, b, ctl, n, seg, st)
+                                     : pair_by_kind<0, 2>(kp, a, b, ctl, n, seg, st);
   return cudaErrorInvalidValue;
 }
 

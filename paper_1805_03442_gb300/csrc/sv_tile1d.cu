@@ -86,7 +86,7 @@ __device__ __forceinline__ void load_tile(float (*dst)[SPAN], const float* Uin, 
   cp_async_commit();
 }
 
-template <int LIM, int SRC, int MINB, int NPT>
+template <int PP, int LIM, int SRC, int MINB, int NPT>
 __global__ void __launch_bounds__(NTT, MINB)
 tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bufB,
               Ctl* __restrict__ ctl, int N) {
@@ -136,7 +136,7 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
         A[f] = pk::sub(X[p][f], XM[p][f]);
         B[f] = pk::sub(pk::pair(X[p][f].y, rf[pos + 2]), X[p][f]);
       }
-      pk::predict<LIM, SRC>(k, X[p], A, B, ndt_2h2, dt_22, WP[p], WM[p], YE[p], YEv[p]);
+      pk::predict<PP, LIM, SRC>(k, X[p], A, B, ndt_2h2, dt_22, WP[p], WM[p], YE[p], YEv[p]);
     }
 
     if (lane == 31) {
@@ -158,7 +158,7 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
       f2 L[4];
 #pragma unroll
       for (int f = 0; f < 4; ++f) L[f] = pk::pair(p ? WP[p - 1][f].y : nb[f], WP[p][f].x);
-      pk::hll(k, L, WM[p], XM[p], X[p], F[p]);    // the pair's left and inner faces
+      pk::hll<PP>(k, L, WM[p], XM[p], X[p], F[p]);   // the pair's left and inner faces
     }
 
     if (lane == 0) {
@@ -182,7 +182,7 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
         for (int f = 0; f < 4; ++f) FR[f] = pk::pair(F[p][f].y, p < NPT - 1 ? F[p + 1][f].x : nf[f]);
         pk::update<SRC>(X[p], F[p], FR, YE[p], YEv[p], dt2, ndtdx2, Nw);
         const bool two = j + 1 < N;
-        pk::cfl<SRC>(k, Nw, two ? 3 : 1, smax, akey, flags);
+        pk::cfl<PP, SRC>(k, Nw, two ? 3 : 1, smax, akey, flags);
         if (two && (N & 1) == 0) {
 #pragma unroll
           for (int f = 0; f < 4; ++f) *reinterpret_cast<f2*>(Uout + (size_t)f * N + j) = Nw[f];
@@ -204,37 +204,42 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
 // per thread at a register budget of 3 blocks per SM (80 registers, 24 warps
 // per SM) or 2 (its natural ~94 registers), or two pairs per thread (1024-cell
 // tiles: half the barriers and exchanges per cell, two independent chains)
-// at 2 blocks per SM.
-template <int LIM, int SRC>
+// at 2 blocks per SM.  PP: the pressure policy (0 float, 2 compensated float).
+template <int PP, int LIM, int SRC>
 struct KT {
-  static constexpr auto fn13 = tile1d_kernel<LIM, SRC, 3, 1>;
-  static constexpr auto fn12 = tile1d_kernel<LIM, SRC, 2, 1>;
-  static constexpr auto fn22 = tile1d_kernel<LIM, SRC, 2, 2>;
+  static constexpr auto fn13 = tile1d_kernel<PP, LIM, SRC, 3, 1>;
+  static constexpr auto fn12 = tile1d_kernel<PP, LIM, SRC, 2, 1>;
+  static constexpr auto fn22 = tile1d_kernel<PP, LIM, SRC, 2, 2>;
 };
 
-template <int LIM, int SRC>
+template <int PP, int LIM, int SRC>
 void* pick_var(int var) {
-  if (var == 12) return (void*)KT<LIM, SRC>::fn12;
-  if (var == 22) return (void*)KT<LIM, SRC>::fn22;
-  return (void*)KT<LIM, SRC>::fn13;
+  if (var == 12) return (void*)KT<PP, LIM, SRC>::fn12;
+  if (var == 22) return (void*)KT<PP, LIM, SRC>::fn22;
+  return (void*)KT<PP, LIM, SRC>::fn13;
 }
 
-template <int LIM>
+template <int PP, int LIM>
 void* pick_src(int src, int var) {
   switch (src) {
-    case 0: return pick_var<LIM, 0>(var);
-    case 1: return pick_var<LIM, 1>(var);
-    default: return pick_var<LIM, 2>(var);
+    case 0: return pick_var<PP, LIM, 0>(var);
+    case 1: return pick_var<PP, LIM, 1>(var);
+    default: return pick_var<PP, LIM, 2>(var);
   }
 }
 
-void* pick(const KParams& kp, int var) {
+template <int PP>
+void* pick_lim(const KParams& kp, int var) {
   const int src = kp.frozen ? 0 : (kp.qi_zero ? 1 : 2);
   switch (kp.limiter) {
-    case 1: return pick_src<1>(src, var);
-    case 2: return pick_src<2>(src, var);
-    default: return pick_src<0>(src, var);
+    case 1: return pick_src<PP, 1>(src, var);
+    case 2: return pick_src<PP, 2>(src, var);
+    default: return pick_src<PP, 0>(src, var);
   }
+}
+
+void* pick(const KParams& kp, int precision, int var) {
+  return precision == PREC_FP32_PC ? pick_lim<2>(kp, var) : pick_lim<0>(kp, var);
 }
 
 size_t smem_of(int var) { return var == 22 ? sizeof(TileSmem<2>) : sizeof(TileSmem<1>); }
@@ -243,9 +248,9 @@ size_t smem_of(int var) { return var == 22 ? sizeof(TileSmem<2>) : sizeof(TileSm
 
 // Sets the kernel's shared-memory limit (host side, outside any capture) and
 // returns the persistent grid size of variant `var` (13, 12 or 22), 0 on failure.
-int tile1d_grid(const KParams& kp, int var) {
+int tile1d_grid(const KParams& kp, int precision, int var) {
   int dev = 0, sms = 0, per = 0;
-  const void* fn = pick(kp, var);
+  const void* fn = pick(kp, precision, var);
   const size_t smem = smem_of(var);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;
@@ -256,12 +261,12 @@ int tile1d_grid(const KParams& kp, int var) {
   return sms * per;
 }
 
-cudaError_t tile1d_launch(const KParams& kp, int var, void* a, void* b, Ctl* ctl, int64_t N,
-                          int grid, cudaStream_t st) {
+cudaError_t tile1d_launch(const KParams& kp, int precision, int var, void* a, void* b, Ctl* ctl,
+                          int64_t N, int grid, cudaStream_t st) {
   if (N >= (1LL << 31) / 4 || N < kTile1dMinCells || grid < 1) return cudaErrorInvalidValue;
   int n32 = (int)N;
   void* args[] = {(void*)&kp, &a, &b, &ctl, &n32};
-  return cudaLaunchKernel(pick(kp, var), dim3(grid), dim3(NTT), args, smem_of(var), st);
+  return cudaLaunchKernel(pick(kp, precision, var), dim3(grid), dim3(NTT), args, smem_of(var), st);
 }
 
 }  // namespace sv

@@ -2,15 +2,17 @@
 
 p = (gamma - 1)(E - rho v^2/2 - E_nu) cancels when E_nu dominates E.  The
 float state is the same for the three float policies; they differ in how the
-subtraction is carried out: SV_FP32 in float (three roundings), SV_FP32_P64 in
-double, SV_FP32_PC in compensated float (exact difference, one rounding).
+subtraction is carried out: SV_FP32 in float with the cancelling pair E - E_nu
+first (exact by Sterbenz's lemma once E_nu >= E/2), SV_FP32_P64 in double,
+SV_FP32_PC in compensated float (exact difference, one rounding).
 
 The eq. 16 time step of a state at rest exposes p directly: dt = cfl h /
 (|v| + sqrt(gamma p / rho)), with no stored intermediate state in between.  The
 state below (E_nu = 1000, p = 1) is the one of a scan over rho v in which the
-float subtraction loses the most: E - rho v^2/2 rounds at the ulp of 1002.5,
-2^-14, so float p comes out as 1.0 against 0.99998779296875 exactly (1.2e-5),
-while a correctly rounded p is exact to 6e-8."""
+float subtraction in written order, (E - rho v^2/2) - E_nu, loses the most:
+E - rho v^2/2 rounds at the ulp of 1002.5, 2^-14, so that order gives p = 1.0
+against 0.99998779296875 exactly (1.2e-5), while each policy of the library
+stays within a few ulp of the exact p."""
 import math
 
 import numpy as np
@@ -56,15 +58,18 @@ def test_dt_exposes_pressure_policy(sv):
     # the exact pressure of the float state, and the float-arithmetic one
     p_exact = 0.4 * (U[2, 0] - 0.5 * U[1, 0] ** 2 - U[3, 0])
     assert p_exact == pytest.approx(0.99998779296875, rel=1e-15)
+    # the subtraction in written order, in float, is 1.2e-5 off on this state
+    f = np.float32
+    E, Ev, kin2 = f(U[2, 0]), f(U[3, 0]), f(U[1, 0]) * f(U[1, 0])
+    p_written = f(0.4) * ((E - f(0.5) * kin2) - Ev)
+    assert p_written == f(1.0) and abs(p_written - p_exact) / p_exact > 1.2e-5
     rel = {k: abs(v - ref) / ref for k, v in dts.items()}
-    # double and compensated float: only the approximate sqrt / reciprocal remain
-    assert rel["FP32_P64"] <= 1.5e-6
-    assert rel["FP32_PC"] <= 1.5e-6
-    # same pressure bits -> same dt bits
+    # every policy recovers p to a few ulp: only the approximate sqrt and
+    # reciprocal of the sound speed remain (p = 1.0 would put dt 5.9e-6 off)
+    for prec in FLOAT_POLICIES:
+        assert rel[prec] <= 1.5e-6, (prec, rel[prec])
+    # double and compensated float: the same pressure bits, the same dt bits
     assert dts["FP32_PC"] == dts["FP32_P64"]
-    # float subtraction: p = 1.0, c too large by 6.1e-6, dt too small by ~5.9e-6
-    assert 4e-6 <= rel["FP32"] <= 8e-6
-    assert dts["FP32"] < ref
 
 
 def _frozen_states(N, seed, ev_per_mass):
