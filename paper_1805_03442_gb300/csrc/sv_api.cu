@@ -246,6 +246,17 @@ int issue_steps(sv_solver* s, int64_t n) {
   return SV_OK;
 }
 
+// The device address of page-locked host memory (cudaHostAlloc or
+// cudaHostRegister, mapped), or null for any other pointer.
+const void* mapped_view(const void* host) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();                  // not a sticky error: clear it for later checks
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int read_ctl(sv_solver* s) {
   SV_TRY(cudaMemcpyAsync(s->host_ctl, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
   SV_TRY(cudaStreamSynchronize(s->stream));
@@ -387,10 +398,16 @@ int sv_init(const sv_params* p, const sv_grid* g, void* cuda_stream, void* devic
 int sv_write_state(sv_solver* s, const double* host_soa, double t) {
   if (!s || !host_soa) return SV_EINVAL;
   const size_t count = (size_t)s->nf * (size_t)s->ncell;
-  SV_TRY(cudaMemcpyAsync(s->staging, host_soa, count * sizeof(double), cudaMemcpyHostToDevice,
-                         s->stream));
+  // pinned host memory: the conversion kernel reads it over the host link
+  // itself (one pass instead of a copy into staging and a second pass)
+  const double* src = (const double*)mapped_view(host_soa);
+  if (!src) {
+    SV_TRY(cudaMemcpyAsync(s->staging, host_soa, count * sizeof(double), cudaMemcpyHostToDevice,
+                           s->stream));
+    src = s->staging;
+  }
   SV_TRY(ctl_reset_launch(s->ctl, t, s->stream));
-  SV_TRY(to_state_launch(s->p.precision, s->staging, s->buf[0], s->buf[1], s->ctl, (int64_t)count,
+  SV_TRY(to_state_launch(s->p.precision, src, s->buf[0], s->buf[1], s->ctl, (int64_t)count,
                          s->stream));
   SV_TRY(dt_reduce_launch(s->p.precision, s->dim, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell,
                           s->stream));
@@ -400,10 +417,13 @@ int sv_write_state(sv_solver* s, const double* host_soa, double t) {
 int sv_read_state(sv_solver* s, double* host_soa, double* t) {
   if (!s || !host_soa) return SV_EINVAL;
   const size_t count = (size_t)s->nf * (size_t)s->ncell;
-  SV_TRY(from_state_launch(s->p.precision, s->buf[0], s->buf[1], s->ctl, s->staging,
+  // pinned host memory: the conversion kernel writes it over the host link
+  double* dst = (double*)mapped_view(host_soa);
+  SV_TRY(from_state_launch(s->p.precision, s->buf[0], s->buf[1], s->ctl, dst ? dst : s->staging,
                            (int64_t)count, s->stream));
-  SV_TRY(cudaMemcpyAsync(host_soa, s->staging, count * sizeof(double), cudaMemcpyDeviceToHost,
-                         s->stream));
+  if (!dst)
+    SV_TRY(cudaMemcpyAsync(host_soa, s->staging, count * sizeof(double), cudaMemcpyDeviceToHost,
+                           s->stream));
   int rc = read_ctl(s);
   if (rc != SV_OK) return rc;
   if (t) *t = s->host_ctl->t;

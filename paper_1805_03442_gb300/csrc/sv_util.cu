@@ -112,21 +112,50 @@ cudaError_t dt_reduce_launch(int precision, int dim, const KParams& kp, const vo
   return cudaGetLastError();
 }
 
+// Host-format (double) <-> state conversion.  `src` / `dst` is a device
+// staging buffer or the device view of mapped pinned host memory (then the
+// kernel itself moves the bytes over the host link).  Pairs of elements go as
+// one 16-byte double2 access where both sides are aligned for it.
+template <typename R> struct Vec2;
+template <> struct Vec2<float> { using T = float2; };
+template <> struct Vec2<double> { using T = double2; };
+
 template <typename R>
 __global__ void to_state_kernel(const double* src, R* a, R* b, const Ctl* ctl, int64_t count) {
   R* U = vload(&ctl->cur) ? b : a;
-  for (int64_t i = (int64_t)blockIdx.x * NTU + threadIdx.x; i < count;
-       i += (int64_t)gridDim.x * NTU)
-    U[i] = (R)src[i];
+  using R2 = typename Vec2<R>::T;
+  const int64_t i0 = (int64_t)blockIdx.x * NTU + threadIdx.x, di = (int64_t)gridDim.x * NTU;
+  if (((uintptr_t)src & 15) == 0 && ((uintptr_t)U & (sizeof(R2) - 1)) == 0) {
+    const int64_t n2 = count / 2;
+    for (int64_t i = i0; i < n2; i += di) {
+      const double2 v = reinterpret_cast<const double2*>(src)[i];
+      R2 w;
+      w.x = (R)v.x;
+      w.y = (R)v.y;
+      reinterpret_cast<R2*>(U)[i] = w;
+    }
+    if (i0 == 0 && (count & 1)) U[count - 1] = (R)src[count - 1];
+  } else {
+    for (int64_t i = i0; i < count; i += di) U[i] = (R)src[i];
+  }
 }
 
 template <typename R>
 __global__ void from_state_kernel(const R* a, const R* b, const Ctl* ctl, double* dst,
                                   int64_t count) {
   const R* U = vload(&ctl->cur) ? b : a;
-  for (int64_t i = (int64_t)blockIdx.x * NTU + threadIdx.x; i < count;
-       i += (int64_t)gridDim.x * NTU)
-    dst[i] = (double)U[i];
+  using R2 = typename Vec2<R>::T;
+  const int64_t i0 = (int64_t)blockIdx.x * NTU + threadIdx.x, di = (int64_t)gridDim.x * NTU;
+  if (((uintptr_t)dst & 15) == 0 && ((uintptr_t)U & (sizeof(R2) - 1)) == 0) {
+    const int64_t n2 = count / 2;
+    for (int64_t i = i0; i < n2; i += di) {
+      const R2 w = reinterpret_cast<const R2*>(U)[i];
+      reinterpret_cast<double2*>(dst)[i] = make_double2((double)w.x, (double)w.y);
+    }
+    if (i0 == 0 && (count & 1)) dst[count - 1] = (double)U[count - 1];
+  } else {
+    for (int64_t i = i0; i < count; i += di) dst[i] = (double)U[i];
+  }
 }
 
 cudaError_t to_state_launch(int precision, const double* src, void* a, void* b, Ctl* ctl,
