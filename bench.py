@@ -174,6 +174,133 @@ def cpu_baseline(name: str, args, budget_s: float = 10.0) -> dict:
                       f"{'x'.join(map(str, dims))} cells ({el:.1f} s wall)"}
 
 
+def wc_problem(N: int):
+    """Colliding shock waves (Sec. 2.4): rho = 1, u = 0, p = 1000 / 0.01 / 100 on
+    [0, 0.1) / [0.1, 0.9] / (0.9, 1], passive e_nu 0.3, frozen gas, walls."""
+    from paper_1805_03442_gb300 import inputs
+    x = inputs.cell_centres(N, 1.0)
+    p = np.where(x < 0.1, 1000.0, np.where(x <= 0.9, 0.01, 100.0))
+    U0 = inputs.prim_to_cons(1.4, np.ones(N), [np.zeros(N)], p, np.full(N, 0.3))
+    return dict(tau0=math.inf, S=0.0), U0, 0.038
+
+
+def driven_problem(N: int, gamma: float = 1.4, Ck: float = 0.1, S: float = 0.5):
+    """Forced source (Sec. 3): the uniform equilibrium of S = 0.5, tau0 =
+    0.0135, and the boundary wave of wavelength 0.1 (frozen acoustic shape,
+    amplitude 1e-4): (params, U0, base state, amplitude vector, omega, k)."""
+    from paper_1805_03442_gb300 import inputs
+    rho0, p0, ev0 = inputs.equilibrium_primitive(Ck, S)
+    base = inputs.prim_to_cons(gamma, np.array([rho0]), [np.array([0.0])], np.array([p0]),
+                               np.array([ev0]))[:, 0]
+    w = 2 * math.pi / 0.1 * math.sqrt(gamma)
+    shape = inputs.acoustic_shape(gamma)          # rho', u', p', e_nu' of a frozen wave
+    amp = 1e-4 * np.array([shape[0], shape[1], shape[2] / (gamma - 1.0) + ev0 * shape[0],
+                           ev0 * shape[0]])
+    U0 = np.repeat(base[:, None], N, axis=1)
+    return dict(S=S, tau0=0.0135), U0, base, amp, w, w / math.sqrt(gamma)
+
+
+def oracle_rate(advance, ncell: int, budget_s: float):
+    """Cell-updates/s of the oracle: `advance(k)` runs k more steps and returns
+    the number it ran (0 once its run has ended); called with growing k until
+    `budget_s` of wall time.  Returns (rate, steps, seconds)."""
+    steps, k, t0 = 0, 4, time.perf_counter()
+    while True:
+        done = advance(k)
+        steps += done
+        el = time.perf_counter() - t0
+        if el >= budget_s or done == 0:
+            break
+        k = min(2 * k, 4096)
+    return (ncell * steps / el if steps else 0.0), steps, el
+
+
+def oracle_special(name: str, args, budget_s: float) -> dict:
+    """The FP64 oracle, as it stands, on the colliding-shock, forced-source,
+    active-sector and sweep workloads: a bounded sample of the same run(s).
+    The sweep's value is runs/s, extrapolated from the oracle's cell-update
+    rate over a stratified sample to the cell-updates the whole sweep needs
+    (each run: N cells x t_end / its initial eq.-16 step)."""
+    from oracle import orc as O
+    from paper_1805_03442_gb300 import inputs
+    if name == "wc":
+        N = args.n if args.n != 1 << 22 else 100000
+        prm, U, t_end = wc_problem(N)
+        Po = O.Params(**prm)
+        st = {"U": U, "t": 0.0}
+
+        def adv(k):
+            U2, t, n, rc = O.run_bc1(Po, st["U"], N, 1.0 / N, t_end, O.REFLECT, O.REFLECT,
+                                     t0=st["t"], max_steps=k)[:4]
+            st["U"], st["t"] = U2, t
+            return n if rc == 0 and t < t_end else 0
+        rate, steps, el = oracle_rate(adv, N, budget_s)
+        return {"value": rate, "unit": METRIC, "cores": O.threads(), "kind": "oracle",
+                "sample": f"first {steps} oracle steps of the colliding-shock run, N={N} "
+                          f"({el:.1f} s wall)"}
+    if name == "driven":
+        N = args.n if args.n != 1 << 22 else 1 << 16
+        prm, U, base, amp, w, kk = driven_problem(N)
+        Po = O.Params(**prm)
+        drv = O.drive(w, kk, base, amp)
+        st = {"U": U, "t": 0.0}
+
+        def adv(k):
+            U2, t, n, rc = O.run_driven(Po, st["U"], N, 1.0 / N, 1.0, drv, t0=st["t"],
+                                        max_steps=k)[:4]
+            st["U"], st["t"] = U2, t
+            return n if rc == 0 and t < 1.0 else 0
+        rate, steps, el = oracle_rate(adv, N, budget_s)
+        return {"value": rate, "unit": METRIC, "cores": O.threads(), "kind": "oracle",
+                "sample": f"first {steps} oracle steps of the forced-source run, N={N} "
+                          f"({el:.1f} s wall)"}
+    if name == "sector":
+        pb = inputs.sector_problem(args.side or 2048)
+        Po = O.Params(S=1.0, tau0=0.0135)
+        U = inputs.sector_rest_state(Po.gamma, Po.Ck, Po.S, pb.nx, pb.ny)
+        lo, hi, dlo, dhi = pb.maps
+        med = O.Medium2(lo, hi, dlo, dhi, pb.omega, pb.amp)
+        st = {"U": U, "t": 0.0}
+
+        def adv(k):
+            U2, t, n, rc = O.run2m(Po, st["U"], pb.nx, pb.ny, pb.h, 1.2, pb.bc, med, t0=st["t"],
+                                   max_steps=k)[:4]
+            st["U"], st["t"] = U2, t
+            return n if rc == 0 and t < 1.2 else 0
+        rate, steps, el = oracle_rate(adv, pb.nx * pb.ny, budget_s)
+        return {"value": rate, "unit": METRIC, "cores": O.threads(), "kind": "oracle",
+                "sample": f"first {steps} oracle steps of the active-sector run, "
+                          f"{pb.nx}x{pb.ny} ({el:.1f} s wall)"}
+    if name == "sweep":
+        runs, states = sweep_inputs(args.runs)
+        cost = [r.N * r.t_end / O.dt_cfl(_oracle_params(O, r), st, r.N, 1.0 / r.N)
+                for r, st in zip(runs, states)]
+        order = sorted(range(len(runs)), key=lambda i: cost[i])
+        sample = order[:: max(1, len(runs) // 64)]
+        cells, t0, used = 0, time.perf_counter(), 0
+        for i in sample:
+            r = runs[i]
+            _, _, n, _ = O.run(_oracle_params(O, r), states[i], r.N, 1.0 / r.N, r.t_end,
+                               max_steps=max(1, int(2e6 // r.N)))[:4]
+            cells += n * r.N
+            used += 1
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        el = time.perf_counter() - t0
+        rate = cells / el
+        return {"value": len(runs) / (sum(cost) / rate), "unit": "runs/s", "cores": O.threads(),
+                "kind": "oracle", "cell_updates_per_s": rate,
+                "sample": f"up to 2e6 cell-updates of each of {used} runs of a cost-stratified "
+                          f"sample ({el:.1f} s wall), extrapolated to the sweep's "
+                          f"{sum(cost):.3g} cell-updates (N t_end / initial dt per run)"}
+    raise ValueError(name)
+
+
+def _oracle_params(O, r):
+    return O.Params(S=r.S, tau0=r.tau0, tau_rho=r.tau_rho, tau_T=r.tau_T, Q_rho=r.Q_rho,
+                    Q_T=r.Q_T, I_rho=r.I_rho, I_T=r.I_T)
+
+
 def dist_init():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
@@ -208,6 +335,19 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import orc as O
+    if args.workload not in WORKLOADS:
+        # bounded samples of the same runs; value in the GPU line's unit
+        base = oracle_special(args.workload, args, budget_s=max(args.cpu_budget, 10.0))
+        unit = base["unit"]
+        line = {"impl": "reference", "metric": "batched sweep runs/s" if unit == "runs/s" else METRIC,
+                "value": base["value"], "unit": unit, "n_gpus": 1, "steps": 1, "warmup": 0,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": args.workload},
+                "cpu_baseline": base,
+                "e2e": {"value": base["value"], "unit": unit, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     W = WORKLOADS[args.workload]
     P = O.Params(**W["params"])
     dims = W["dims"](args)
@@ -487,6 +627,8 @@ def run_sweep(args):
             "subset": {"runs": len(sub), "looped_single_runs_s": t_loop, "batched_s": t_sub,
                        "speedup": t_loop / t_sub},
             "gpu_launches": 2, "clocks": getattr(clk, "result", None)}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_special("sweep", args, args.cpu_budget)
     print(json.dumps(line), flush=True)
 
 
@@ -500,10 +642,8 @@ def run_wc(args):
     build()
     N = args.n if args.n != 1 << 22 else 100000
     prec = PRECISIONS[args.precision]
-    P = sv.Params(precision=prec, tau0=math.inf, S=0.0)
-    x = inputs.cell_centres(N, 1.0)
-    p = np.where(x < 0.1, 1000.0, np.where(x <= 0.9, 0.01, 100.0))
-    U0 = inputs.prim_to_cons(1.4, np.ones(N), [np.zeros(N)], p, np.full(N, 0.3))
+    prm, U0, _ = wc_problem(N)
+    P = sv.Params(precision=prec, **prm)
     stream = torch.cuda.Stream()
     s = sv.Solver(P, (N,), (1.0,), stream=stream, bc=(sv.BC_REFLECT, sv.BC_REFLECT))
     s.write_state(U0)
@@ -529,6 +669,8 @@ def run_wc(args):
                        "cells": N, "l2": "not flushed: whole run timed (3.2 MB state)"},
             "time_to_solution_s": wall, "gpu_event_s": gpu_s, "gpu_launches": steps,
             "clocks": getattr(clk, "result", None)}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_special("wc", args, args.cpu_budget)
     print(json.dumps(line), flush=True)
 
 
@@ -594,6 +736,8 @@ def run_sector(args):
             "status": rc, "status_flags": status, "sim_time": t,
             "amplitude_in_sector": amp_in, "amplitude_outside": amp_out,
             "gpu_launches": steps, "clocks": getattr(clk, "result", None)}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_special("sector", args, args.cpu_budget)
     print(json.dumps(line), flush=True)
 
 
@@ -610,18 +754,11 @@ def run_driven(args):
     build()
     N = args.n if args.n != 1 << 22 else 1 << 16
     prec = PRECISIONS[args.precision]
-    P = sv.Params(precision=prec, S=0.5, tau0=0.0135)
-    rho0, p0, ev0 = inputs.equilibrium_primitive(P.Ck, P.S)
-    base = inputs.prim_to_cons(P.gamma, np.array([rho0]), [np.array([0.0])], np.array([p0]),
-                               np.array([ev0]))[:, 0]
-    w = 2 * math.pi / 0.1 * math.sqrt(P.gamma)
-    shape = inputs.acoustic_shape(P.gamma)          # rho', u', p', e_nu' of a frozen wave
-    amp = 1e-4 * np.array([shape[0], shape[1], shape[2] / (P.gamma - 1.0) + ev0 * shape[0],
-                           ev0 * shape[0]])
+    prm, U0, base, amp, w, kk = driven_problem(N)
+    P = sv.Params(precision=prec, **prm)
     stream = torch.cuda.Stream()
     s = sv.Solver(P, (N,), (1.0,), stream=stream, bc=(sv.BC_DRIVEN, sv.BC_OUTFLOW))
-    s.set_drive(w, w / math.sqrt(P.gamma), base, amp)
-    U0 = np.repeat(base[:, None], N, axis=1)
+    s.set_drive(w, kk, base, amp)
     s.write_state(U0)
     s.run_to(0.01)
     s.write_state(U0)
@@ -642,6 +779,8 @@ def run_driven(args):
                        "l2": "not flushed: whole run timed"},
             "time_to_solution_s": wall, "gpu_launches": steps, "status": rc,
             "clocks": getattr(clk, "result", None)}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_special("driven", args, args.cpu_budget)
     print(json.dumps(line), flush=True)
 
 
