@@ -138,8 +138,10 @@ int orc_run2m(const orc_params* P, long nx, long ny, double h, const int* bc,
               const orc_medium2* M, double* U, double t0, double t_end, long max_steps,
               double* t_out, long* steps_out);
 
-/* Number of OpenMP threads the array loops use (1 without OpenMP). */
+/* Number of OpenMP threads the array loops use (1 without OpenMP), and a
+   way to change it (timing only: results do not depend on it). */
 int orc_threads(void);
+void orc_set_threads(int n);
 
 #ifdef __cplusplus
 }

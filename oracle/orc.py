@@ -123,6 +123,7 @@ def lib():
         L.orc_run.argtypes = [pp, ctypes.c_int, lp, ctypes.c_double, dp, ctypes.c_double,
                               ctypes.c_double, ctypes.c_long, dp, lp]
         L.orc_threads.restype = ctypes.c_int
+        L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_step_bc1.argtypes = [pp, ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                    ctypes.c_int, dp, dp]
         L.orc_run_bc1.argtypes = [pp, ctypes.c_long, ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -256,6 +257,11 @@ def run(P: Params, U: np.ndarray, n, h: float, t_end: float, t0: float = 0.0,
 
 def threads() -> int:
     return int(lib().orc_threads())
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of the array loops (timing only)."""
+    lib().orc_set_threads(int(n))
 
 
 def step_bc1(P: Params, U: np.ndarray, N: int, h: float, dt: float, bc_lo: int, bc_hi: int):

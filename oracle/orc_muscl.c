@@ -48,6 +48,14 @@ int orc_threads(void) {
 #endif
 }
 
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* eq. 5: E = p/(gamma-1) + rho |v|^2 / 2 + E_nu  ->  p */
 double orc_pressure(const orc_params* P, int dim, const double* u) {
   double rho = u[0];
