@@ -10,7 +10,7 @@ fused kernel).  The state (64 MiB per buffer) fits in L2, so L2 is flushed by a
 events on the solver's stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision fp32|fp64|fp32_p64|fp32_pc] [--n CELLS]
+                  [--precision fp32|fp64|fp32_p64|fp32_pc|fp32_ps] [--n CELLS]
 
 Under torchrun (N > 1) every rank runs an independent replica (the 1D problem
 is not sharded: "replicas only"); value = all ranks' cell-updates / max time.
@@ -42,9 +42,9 @@ L2_FLUSH_BYTES = 256 << 20
 TRAFFIC_1D_FP32_N22 = 86.2e6
 
 # --precision names -> sv_params.precision (SV_FP32, SV_FP64, SV_FP32_P64,
-# SV_FP32_PC of include/sv.h) and the arithmetic type reported as "dtype"
-PRECISIONS = {"fp32": 0, "fp64": 1, "fp32_p64": 2, "fp32_pc": 3}
-DTYPES = {"fp32": "f32", "fp64": "f64", "fp32_p64": "f32", "fp32_pc": "f32"}
+# SV_FP32_PC, SV_FP32_PS of include/sv.h) and the arithmetic type reported as "dtype"
+PRECISIONS = {"fp32": 0, "fp64": 1, "fp32_p64": 2, "fp32_pc": 3, "fp32_ps": 4}
+DTYPES = {"fp32": "f32", "fp64": "f64", "fp32_p64": "f32", "fp32_pc": "f32", "fp32_ps": "f32"}
 
 
 def workload(n_cells: int, gamma: float, Ck: float, S: float):
@@ -803,7 +803,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_p64", "fp32_pc"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_p64", "fp32_pc", "fp32_ps"])
     ap.add_argument("--n", type=int, default=1 << 22, help="cells of the 1d workload")
     ap.add_argument("--workload", default="1d",
                     choices=sorted(WORKLOADS) + ["sweep", "wc", "driven", "sector"])

@@ -74,6 +74,11 @@ extern "C" {
                            the exact E - rho v^2/2 - E_nu of the float operands (two
                            error-free float sums), times gamma - 1, rounded once; the
                            same p as SV_FP32_P64 to within its last bit, at float speed */
+#define SV_FP32_PS  4   /* 1D MUSCL-Hancock only: float perturbations about the uniform
+                           equilibrium (rho = p = 1, v = 0, E_nu = C_k + S) on the device, the
+                           fluxes and the source Y written so that the equilibrium part cancels
+                           exactly; host I/O stays full double states.  Float rounding then
+                           scales with the perturbation instead of the O(1) background */
 
 /* ---- time integration */
 #define SV_HANCOCK  0   /* MUSCL-Hancock: half-step predictor + corrector (eqs. 14-15) */
@@ -92,7 +97,7 @@ typedef struct {
   double cfl;                   /* factor on the eq. 16 bound, e.g. 0.4 */
   double c_tau;                 /* dt <= c_tau * min tau (explicit source), e.g. 0.5 */
   int limiter;                  /* SV_MINMOD, SV_VANLEER, SV_MC */
-  int precision;                /* SV_FP32, SV_FP64, SV_FP32_P64, SV_FP32_PC */
+  int precision;                /* SV_FP32, SV_FP64, SV_FP32_P64, SV_FP32_PC, SV_FP32_PS */
   int method;                   /* SV_HANCOCK (0) or SV_HEUN */
 } sv_params;
 

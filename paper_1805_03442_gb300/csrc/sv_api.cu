@@ -80,7 +80,9 @@ int check_inputs(const sv_params* p, const sv_grid* g) {
   if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->c_tau > 0.0) || !(p->tau0 > 0.0))
     return SV_EINVAL;
   if (p->limiter < SV_MINMOD || p->limiter > SV_MC) return SV_EINVAL;
-  if (p->precision < SV_FP32 || p->precision > SV_FP32_PC) return SV_EINVAL;
+  if (p->precision < SV_FP32 || p->precision > SV_FP32_PS) return SV_EINVAL;
+  // the perturbation layout: 1D MUSCL-Hancock
+  if (p->precision == SV_FP32_PS && (g->dim != 1 || p->method != SV_HANCOCK)) return SV_EINVAL;
   for (int side = 0; side < 2; ++side)
     if (g->bc[side] < SV_BC_PERIODIC || g->bc[side] > SV_BC_DRIVEN) return SV_EINVAL;
   if (g->bc[1] == SV_BC_DRIVEN) return SV_EINVAL;
@@ -308,6 +310,7 @@ int sv_init(const sv_params* p, const sv_grid* g, void* cuda_stream, void* devic
   k.gamma = p->gamma;
   k.g1 = p->gamma - 1.0;
   k.Ck = p->Ck;
+  k.S = p->S;
   k.frozen = isinf(p->tau0) ? 1 : 0;
   k.tau0 = p->tau0;
   k.inv_tau0 = k.frozen ? 0.0 : 1.0 / p->tau0;
@@ -408,7 +411,7 @@ int sv_write_state(sv_solver* s, const double* host_soa, double t) {
   }
   SV_TRY(ctl_reset_launch(s->ctl, t, s->stream));
   SV_TRY(to_state_launch(s->p.precision, src, s->buf[0], s->buf[1], s->ctl, (int64_t)count,
-                         s->stream));
+                         s->stream, s->kp.ref));
   SV_TRY(dt_reduce_launch(s->p.precision, s->dim, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell,
                           s->stream));
   return SV_OK;
@@ -420,7 +423,7 @@ int sv_read_state(sv_solver* s, double* host_soa, double* t) {
   // pinned host memory: the conversion kernel writes it over the host link
   double* dst = (double*)mapped_view(host_soa);
   SV_TRY(from_state_launch(s->p.precision, s->buf[0], s->buf[1], s->ctl, dst ? dst : s->staging,
-                           (int64_t)count, s->stream));
+                           (int64_t)count, s->stream, s->kp.ref));
   if (!dst)
     SV_TRY(cudaMemcpyAsync(host_soa, s->staging, count * sizeof(double), cudaMemcpyDeviceToHost,
                            s->stream));
@@ -512,17 +515,18 @@ int sv_autotune(sv_solver* s, int steps, int* best, double* us_per_step) {
   if (!s || steps < 1) return SV_EINVAL;
   const int ncfg = (int)s->cfgs.size();
   const size_t count = (size_t)s->nf * (size_t)s->ncell;
-  // keep the state (exactly: float -> double -> float is lossless) and the
-  // control block; every trial is undone before the next one
+  // keep the state (a raw copy of the current buffer into the staging area,
+  // which holds count doubles) and the control block; every trial is undone
+  // before the next one
   Ctl saved;
-  SV_TRY(from_state_launch(s->p.precision, s->buf[0], s->buf[1], s->ctl, s->staging,
-                           (int64_t)count, s->stream));
+  const int64_t state_bytes = (int64_t)count * s->esize;
+  SV_TRY(raw_state_launch(s->buf[0], s->buf[1], s->ctl, s->staging, state_bytes, true, s->stream));
   SV_TRY(cudaMemcpyAsync(&saved, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
   SV_TRY(cudaStreamSynchronize(s->stream));
   auto restore = [&]() -> int {
     SV_TRY(cudaMemcpyAsync(s->ctl, &saved, sizeof(Ctl), cudaMemcpyHostToDevice, s->stream));
-    SV_TRY(to_state_launch(s->p.precision, s->staging, s->buf[0], s->buf[1], s->ctl,
-                           (int64_t)count, s->stream));
+    SV_TRY(raw_state_launch(s->buf[0], s->buf[1], s->ctl, s->staging, state_bytes, false,
+                            s->stream));
     SV_TRY(cudaStreamSynchronize(s->stream));
     return SV_OK;
   };
@@ -659,6 +663,8 @@ int sv_conservation(sv_solver* s, double* sums) {
                          s->stream));
   SV_TRY(cudaStreamSynchronize(s->stream));
   memcpy(sums, s->host_sums, s->nf * sizeof(double));
+  if (s->p.precision == SV_FP32_PS)      // the device holds U - ref
+    for (int f = 0; f < s->nf; ++f) sums[f] += (double)s->ncell * s->kp.ref[f];
   return SV_OK;
 }
 

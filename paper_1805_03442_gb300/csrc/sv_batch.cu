@@ -36,6 +36,7 @@ struct sv_batch {
   int64_t nruns = 0;
   int log_cap = 0;
   int esize = 4;
+  bool ps = false;                    // perturbation layout (SV_FP32_PS)
   cudaStream_t stream = nullptr, cap_stream = nullptr;
   void* mem = nullptr;
   bool owns_mem = false;
@@ -70,7 +71,7 @@ int check_batch(const sv_params* p, const sv_run* r, int64_t nruns, int log_cap)
   if (!p || !r || nruns < 1 || nruns > (1 << 30) || log_cap < 0) return SV_EINVAL;
   if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->c_tau > 0.0)) return SV_EINVAL;
   if (p->limiter < SV_MINMOD || p->limiter > SV_MC) return SV_EINVAL;
-  if (p->precision < SV_FP32 || p->precision > SV_FP32_PC) return SV_EINVAL;
+  if (p->precision < SV_FP32 || p->precision > SV_FP32_PS) return SV_EINVAL;
   if (p->method != SV_HANCOCK) return SV_EINVAL;
   for (int64_t i = 0; i < nruns; ++i) {
     if (r[i].n < 1 || r[i].n > (1 << 24) || !(r[i].L > 0.0) || !(r[i].tau0 > 0.0) ||
@@ -107,9 +108,11 @@ int upload(sv_batch* b, const double* host) {
   int64_t src = 0;
   for (int64_t i = 0; i < b->nruns; ++i) {
     const int64_t n = b->n[i], st = stride_of(n), off = b->host_runs[i].off;
+    const double* ref = b->host_runs[i].kp.ref;
     for (int f = 0; f < 4; ++f)
       for (int64_t j = 0; j < n; ++j) {
-        const double v = host[src + f * n + j];
+        // the perturbation layout holds U - ref (difference in double)
+        const double v = host[src + f * n + j] - (b->ps ? ref[f] : 0.0);
         const size_t at = (size_t)(off + f * st + j);
         if (es == 8) memcpy(&tmp[at * 8], &v, 8);
         else {
@@ -223,6 +226,7 @@ int sv_batch_init(const sv_params* p, const sv_run* runs, int64_t nruns,
   b->nruns = nruns;
   b->log_cap = log_cap;
   b->esize = p->precision == SV_FP64 ? 8 : 4;
+  b->ps = p->precision == SV_FP32_PS;
   b->stream = (cudaStream_t)cuda_stream;
   b->max_steps = max_steps_per_run;
   b->host_runs.resize((size_t)nruns);
@@ -236,6 +240,7 @@ int sv_batch_init(const sv_params* p, const sv_run* runs, int64_t nruns,
     k.gamma = p->gamma;
     k.g1 = p->gamma - 1.0;
     k.Ck = p->Ck;
+    k.S = r.S;
     k.frozen = isinf(r.tau0) ? 1 : 0;
     k.tau0 = r.tau0;
     k.inv_tau0 = k.frozen ? 0.0 : 1.0 / r.tau0;
@@ -359,7 +364,7 @@ int sv_batch_read(sv_batch* b, int64_t run, double* host_soa, double* t, int64_t
         else {
           float fv;
           memcpy(&fv, &tmp[at * 4], 4);
-          host_soa[f * n + j] = fv;
+          host_soa[f * n + j] = (b->ps ? d.kp.ref[f] : 0.0) + (double)fv;
         }
       }
   }

@@ -104,7 +104,7 @@ batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns
     auto log_mode = [&](const R* U, double t, int slot) {
       R re = 0, im = 0;
       for (int j = threadIdx.x; j < n; j += NTB) {
-        const R v = U[stride + j] / U[j];
+        const R v = U[stride + j] / (PP == 3 ? (R)1 + U[j] : U[j]);   // PP 3: perturbations
         R sn, cs;
         const R ph = (R)(2.0 * mode) * ((R)j + (R)0.5) / (R)n;
         if constexpr (sizeof(R) == 4) sincospif(ph, &sn, &cs);
@@ -126,11 +126,8 @@ batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns
       R smax = 0, akey = -INFINITY;
       uint32_t flags = 0;
       for (int j = threadIdx.x; j < n; j += NTB) {
-        const R rho = A[j], m = A[stride + j];
-        const R ir = Ar<R>::rcp(rho);
-        const R v = m * ir;
-        cfl_cell<R, PP, 1>(k, rho, m * v, fabs(m * ir), A[2 * stride + j], A[3 * stride + j], smax,
-                           akey, flags);
+        const R u[4] = {A[j], A[stride + j], A[2 * stride + j], A[3 * stride + j]};
+        cell_bound<R, PP, 1>(k, u, smax, akey, flags);
       }
       block_max<NTB>(smax, akey, flags, s_a, s_b, s_f);
       if (threadIdx.x == 0) {
@@ -233,6 +230,7 @@ void* bpick_prec(int precision) {
     case PREC_FP64: return (void*)KB<NTB, double, 0, LIM>::fn;
     case PREC_FP32_P64: return (void*)KB<NTB, float, 1, LIM>::fn;
     case PREC_FP32_PC: return (void*)KB<NTB, float, 2, LIM>::fn;
+    case PREC_FP32_PS: return (void*)KB<NTB, float, 3, LIM>::fn;
     default: return (void*)KB<NTB, float, 0, LIM>::fn;
   }
 }

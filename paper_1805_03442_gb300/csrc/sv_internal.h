@@ -10,7 +10,7 @@ namespace sv {
 struct KParams;
 struct Ctl;
 
-enum { PREC_FP32 = 0, PREC_FP64 = 1, PREC_FP32_P64 = 2, PREC_FP32_PC = 3 };
+enum { PREC_FP32 = 0, PREC_FP64 = 1, PREC_FP32_P64 = 2, PREC_FP32_PC = 3, PREC_FP32_PS = 4 };
 
 // 1D fused step (sv_step1d.cu)
 int step1d_grid(const KParams& kp, int precision);
@@ -58,10 +58,16 @@ cudaError_t dt_reduce_launch(int precision, int dim, const KParams& kp, const vo
                              const void* b, Ctl* ctl, int64_t ncell, cudaStream_t st);
 cudaError_t set_target_launch(int precision, Ctl* ctl, double t_end, const KParams& kp,
                               cudaStream_t st);
+// Host-format (double, full state) <-> device state; `ref` (4 values) is the
+// reference state the perturbation layout PREC_FP32_PS subtracts, unused otherwise.
 cudaError_t to_state_launch(int precision, const double* src, void* a, void* b, Ctl* ctl,
-                            int64_t count, cudaStream_t st);
+                            int64_t count, cudaStream_t st, const double* ref = nullptr);
 cudaError_t from_state_launch(int precision, const void* a, const void* b, const Ctl* ctl,
-                              double* dst, int64_t count, cudaStream_t st);
+                              double* dst, int64_t count, cudaStream_t st,
+                              const double* ref = nullptr);
+// Exact copy of the current state buffer's `bytes` to (save) or from `other`.
+cudaError_t raw_state_launch(void* a, void* b, const Ctl* ctl, void* other, int64_t bytes,
+                             bool save, cudaStream_t st);
 cudaError_t sums_launch(int precision, const void* a, const void* b, const Ctl* ctl, int nf,
                         int64_t ncell, double* partial, int nblocks, double* out,
                         cudaStream_t st);

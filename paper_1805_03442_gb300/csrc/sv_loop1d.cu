@@ -117,6 +117,7 @@ void* pick_prec(int precision) {
     case PREC_FP64: return (void*)KL<double, 0, LIM, SRC>::fn;
     case PREC_FP32_P64: return (void*)KL<float, 1, LIM, SRC>::fn;
     case PREC_FP32_PC: return (void*)KL<float, 2, LIM, SRC>::fn;
+    case PREC_FP32_PS: return (void*)KL<float, 3, LIM, SRC>::fn;
     default: return (void*)KL<float, 0, LIM, SRC>::fn;
   }
 }

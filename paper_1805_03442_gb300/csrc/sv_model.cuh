@@ -53,6 +53,12 @@ struct KParams {
   // float constants of the dt rule of the float solvers: cfl h, 1/h, 1/(2h),
   // c_tau tau0 (0 in the frozen limit)
   float fdt[4];
+  // degree of non-equilibrium S, and the uniform equilibrium rho = p = T = 1,
+  // v = 0, E_nu = C_k + S that the perturbation layout (SV_FP32_PS) subtracts:
+  // ref = (rho, rho v, E, E_nu); fps = (E + p, E_nu, S) of it in float
+  double S;
+  double ref[4];
+  float fps[4];
 };
 
 // Fill the float copies once on the host, so float kernels convert nothing.
@@ -68,6 +74,15 @@ inline void kparams_finish(KParams& k) {
   k.fdt[1] = (float)(1.0 / k.h);
   k.fdt[2] = (float)(0.5 / k.h);
   k.fdt[3] = k.frozen ? 0.0f : (float)(k.c_tau * k.tau0);
+  const double ev0 = k.Ck + k.S;
+  k.ref[0] = 1.0;
+  k.ref[1] = 0.0;
+  k.ref[2] = 1.0 / k.g1 + ev0;
+  k.ref[3] = ev0;
+  k.fps[0] = (float)(k.ref[2] + 1.0);
+  k.fps[1] = (float)ev0;
+  k.fps[2] = (float)k.S;
+  k.fps[3] = 0.0f;
 }
 
 // Device control block: time, step size and the reductions of one solver.
@@ -152,11 +167,13 @@ template <> struct P<float> {
   float tau_rho, tau_T, Q_rho, Q_T, I_rho, I_T;
   float l2_inv_tau0, ntau_rho, ntau_T;   // log2(1/tau0), -tau_rho, -tau_T
   float g1lo;                            // g1 - (float)g1
+  float h0, ev0, S;                      // perturbation layout: E + p, E_nu, S of the reference
   int limiter, frozen, qi_zero, bc_lo, bc_hi;
   __device__ __forceinline__ explicit P(const KParams& k)
       : gamma(k.f[0]), g1(k.f[1]), Ck(k.f[2]), Q0(k.f[3]), inv_tau0(k.f[5]), tau0(k.f[4]),
         tau_rho(k.f[6]), tau_T(k.f[7]), Q_rho(k.f[8]), Q_T(k.f[9]), I_rho(k.f[10]),
         I_T(k.f[11]), l2_inv_tau0(k.f[12]), ntau_rho(k.f[13]), ntau_T(k.f[14]), g1lo(k.f[15]),
+        h0(k.fps[0]), ev0(k.fps[1]), S(k.fps[2]),
         limiter(k.limiter), frozen(k.frozen), qi_zero(k.qi_zero), bc_lo(k.bc_lo),
         bc_hi(k.bc_hi) {}
 };

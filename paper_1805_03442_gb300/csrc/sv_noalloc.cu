@@ -58,7 +58,7 @@ extern "C" int sv_step1d_noalloc(const sv_params* p, int64_t n, double L, const 
   if (n < 1 || !(L > 0.0)) return SV_EINVAL;
   if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->c_tau > 0.0) || !(p->tau0 > 0.0) ||
       p->limiter < SV_MINMOD || p->limiter > SV_MC || p->precision < SV_FP32 ||
-      p->precision > SV_FP32_PC || p->method != SV_HANCOCK)
+      p->precision > SV_FP32_PC || p->method != SV_HANCOCK)   // not the perturbation layout
     return SV_EINVAL;
   void* scratch = nullptr;
   int rc = scratch_address(&scratch);
@@ -71,6 +71,7 @@ extern "C" int sv_step1d_noalloc(const sv_params* p, int64_t n, double L, const 
   k.gamma = p->gamma;
   k.g1 = p->gamma - 1.0;
   k.Ck = p->Ck;
+  k.S = p->S;
   k.frozen = isinf(p->tau0) ? 1 : 0;
   k.tau0 = p->tau0;
   k.inv_tau0 = k.frozen ? 0.0 : 1.0 / p->tau0;

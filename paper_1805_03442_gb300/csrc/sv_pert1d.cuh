@@ -1,0 +1,175 @@
+// sv_pert1d.cuh -- the float 1D MUSCL-Hancock arithmetic on perturbations
+// about the uniform equilibrium (precision SV_FP32_PS): Sec. 2.3, eq. 14
+// reconstruction with xi = 0, half-step predictor, eq. 13 HLL, eq. 15 update,
+// the source Y of eqs. 4 and 6, and the eq. 16 bound.
+//
+// The device holds u = U - U_ref with U_ref = (1, 0, E0, E_nu0) the
+// equilibrium rho = p = T = 1, v = 0, E_nu0 = C_k + S (R = 1; E0 = 1/(gamma-1)
+// + E_nu0).  A float state of the full fields is rounded at ~6e-8 of the O(1)
+// background every step; here the rounding scales with the perturbation.  Every
+// quantity the step needs is formed so that the equilibrium part cancels
+// algebraically before any rounding:
+//   p - 1           = (gamma - 1)((dE - dE_nu) - rho v^2 / 2)
+//   flux - F(U_ref) = (m, rho v^2 + (p - 1), v (E0 + p0 + dE + (p - 1)), v (E_nu0 + dE_nu))
+//                     (the constant F(U_ref) = (0, 1, 0, 0) cancels in flux
+//                     differences and passes through HLL, whose weights sum to 1)
+//   rho C_k T - E_nu + rho Q tau = C_k (p - 1) - dE_nu + S expm1(a ln rho + b ln T),
+//                     a = 1 + Q_rho + tau_rho, b = Q_T + tau_T (rho Q tau = S rho^a T^b
+//                     with Q0 tau0 = S), so Y_Enu = (that) / tau
+//   rho (Q - I)     = rho Q0 (expm1(Q_rho ln rho + Q_T ln T) - expm1(I_rho ln rho + I_T ln T))
+// with ln rho = log1p(d rho) and ln T = log1p((dp - d rho) / rho).  Only rates
+// (1/tau, the sound speed, 1/rho) are formed from full values: they multiply
+// perturbation-sized quantities, so their relative rounding stays relative.
+#pragma once
+
+#include "sv_model.cuh"
+#include "sv_reduce.cuh"
+
+namespace sv {
+namespace ps {
+
+struct Prim {
+  float rho, ir, v, kin2, dp, p;
+};
+
+__device__ __forceinline__ Prim prim(const P<float>& k, const float (&u)[4]) {
+  Prim q;
+  q.rho = 1.0f + u[0];
+  q.ir = Ar<float>::rcp(q.rho);
+  q.v = u[1] * q.ir;
+  q.kin2 = u[1] * q.v;
+  q.dp = k.g1 * fmaf(q.kin2, -0.5f, u[2] - u[3]);
+  q.p = 1.0f + q.dp;
+  return q;
+}
+
+// F(U) - F(U_ref) of eq. 13's flux.
+__device__ __forceinline__ void flux(const P<float>& k, const float (&u)[4], const Prim& q,
+                                     float (&F)[4]) {
+  F[0] = u[1];
+  F[1] = q.kin2 + q.dp;
+  F[2] = q.v * (k.h0 + (u[2] + q.dp));
+  F[3] = q.v * (k.ev0 + u[3]);
+}
+
+// Components E and E_nu of Y at the perturbed state u (SRC as Src<R, SRC>).
+template <int SRC>
+__device__ __forceinline__ void source(const P<float>& k, const float (&u)[4], const Prim& q,
+                                       float& yE, float& yEv) {
+  yE = yEv = 0.0f;
+  if (SRC == 0) return;
+  const float lr = log1pf(u[0]);
+  const float lT = log1pf((q.dp - u[0]) * q.ir);
+  const float inv_tau = k.inv_tau0 * expf(fmaf(k.ntau_rho, lr, k.ntau_T * lT));
+  const float a = 1.0f + k.Q_rho + k.tau_rho, b = k.Q_T + k.tau_T;
+  const float relax = fmaf(k.Ck, q.dp, -u[3]) + k.S * expm1f(fmaf(a, lr, b * lT));
+  yEv = relax * inv_tau;
+  if (SRC == 2)
+    yE = q.rho * k.Q0 *
+         (expm1f(fmaf(k.Q_rho, lr, k.Q_T * lT)) - expm1f(fmaf(k.I_rho, lr, k.I_T * lT)));
+}
+
+// eq. 16 bound and physicality of one perturbed state.
+template <int SRC>
+__device__ __forceinline__ void bound(const P<float>& k, const float (&u)[4], float& smax,
+                                      float& akey, uint32_t& flags) {
+  const Prim q = prim(k, u);
+  if (!((q.rho > 0.0f) && (q.p > 0.0f))) {
+    flags |= FLAG_NONPHYS;
+    return;
+  }
+  const float vmag = fabsf(q.v);
+  const float c = Ar<float>::sqrt_pos(k.gamma * q.p * q.ir);
+  smax = fmaxf(smax, fmaxf(2.0f * vmag, vmag + c));
+  if (SRC != 0) akey = fmaxf(akey, TauKey<float>::of(k, q.rho, q.p * q.ir));
+}
+
+// Slopes, positivity guard, predictor and face states of one cell (as the
+// full-state predict() of sv_step1d.cuh).
+template <int LIM, int SRC>
+__device__ __forceinline__ void predict(const P<float>& k, const float (&u)[4],
+                                        const float (&um)[4], const float (&up)[4], float dt_2h,
+                                        float dt_2, float (&wp)[4], float (&wm)[4], float& yEh,
+                                        float& yEvh) {
+  float d[4], a[4], b[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    d[f] = limit<LIM, float>(u[f] - um[f], up[f] - u[f]);
+    a[f] = u[f] + 0.5f * d[f];
+    b[f] = u[f] - 0.5f * d[f];
+  }
+  const Prim qa = prim(k, a), qb = prim(k, b);
+  float Fa[4], Fb[4], dF[4];
+  flux(k, a, qa, Fa);
+  flux(k, b, qb, Fb);
+#pragma unroll
+  for (int f = 0; f < 4; ++f) dF[f] = Fa[f] - Fb[f];
+  if (!(fminf(fminf(qa.rho, qa.p), fminf(qb.rho, qb.p)) > 0.0f)) {
+#pragma unroll
+    for (int f = 0; f < 4; ++f) d[f] = dF[f] = 0.0f;
+  }
+  float yE = 0.0f, yEv = 0.0f;
+  if (SRC != 0) source<SRC>(k, u, prim(k, u), yE, yEv);
+  float uh[4];
+  uh[0] = u[0] - dt_2h * dF[0];
+  uh[1] = u[1] - dt_2h * dF[1];
+  uh[2] = u[2] - dt_2h * dF[2] + dt_2 * yE;
+  uh[3] = u[3] - dt_2h * dF[3] + dt_2 * yEv;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    wp[f] = uh[f] + 0.5f * d[f];
+    wm[f] = uh[f] - 0.5f * d[f];
+  }
+  yEh = yEvh = 0.0f;
+  if (SRC != 0) source<SRC>(k, uh, prim(k, uh), yEh, yEvh);
+}
+
+// eq. 13 at one face (as hll() of sv_step1d.cuh), on perturbed states and
+// the reduced fluxes.
+__device__ __forceinline__ void hll(const P<float>& k, const float (&l)[4], const float (&r)[4],
+                                    const float (&fl)[4], const float (&fr)[4], float (&F)[4]) {
+  float L[4], Rr[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    L[f] = l[f];
+    Rr[f] = r[f];
+  }
+  Prim qL = prim(k, L), qR = prim(k, Rr);
+  if (!(fminf(fminf(qL.rho, qL.p), fminf(qR.rho, qR.p)) > 0.0f)) {
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      L[f] = fl[f];
+      Rr[f] = fr[f];
+    }
+    qL = prim(k, L);
+    qR = prim(k, Rr);
+  }
+  const float cL = Ar<float>::sqrt_pos(k.gamma * qL.p * qL.ir);
+  const float cR = Ar<float>::sqrt_pos(k.gamma * qR.p * qR.ir);
+  const float sl = fminf(fminf(qL.v - cL, qR.v - cR), 0.0f);
+  const float sr = fmaxf(fmaxf(qL.v + cL, qR.v + cR), 0.0f);
+  float FL[4], FR[4];
+  flux(k, L, qL, FL);
+  flux(k, Rr, qR, FR);
+  const float inv = Ar<float>::rcp(sr - sl);
+  const float wl = sr * inv, wr = -sl * inv, wd = sl * sr * inv;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) F[f] = wl * FL[f] + wr * FR[f] + wd * (Rr[f] - L[f]);
+}
+
+}  // namespace ps
+
+// eq. 16 bound of one 1D cell state u (rho, rho v, E, E_nu), or of its
+// perturbation (PP = 3), folded into the caller's maxima.
+template <typename R, int PP, int SRC>
+__device__ __forceinline__ void cell_bound(const P<R>& k, const R (&u)[4], R& smax, R& akey,
+                                           uint32_t& flags) {
+  if constexpr (PP == 3) {
+    ps::bound<SRC>(k, u, smax, akey, flags);
+  } else {
+    const R v = u[1] * Ar<R>::rcp(u[0]);
+    cfl_cell<R, PP, SRC>(k, u[0], u[1] * v, fabs(v), u[2], u[3], smax, akey, flags);
+  }
+}
+
+}  // namespace sv

@@ -58,6 +58,7 @@ static void* pick_prec(int precision) {
     case PREC_FP64: return (void*)K1<double, 0, LIM, SRC>::fn;
     case PREC_FP32_P64: return (void*)K1<float, 1, LIM, SRC>::fn;
     case PREC_FP32_PC: return (void*)K1<float, 2, LIM, SRC>::fn;
+    case PREC_FP32_PS: return (void*)K1<float, 3, LIM, SRC>::fn;
     default: return (void*)K1<float, 0, LIM, SRC>::fn;
   }
 }

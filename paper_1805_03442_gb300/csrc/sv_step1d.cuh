@@ -28,6 +28,7 @@
 #include <type_traits>
 
 #include "sv_pair1d.cuh"
+#include "sv_pert1d.cuh"
 #include "sv_reduce.cuh"
 
 namespace sv {
@@ -74,6 +75,10 @@ template <typename R, int PP, int LIM, int SRC>
 __device__ __forceinline__ void predict(const P<R>& k, const R (&u)[4], const R (&um)[4],
                                         const R (&up)[4], R dt_2h, R dt_2, R (&wp)[4], R (&wm)[4],
                                         R& yEh, R& yEvh) {
+  if constexpr (PP == 3) {          // perturbation layout (sv_pert1d.cuh)
+    ps::predict<LIM, SRC>(k, u, um, up, dt_2h, dt_2, wp, wm, yEh, yEvh);
+    return;
+  }
   R d[4], a[4], b[4];
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
@@ -156,6 +161,10 @@ __device__ __forceinline__ void level_states(const P<R>& k, const R (&u)[4], con
 template <typename R, int PP>
 __device__ __forceinline__ void hll(const P<R>& k, const R (&l)[4], const R (&r)[4],
                                     const R (&fl)[4], const R (&fr)[4], R (&F)[4]) {
+  if constexpr (PP == 3) {
+    ps::hll(k, l, r, fl, fr, F);
+    return;
+  }
   R L[4], Rr[4];
 #pragma unroll
   for (int f = 0; f < 4; ++f) { L[f] = l[f]; Rr[f] = r[f]; }
@@ -213,10 +222,7 @@ __device__ __forceinline__ void update_cell(const P<R>& k, const R (&u)[4], cons
   un[1] = u[1] - dtdx * (Fr[1] - Fl[1]);
   un[2] = u[2] - dtdx * (Fr[2] - Fl[2]) + dt * yE;
   un[3] = u[3] - dtdx * (Fr[3] - Fl[3]) + dt * yEv;
-  if (CFL) {
-    const R v = un[1] * Ar<R>::rcp(un[0]);
-    cfl_cell<R, PP, SRC>(k, un[0], un[1] * v, fabs(v), un[2], un[3], smax, akey, flags);
-  }
+  if (CFL) cell_bound<R, PP, SRC>(k, un, smax, akey, flags);
 }
 
 // State of the driven boundary's ghost cell centred at x at time t (double).
@@ -268,7 +274,7 @@ __device__ __forceinline__ void step1d_warp(const P<R>& k, const R* __restrict__
             double u[4];
             drive_state(kp, ((double)(j + e) + 0.5) * kp.h, t, u);
 #pragma unroll
-            for (int f = 0; f < 4; ++f) dst[f * RN + e] = (R)u[f];
+            for (int f = 0; f < 4; ++f) dst[f * RN + e] = (R)(PP == 3 ? u[f] - kp.ref[f] : u[f]);
           } else {
             bool fl;
             const int i = bc_index(j + e, N, k.bc_lo, k.bc_hi, fl);

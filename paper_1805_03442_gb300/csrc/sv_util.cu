@@ -3,6 +3,7 @@
 // conversion and the compensated conservation sums.
 #include "sv_internal.h"
 #include "sv_reduce.cuh"
+#include "sv_pert1d.cuh"
 
 namespace sv {
 
@@ -63,6 +64,15 @@ __global__ void __launch_bounds__(NTU) dt_reduce_kernel(const KParams kp, const 
   const P<R> k(kp);
   R smax = 0, akey = -INFINITY;
   uint32_t flags = 0;
+  if constexpr (PP == 3) {        // 1D perturbation layout
+    for (int64_t i = (int64_t)blockIdx.x * NTU + threadIdx.x; i < ncell;
+         i += (int64_t)gridDim.x * NTU) {
+      const R u[4] = {U[i], U[ncell + i], U[2 * ncell + i], U[3 * ncell + i]};
+      cell_bound<R, 3, 1>(k, u, smax, akey, flags);
+    }
+    reduce_and_finalize<R, NTU>(ctl, kp, smax, akey, flags, false);
+    return;
+  }
   for (int64_t i = (int64_t)blockIdx.x * NTU + threadIdx.x; i < ncell;
        i += (int64_t)gridDim.x * NTU) {
     const R rho = U[i];
@@ -103,6 +113,10 @@ cudaError_t dt_reduce_launch(int precision, int dim, const KParams& kp, const vo
       break;
     case PREC_FP32_PC:
       dt_reduce_kernel<float, 2><<<g, NTU, 0, st>>>(kp, (const float*)a, (const float*)b, ctl,
+                                                    dim, ncell);
+      break;
+    case PREC_FP32_PS:
+      dt_reduce_kernel<float, 3><<<g, NTU, 0, st>>>(kp, (const float*)a, (const float*)b, ctl,
                                                     dim, ncell);
       break;
     default:
@@ -158,9 +172,56 @@ __global__ void from_state_kernel(const R* a, const R* b, const Ctl* ctl, double
   }
 }
 
+// The perturbation layout (SV_FP32_PS): element i of field f = i / ncell holds
+// (float)(U - ref[f]) (the difference taken in double).
+struct Ref4 {
+  double v[4];
+};
+
+__global__ void to_state_ps_kernel(const double* src, float* a, float* b, const Ctl* ctl,
+                                   int64_t ncell, Ref4 ref) {
+  float* U = vload(&ctl->cur) ? b : a;
+  for (int64_t i = (int64_t)blockIdx.x * NTU + threadIdx.x; i < 4 * ncell;
+       i += (int64_t)gridDim.x * NTU)
+    U[i] = (float)(src[i] - ref.v[i / ncell]);
+}
+
+__global__ void from_state_ps_kernel(const float* a, const float* b, const Ctl* ctl, double* dst,
+                                     int64_t ncell, Ref4 ref) {
+  const float* U = vload(&ctl->cur) ? b : a;
+  for (int64_t i = (int64_t)blockIdx.x * NTU + threadIdx.x; i < 4 * ncell;
+       i += (int64_t)gridDim.x * NTU)
+    dst[i] = ref.v[i / ncell] + (double)U[i];
+}
+
+// Raw copies of the current state buffer (`words` 4-byte words) to / from
+// `other` (the autotuner's exact save and restore).
+__global__ void raw_state_kernel(uint32_t* a, uint32_t* b, const Ctl* ctl, uint32_t* other,
+                                 int64_t words, bool save) {
+  uint32_t* U = vload(&ctl->cur) ? b : a;
+  for (int64_t i = (int64_t)blockIdx.x * NTU + threadIdx.x; i < words;
+       i += (int64_t)gridDim.x * NTU) {
+    if (save) other[i] = U[i];
+    else U[i] = other[i];
+  }
+}
+
+cudaError_t raw_state_launch(void* a, void* b, const Ctl* ctl, void* other, int64_t bytes,
+                             bool save, cudaStream_t st) {
+  const int64_t words = bytes / 4;
+  raw_state_kernel<<<grid_small(words), NTU, 0, st>>>((uint32_t*)a, (uint32_t*)b, ctl,
+                                                      (uint32_t*)other, words, save);
+  return cudaGetLastError();
+}
+
 cudaError_t to_state_launch(int precision, const double* src, void* a, void* b, Ctl* ctl,
-                            int64_t count, cudaStream_t st) {
+                            int64_t count, cudaStream_t st, const double* ref) {
   const int g = grid_small(count);
+  if (precision == PREC_FP32_PS) {
+    Ref4 r{{ref[0], ref[1], ref[2], ref[3]}};
+    to_state_ps_kernel<<<g, NTU, 0, st>>>(src, (float*)a, (float*)b, ctl, count / 4, r);
+    return cudaGetLastError();
+  }
   if (precision == PREC_FP64)
     to_state_kernel<double><<<g, NTU, 0, st>>>(src, (double*)a, (double*)b, ctl, count);
   else
@@ -169,8 +230,14 @@ cudaError_t to_state_launch(int precision, const double* src, void* a, void* b, 
 }
 
 cudaError_t from_state_launch(int precision, const void* a, const void* b, const Ctl* ctl,
-                              double* dst, int64_t count, cudaStream_t st) {
+                              double* dst, int64_t count, cudaStream_t st, const double* ref) {
   const int g = grid_small(count);
+  if (precision == PREC_FP32_PS) {
+    Ref4 r{{ref[0], ref[1], ref[2], ref[3]}};
+    from_state_ps_kernel<<<g, NTU, 0, st>>>((const float*)a, (const float*)b, ctl, dst, count / 4,
+                                            r);
+    return cudaGetLastError();
+  }
   if (precision == PREC_FP64)
     from_state_kernel<double><<<g, NTU, 0, st>>>((const double*)a, (const double*)b, ctl, dst,
                                                  count);
@@ -197,6 +264,8 @@ __global__ void fill_equilibrium_kernel(R* a, int nf, int64_t ncell, double gamm
 cudaError_t fill_equilibrium_launch(int precision, void* a, int nf, int64_t ncell, double gamma,
                                     double ev0, cudaStream_t st) {
   const int g = grid_small((int64_t)nf * ncell);
+  if (precision == PREC_FP32_PS)      // the equilibrium is the layout's reference: all zero
+    return cudaMemsetAsync(a, 0, sizeof(float) * (size_t)nf * (size_t)ncell, st);
   if (precision == PREC_FP64)
     fill_equilibrium_kernel<double><<<g, NTU, 0, st>>>((double*)a, nf, ncell, gamma, ev0);
   else

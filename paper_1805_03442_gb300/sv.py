@@ -23,7 +23,7 @@ NOALLOC_MAX_CELLS = (1 << 29) - 1
 FLAG_NONPHYS, FLAG_DT, FLAG_MAXSTEPS, FLAG_STALL = 1, 2, 4, 8
 LAUNCH_AUTO, LAUNCH_PER_STEP, LAUNCH_PERSISTENT = 0, 1, 2
 MINMOD, VANLEER, MC = 0, 1, 2
-FP32, FP64, FP32_P64, FP32_PC = 0, 1, 2, 3
+FP32, FP64, FP32_P64, FP32_PC, FP32_PS = 0, 1, 2, 3, 4
 BC_PERIODIC, BC_REFLECT, BC_OUTFLOW, BC_DRIVEN = 0, 1, 2, 3
 HANCOCK, HEUN = 0, 1
 

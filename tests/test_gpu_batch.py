@@ -68,7 +68,7 @@ def _single(sv, prec, run, U0):
     return U, t, k, flags
 
 
-@pytest.mark.parametrize("prec", ["FP32", "FP64", "FP32_PC"])
+@pytest.mark.parametrize("prec", ["FP32", "FP64", "FP32_PC", "FP32_PS"])
 def test_batch_equals_looped_single_runs(sv, prec):
     runs, states = _mini_sweep(3, 40)
     P = sv.Params(precision=getattr(sv, prec))

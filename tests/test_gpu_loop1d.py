@@ -48,7 +48,7 @@ def assert_same(a, b):
     assert a[1:] == b[1:]
 
 
-@pytest.mark.parametrize("prec", ["FP32", "FP64", "FP32_P64", "FP32_PC"])
+@pytest.mark.parametrize("prec", ["FP32", "FP64", "FP32_P64", "FP32_PC", "FP32_PS"])
 @pytest.mark.parametrize("N", [1, 63, 200, 1601, 4099, 100000])
 def test_bitwise_equal_to_per_step(sv, prec, N):
     P = sv.Params(precision=getattr(sv, prec))
