@@ -17,7 +17,7 @@
 //                     a = 1 + Q_rho + tau_rho, b = Q_T + tau_T (rho Q tau = S rho^a T^b
 //                     with Q0 tau0 = S), so Y_Enu = (that) / tau
 //   rho (Q - I)     = rho Q0 (expm1(Q_rho ln rho + Q_T ln T) - expm1(I_rho ln rho + I_T ln T))
-// with ln rho = log1p(d rho) and ln T = log1p((dp - d rho) / rho).  Only rates
+// with ln rho = ln(1 + d rho) and ln T = ln(1 + (dp - d rho) / rho).  Only rates
 // (1/tau, the sound speed, 1/rho) are formed from full values: they multiply
 // perturbation-sized quantities, so their relative rounding stays relative.
 #pragma once
@@ -52,21 +52,52 @@ __device__ __forceinline__ void flux(const P<float>& k, const float (&u)[4], con
   F[3] = q.v * (k.ev0 + u[3]);
 }
 
+// ln(1 + x) and exp(y) - 1 with relative accuracy near 0.  Perturbations of
+// the linear stage are small, so the Mercator series of ln(1 + x) and the
+// exponential series (textbook Taylor coefficients 1/n and 1/n!, Horner form)
+// cover |x| < 1/16 with a truncation below 1e-8 relative (six terms: (1/16)^6
+// / 7 and (1/16)^6 / 7!); larger arguments go to the CUDA math library.
+__device__ __forceinline__ float ln1p(float x) {
+  if (fabsf(x) < 0.0625f) {
+    float s = -1.0f / 6.0f;
+    s = fmaf(s, x, 1.0f / 5.0f);
+    s = fmaf(s, x, -1.0f / 4.0f);
+    s = fmaf(s, x, 1.0f / 3.0f);
+    s = fmaf(s, x, -1.0f / 2.0f);
+    s = fmaf(s, x, 1.0f);
+    return s * x;
+  }
+  return log1pf(x);
+}
+__device__ __forceinline__ float em1(float y) {
+  if (fabsf(y) < 0.0625f) {
+    float s = 1.0f / 720.0f;
+    s = fmaf(s, y, 1.0f / 120.0f);
+    s = fmaf(s, y, 1.0f / 24.0f);
+    s = fmaf(s, y, 1.0f / 6.0f);
+    s = fmaf(s, y, 1.0f / 2.0f);
+    s = fmaf(s, y, 1.0f);
+    return s * y;
+  }
+  return expm1f(y);
+}
+
 // Components E and E_nu of Y at the perturbed state u (SRC as Src<R, SRC>).
 template <int SRC>
 __device__ __forceinline__ void source(const P<float>& k, const float (&u)[4], const Prim& q,
                                        float& yE, float& yEv) {
   yE = yEv = 0.0f;
   if (SRC == 0) return;
-  const float lr = log1pf(u[0]);
-  const float lT = log1pf((q.dp - u[0]) * q.ir);
-  const float inv_tau = k.inv_tau0 * expf(fmaf(k.ntau_rho, lr, k.ntau_T * lT));
+  const float lr = ln1p(u[0]);
+  const float lT = ln1p((q.dp - u[0]) * q.ir);
+  // 1/tau = (1/tau0) rho^-tau_rho T^-tau_T: a rate, so the SFU exp2 suffices
+  const float inv_tau =
+      Ar<float>::ex2(fmaf(1.44269504f, fmaf(k.ntau_rho, lr, k.ntau_T * lT), k.l2_inv_tau0));
   const float a = 1.0f + k.Q_rho + k.tau_rho, b = k.Q_T + k.tau_T;
-  const float relax = fmaf(k.Ck, q.dp, -u[3]) + k.S * expm1f(fmaf(a, lr, b * lT));
+  const float relax = fmaf(k.Ck, q.dp, -u[3]) + k.S * em1(fmaf(a, lr, b * lT));
   yEv = relax * inv_tau;
   if (SRC == 2)
-    yE = q.rho * k.Q0 *
-         (expm1f(fmaf(k.Q_rho, lr, k.Q_T * lT)) - expm1f(fmaf(k.I_rho, lr, k.I_T * lT)));
+    yE = q.rho * k.Q0 * (em1(fmaf(k.Q_rho, lr, k.Q_T * lT)) - em1(fmaf(k.I_rho, lr, k.I_T * lT)));
 }
 
 // eq. 16 bound and physicality of one perturbed state.
