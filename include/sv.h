@@ -232,7 +232,8 @@ int sv_status(sv_solver* s, uint32_t* flags);
 
 /* Device pointer of the current state buffer (nf * ncell elements of the
    solver's precision, field-major), valid until the next step.  For callers
-   that keep data on the device. */
+   that keep data on the device.  Under SV_FP32_PS the buffer holds U - U_ref
+   (U_ref = (1, 0, 1/(gamma-1) + C_k + S, C_k + S)). */
 int sv_state_device(sv_solver* s, void** dev_ptr, int* elem_bytes);
 
 /* Release the solver (waits for its stream). */
