@@ -190,7 +190,9 @@ const char* seg_desc(int seg) {
 void build_configs(sv_solver* s) {
   s->cfgs.clear();
   if (s->dim == 1) {
-    if (s->p.method == SV_HANCOCK && (s->p.precision == SV_FP32 || s->p.precision == SV_FP32_PC) &&
+    if (s->p.method == SV_HANCOCK &&
+        (s->p.precision == SV_FP32 || s->p.precision == SV_FP32_PC ||
+         s->p.precision == SV_FP32_PS) &&
         s->ncell >= kTile1dMinCells) {
       s->cfgs.push_back({CFG_TILE, 13,
                          "1D: 512-cell block tiles, 2 cells per thread, 80 registers, 3 blocks/SM"});

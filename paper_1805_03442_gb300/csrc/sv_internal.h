@@ -18,7 +18,7 @@ cudaError_t step1d_launch(int precision, const KParams& kp, void* a, void* b, Ct
                           int grid, cudaStream_t st);
 
 // Float 1D MUSCL-Hancock step on block tiles (sv_tile1d.cu), grids of at
-// least kTile1dMinCells cells; precision PREC_FP32 or PREC_FP32_PC
+// least kTile1dMinCells cells; precision PREC_FP32, PREC_FP32_PC or PREC_FP32_PS
 constexpr int64_t kTile1dMinCells = 4096;
 // var = 10 * (cell pairs per thread) + (blocks per SM of the register budget):
 // 13, 12 or 22

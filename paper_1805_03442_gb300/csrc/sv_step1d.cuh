@@ -308,12 +308,13 @@ __device__ __forceinline__ void step1d_warp(const P<R>& k, const R* __restrict__
   R Wp1_prev[4] = {0, 0, 0, 0}, Fa_prev[4] = {0, 0, 0, 0}, Fb_prev[4] = {0, 0, 0, 0};
   R y0E_prev = 0, y0Ev_prev = 0, y1E_prev = 0, y1Ev_prev = 0;
   const int src_m = (lane + 31) & 31, src_p = (lane + 1) & 31;
-  // The float MUSCL-Hancock step (float or compensated-float pressure) runs
-  // both cells of a lane in packed f32x2 arithmetic (sv_pair1d.cuh); double,
-  // double-pressure and Heun stay scalar.
-  constexpr bool PACKED = std::is_same<R, float>::value && (PP == 0 || PP == 2) &&
+  // The float MUSCL-Hancock step (float or compensated-float pressure, or the
+  // perturbation layout) runs both cells of a lane in packed f32x2 arithmetic
+  // (sv_pair1d.cuh, sv_pert1d.cuh); double, double-pressure and Heun stay
+  // scalar.
+  constexpr bool PACKED = std::is_same<R, float>::value && (PP == 0 || PP == 2 || PP == 3) &&
                           MODE == MODE_HANCOCK;
-  constexpr int PPK = PP == 2 ? 2 : 0;      // the packed policy (unused when not PACKED)
+  constexpr int PPK = PP == 1 ? 0 : PP;     // the packed policy (unused when not PACKED)
   using pk::f2;
   // carried from chunk to chunk: the odd cell's right face state (its first
   // use, by lane 0 of the warm-up chunk, only needs to be physical), the
@@ -341,10 +342,10 @@ __device__ __forceinline__ void step1d_warp(const P<R>& k, const R* __restrict__
         B[f] = pk::sub(pk::pair(X[f].y, rf[(pos + 2) & MASK]), X[f]);
       }
       f2 WP[4], WM[4], YE, YEv, L[4], F[4];
-      pk::predict<PPK, LIM, SRC>(k, X, A, B, ndt_2h2, dt_22, WP, WM, YE, YEv);
+      pkx::predict<PPK, LIM, SRC>(k, X, A, B, ndt_2h2, dt_22, WP, WM, YE, YEv);
 #pragma unroll
       for (int f = 0; f < 4; ++f) L[f] = pk::pair(shfl(lane == 31 ? Wy_prev[f] : WP[f].y, src_m), WP[f].x);
-      pk::hll<PPK>(k, L, WM, XM, X, F);             // faces 2i - 1/2 and 2i + 1/2
+      pkx::hll<PPK>(k, L, WM, XM, X, F);            // faces 2i - 1/2 and 2i + 1/2
       if (kk > c0) {
         // update of the pair of chunk kk-1: left faces F_prev, right faces
         // (inner face, next lane's left face)
@@ -357,7 +358,7 @@ __device__ __forceinline__ void step1d_warp(const P<R>& k, const R* __restrict__
           f2 Nw[4];
           pk::update<SRC>(Qp, F_prev, FRt, YE_prev, YEv_prev, dt2, ndtdx2, Nw);
           const bool two = jo + 1 < N;
-          pk::cfl<PPK, SRC>(k, Nw, two ? 3 : 1, smax, akey, flags);
+          pkx::cfl<PPK, SRC>(k, Nw, two ? 3 : 1, smax, akey, flags);
           if (two && (stride % 2) == 0) {
 #pragma unroll
             for (int f = 0; f < 4; ++f) *reinterpret_cast<f2*>(Uout + f * stride + jo) = Nw[f];

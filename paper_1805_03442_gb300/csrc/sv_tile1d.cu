@@ -54,7 +54,7 @@ __device__ __forceinline__ void cp16(void* smem, const void* gmem) {
 // of a grid whose fields start on 16-byte boundaries use 16-byte copies; the
 // others go cell by cell through the boundary mapping (periodic wrap, wall
 // mirror, outflow copy, driven ghost state).  Commits one cp.async group.
-template <int SPAN>
+template <int SPAN, int PP>
 __device__ __forceinline__ void load_tile(float (*dst)[SPAN], const float* Uin, int N, int b,
                                           const P<float>& k, const KParams& kp, double t) {
   const int lo = b - 2;
@@ -71,7 +71,7 @@ __device__ __forceinline__ void load_tile(float (*dst)[SPAN], const float* Uin, 
         double u[4];
         drive_state(kp, ((double)j + 0.5) * kp.h, t, u);
 #pragma unroll
-        for (int f = 0; f < 4; ++f) dst[f][e] = (float)u[f];
+        for (int f = 0; f < 4; ++f) dst[f][e] = (float)(PP == 3 ? u[f] - kp.ref[f] : u[f]);
       } else {
         bool flip;
         const int i = bc_index(j, N, k.bc_lo, k.bc_hi, flip);
@@ -113,14 +113,14 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
   uint32_t flags = 0;
 
   int tile = blockIdx.x;
-  if (tile < ntile) load_tile<SPAN>(S.u[0], Uin, N, OUT * tile - 2, k, kp, t);
+  if (tile < ntile) load_tile<SPAN, PP>(S.u[0], Uin, N, OUT * tile - 2, k, kp, t);
   for (int it = 0; tile < ntile; ++it, tile += gridDim.x) {
     const int buf = it & 1;
     const int b = OUT * tile - 2;
     cp_async_wait<0>();
     __syncthreads();                              // tile in place; the other buffer is free
     if (tile + (int)gridDim.x < ntile)
-      load_tile<SPAN>(S.u[buf ^ 1], Uin, N, OUT * (tile + gridDim.x) - 2, k, kp, t);
+      load_tile<SPAN, PP>(S.u[buf ^ 1], Uin, N, OUT * (tile + gridDim.x) - 2, k, kp, t);
 
     // pair p of the thread sits at span offsets 2 + 2 (NPT t + p) and the next
     f2 X[NPT][4], XM[NPT][4], WP[NPT][4], WM[NPT][4], YE[NPT], YEv[NPT];
@@ -136,7 +136,7 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
         A[f] = pk::sub(X[p][f], XM[p][f]);
         B[f] = pk::sub(pk::pair(X[p][f].y, rf[pos + 2]), X[p][f]);
       }
-      pk::predict<PP, LIM, SRC>(k, X[p], A, B, ndt_2h2, dt_22, WP[p], WM[p], YE[p], YEv[p]);
+      pkx::predict<PP, LIM, SRC>(k, X[p], A, B, ndt_2h2, dt_22, WP[p], WM[p], YE[p], YEv[p]);
     }
 
     if (lane == 31) {
@@ -158,7 +158,7 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
       f2 L[4];
 #pragma unroll
       for (int f = 0; f < 4; ++f) L[f] = pk::pair(p ? WP[p - 1][f].y : nb[f], WP[p][f].x);
-      pk::hll<PP>(k, L, WM[p], XM[p], X[p], F[p]);   // the pair's left and inner faces
+      pkx::hll<PP>(k, L, WM[p], XM[p], X[p], F[p]);  // the pair's left and inner faces
     }
 
     if (lane == 0) {
@@ -182,7 +182,7 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
         for (int f = 0; f < 4; ++f) FR[f] = pk::pair(F[p][f].y, p < NPT - 1 ? F[p + 1][f].x : nf[f]);
         pk::update<SRC>(X[p], F[p], FR, YE[p], YEv[p], dt2, ndtdx2, Nw);
         const bool two = j + 1 < N;
-        pk::cfl<PP, SRC>(k, Nw, two ? 3 : 1, smax, akey, flags);
+        pkx::cfl<PP, SRC>(k, Nw, two ? 3 : 1, smax, akey, flags);
         if (two && (N & 1) == 0) {
 #pragma unroll
           for (int f = 0; f < 4; ++f) *reinterpret_cast<f2*>(Uout + (size_t)f * N + j) = Nw[f];
@@ -204,7 +204,8 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
 // per thread at a register budget of 3 blocks per SM (80 registers, 24 warps
 // per SM) or 2 (its natural ~94 registers), or two pairs per thread (1024-cell
 // tiles: half the barriers and exchanges per cell, two independent chains)
-// at 2 blocks per SM.  PP: the pressure policy (0 float, 2 compensated float).
+// at 2 blocks per SM.  PP: the pressure policy (0 float, 2 compensated float)
+// or the perturbation layout (3).
 template <int PP, int LIM, int SRC>
 struct KT {
   static constexpr auto fn13 = tile1d_kernel<PP, LIM, SRC, 3, 1>;
@@ -239,7 +240,9 @@ void* pick_lim(const KParams& kp, int var) {
 }
 
 void* pick(const KParams& kp, int precision, int var) {
-  return precision == PREC_FP32_PC ? pick_lim<2>(kp, var) : pick_lim<0>(kp, var);
+  if (precision == PREC_FP32_PC) return pick_lim<2>(kp, var);
+  if (precision == PREC_FP32_PS) return pick_lim<3>(kp, var);
+  return pick_lim<0>(kp, var);
 }
 
 size_t smem_of(int var) { return var == 22 ? sizeof(TileSmem<2>) : sizeof(TileSmem<1>); }

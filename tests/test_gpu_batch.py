@@ -153,6 +153,31 @@ def test_logged_mode_grows_at_eq8_rate(sv, m):
     assert abs(freq - w.real) <= 0.01 * abs(w.real)
 
 
+@pytest.mark.parametrize("m,amp", [(1, 1e-6), (3, 1e-6), (2, 1e-8)])
+def test_logged_mode_small_amplitude_perturbation_layout(sv, m, amp):
+    """The same eigenmode runs at amplitudes a float state cannot follow, in
+    the perturbation layout SV_FP32_PS (its rounding scales with the
+    perturbation): growth within 2% and frequency within 1% of eq. 8."""
+    N = 512 * m
+    Po = O.Params(tau0=0.1, limiter=O.VANLEER)
+    k = 2 * math.pi * m
+    w = D.growing_acoustic_root(Po, k)
+    t_end = math.log(30.0) / w.imag
+    md = D.eigenmode(Po, k, w)
+    U0 = inputs.waves_1d(1.4, N, 1.0, inputs.equilibrium_primitive(Po.Ck, Po.S),
+                         [inputs.Mode(m=m, shape=md["prim"], scale=amp)])
+    run = Run(n=N, t_end=t_end, S=1.0, tau0=0.1, m=m)
+    P = sv.Params(precision=sv.FP32_PS, limiter=sv.VANLEER)
+    with sv.Batch(P, [run], [U0], log_cap=40) as b:
+        b.run()
+        t, a = b.mode_log(0)
+        assert b.read(0, state=False)[3] == 0
+    growth = np.polyfit(t, np.log(np.abs(a)), 1)[0]
+    freq = -np.polyfit(t, np.unwrap(np.angle(a)), 1)[0]
+    assert abs(growth - w.imag) <= 0.02 * w.imag
+    assert abs(freq - w.real) <= 0.01 * abs(w.real)
+
+
 def test_stability_map_signs(sv):
     """Runs on either side of the S1 boundary (Q/I exponents 0): the logged
     fundamental decays below S1 and grows above it."""

@@ -44,9 +44,10 @@ def assert_all_equal(out):
         assert o[1:] == out[0][1:]
 
 
+@pytest.mark.parametrize("prec", ["FP32", "FP32_PC", "FP32_PS"])
 @pytest.mark.parametrize("N", [4096, 5001, 65536 + 3])
-def test_1d_float_configs_bitwise(sv, N):
-    P = sv.Params(precision=sv.FP32)
+def test_1d_float_configs_bitwise(sv, N, prec):
+    P = sv.Params(precision=getattr(sv, prec))
     descs, out = run_each_config(sv, P, (N,), wave_1d(N, seed=N), 30)
     assert len(descs) == 4 and "block tiles" in descs[0] and "4 cells per thread" in descs[2]
     assert "sliding" in descs[3]
