@@ -566,7 +566,8 @@ def run_sweep(args):
     build()
     runs, states = sweep_inputs(args.runs)
     runs = [_R(r) for r in runs]
-    P = sv.Params(precision=sv.FP32)
+    prec = PRECISIONS[args.precision]
+    P = sv.Params(precision=prec)
     stream = torch.cuda.Stream()
     # per-run step cap: about twice the expected CFL step count plus the tau bound
     max_steps = 30 * max(r.n for r in runs) + 20000
@@ -612,7 +613,7 @@ def run_sweep(args):
     t0 = time.perf_counter()
     for i in sub:
         r = runs[i]
-        Pi = sv.Params(precision=sv.FP32, S=r.S, tau0=r.tau0, tau_rho=r.tau_rho, tau_T=r.tau_T,
+        Pi = sv.Params(precision=prec, S=r.S, tau0=r.tau0, tau_rho=r.tau_rho, tau_T=r.tau_T,
                        Q_rho=r.Q_rho, Q_T=r.Q_T, I_rho=r.I_rho, I_T=r.I_T)
         with sv.Solver(Pi, (r.n,), (1.0,), stream=stream) as s:
             s.write_state(states[i])
@@ -629,11 +630,12 @@ def run_sweep(args):
     sb.close()
     line = {"metric": "batched sweep runs/s", "value": len(runs) / t_batch, "unit": "runs/s",
             "n_gpus": 1, "steps": len(times), "warmup": 0, "ms_per_step": 1e3 * t_batch,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPES[args.precision], "data": "synthetic",
             "config": {"workload": f"batched 1D stability sweep, {len(runs)} runs, N~U[256,16384], "
                                    "tau0 log-uniform [1e-3,1e1], S in [0,2], exponents in "
                                    "[-2.5,1], m in 1..8, 5 periods", "runs": len(runs),
+                       "precision": args.precision,
                        "launch_config": tuned["config"], "tuning_us": tuned["us"]},
             "cell_updates_per_s": cells / t_batch, "cell_updates": cells,
             "run_flags": {str(k): v for k, v in sorted(flags.items())},
