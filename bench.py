@@ -36,10 +36,10 @@ L2_FLUSH_BYTES = 256 << 20
 
 # DRAM bytes (read + write) of one launch of the 1D FP32 step kernel at N = 2^22
 # (the 512-cell block-tile configuration of tile1d_kernel), from one ncu capture
-# of the current kernel (67.2 MB read + 19.1 MB written during the launch; the
+# of the current kernel (67.2 MB read + 19.6 MB written during the launch; the
 # remaining writes are still dirty in L2 when it ends).  Only valid for that
 # workload, precision and launch configuration; other lines report null.
-TRAFFIC_1D_FP32_N22 = 86.2e6
+TRAFFIC_1D_FP32_N22 = 86.8e6
 
 # --precision names -> sv_params.precision (SV_FP32, SV_FP64, SV_FP32_P64,
 # SV_FP32_PC, SV_FP32_PS of include/sv.h) and the arithmetic type reported as "dtype"

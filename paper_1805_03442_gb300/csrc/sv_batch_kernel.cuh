@@ -220,7 +220,9 @@ batch_kernel(RunDev* __restrict__ runs, const int* __restrict__ order, int nruns
 // Kernel of the given block size for (limiter, precision).
 template <int NTB, typename R, int PP, int LIM>
 struct KB {
-  static constexpr int MINB = sizeof(R) == 8 ? 1 : 256 / NTB * 2;
+  // double and the perturbation layout take the whole register file (one
+  // block per SM) rather than spill
+  static constexpr int MINB = (sizeof(R) == 8 || PP == 3) ? 1 : 256 / NTB * 2;
   static constexpr auto fn = batch_kernel<R, PP, LIM, NTB, MINB>;
 };
 
