@@ -74,7 +74,7 @@ extern "C" {
                            the exact E - rho v^2/2 - E_nu of the float operands (two
                            error-free float sums), times gamma - 1, rounded once; the
                            same p as SV_FP32_P64 to within its last bit, at float speed */
-#define SV_FP32_PS  4   /* 1D MUSCL-Hancock only: float perturbations about the uniform
+#define SV_FP32_PS  4   /* MUSCL-Hancock (1D, 2D, 3D): float perturbations about the uniform
                            equilibrium (rho = p = 1, v = 0, E_nu = C_k + S) on the device, the
                            fluxes and the source Y written so that the equilibrium part cancels
                            exactly; host I/O stays full double states.  Float rounding then
@@ -233,7 +233,7 @@ int sv_status(sv_solver* s, uint32_t* flags);
 /* Device pointer of the current state buffer (nf * ncell elements of the
    solver's precision, field-major), valid until the next step.  For callers
    that keep data on the device.  Under SV_FP32_PS the buffer holds U - U_ref
-   (U_ref = (1, 0, 1/(gamma-1) + C_k + S, C_k + S)). */
+   (U_ref: rho = 1, zero momenta, E = 1/(gamma-1) + C_k + S, E_nu = C_k + S). */
 int sv_state_device(sv_solver* s, void** dev_ptr, int* elem_bytes);
 
 /* Release the solver (waits for its stream). */

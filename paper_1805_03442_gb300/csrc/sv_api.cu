@@ -81,8 +81,8 @@ int check_inputs(const sv_params* p, const sv_grid* g) {
     return SV_EINVAL;
   if (p->limiter < SV_MINMOD || p->limiter > SV_MC) return SV_EINVAL;
   if (p->precision < SV_FP32 || p->precision > SV_FP32_PS) return SV_EINVAL;
-  // the perturbation layout: 1D MUSCL-Hancock
-  if (p->precision == SV_FP32_PS && (g->dim != 1 || p->method != SV_HANCOCK)) return SV_EINVAL;
+  // the perturbation layout: MUSCL-Hancock
+  if (p->precision == SV_FP32_PS && p->method != SV_HANCOCK) return SV_EINVAL;
   for (int side = 0; side < 2; ++side)
     if (g->bc[side] < SV_BC_PERIODIC || g->bc[side] > SV_BC_DRIVEN) return SV_EINVAL;
   if (g->bc[1] == SV_BC_DRIVEN) return SV_EINVAL;
@@ -413,7 +413,7 @@ int sv_write_state(sv_solver* s, const double* host_soa, double t) {
   }
   SV_TRY(ctl_reset_launch(s->ctl, t, s->stream));
   SV_TRY(to_state_launch(s->p.precision, src, s->buf[0], s->buf[1], s->ctl, (int64_t)count,
-                         s->stream, s->kp.ref));
+                         s->stream, s->kp.ref, s->nf));
   SV_TRY(dt_reduce_launch(s->p.precision, s->dim, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell,
                           s->stream));
   return SV_OK;
@@ -425,7 +425,7 @@ int sv_read_state(sv_solver* s, double* host_soa, double* t) {
   // pinned host memory: the conversion kernel writes it over the host link
   double* dst = (double*)mapped_view(host_soa);
   SV_TRY(from_state_launch(s->p.precision, s->buf[0], s->buf[1], s->ctl, dst ? dst : s->staging,
-                           (int64_t)count, s->stream, s->kp.ref));
+                           (int64_t)count, s->stream, s->kp.ref, s->nf));
   if (!dst)
     SV_TRY(cudaMemcpyAsync(host_soa, s->staging, count * sizeof(double), cudaMemcpyDeviceToHost,
                            s->stream));
@@ -666,7 +666,7 @@ int sv_conservation(sv_solver* s, double* sums) {
   SV_TRY(cudaStreamSynchronize(s->stream));
   memcpy(sums, s->host_sums, s->nf * sizeof(double));
   if (s->p.precision == SV_FP32_PS)      // the device holds U - ref
-    for (int f = 0; f < s->nf; ++f) sums[f] += (double)s->ncell * s->kp.ref[f];
+    for (int f = 0; f < s->nf; ++f) sums[f] += (double)s->ncell * ref_field(s->kp.ref, f, s->nf);
   return SV_OK;
 }
 

@@ -61,10 +61,11 @@ cudaError_t set_target_launch(int precision, Ctl* ctl, double t_end, const KPara
 // Host-format (double, full state) <-> device state; `ref` (4 values) is the
 // reference state the perturbation layout PREC_FP32_PS subtracts, unused otherwise.
 cudaError_t to_state_launch(int precision, const double* src, void* a, void* b, Ctl* ctl,
-                            int64_t count, cudaStream_t st, const double* ref = nullptr);
+                            int64_t count, cudaStream_t st, const double* ref = nullptr,
+                            int nf = 4);
 cudaError_t from_state_launch(int precision, const void* a, const void* b, const Ctl* ctl,
                               double* dst, int64_t count, cudaStream_t st,
-                              const double* ref = nullptr);
+                              const double* ref = nullptr, int nf = 4);
 // Exact copy of the current state buffer's `bytes` to (save) or from `other`.
 cudaError_t raw_state_launch(void* a, void* b, const Ctl* ctl, void* other, int64_t bytes,
                              bool save, cudaStream_t st);

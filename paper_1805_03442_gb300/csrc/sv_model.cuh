@@ -85,6 +85,15 @@ inline void kparams_finish(KParams& k) {
   k.fps[3] = 0.0f;
 }
 
+// Entry f of the perturbation layout's reference state U_ref for nf = DIM + 3
+// fields (ref holds its 1D form: rho, rho v, E, E_nu).
+__host__ __device__ __forceinline__ double ref_field(const double (&ref)[4], int f, int nf) {
+  if (f == 0) return ref[0];
+  if (f == nf - 2) return ref[2];
+  if (f == nf - 1) return ref[3];
+  return 0.0;
+}
+
 // Device control block: time, step size and the reductions of one solver.
 struct Ctl {
   double t;            // current time

@@ -27,6 +27,7 @@
 #include "sv_internal.h"
 #include "sv_ndbnd.cuh"
 #include "sv_pairnd.cuh"
+#include "sv_pertnd.cuh"
 #include "sv_step1d.cuh"      // cp.async helpers, wrap
 
 namespace sv {
@@ -230,12 +231,12 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
     }
     f2 div[NF], dF[NF];
     bool ok0 = true, ok1 = true;
-    pkn::dflux<DIM, PP, 0>(k, X, d[0], div, ok0, ok1);
-    pkn::dflux<DIM, PP, 1>(k, X, d[1], dF, ok0, ok1);
+    pknx::dflux<DIM, PP, 0>(k, X, d[0], div, ok0, ok1);
+    pknx::dflux<DIM, PP, 1>(k, X, d[1], dF, ok0, ok1);
 #pragma unroll
     for (int f = 0; f < NF; ++f) div[f] = pk::add(div[f], dF[f]);
     if (DIM == 3) {
-      pkn::dflux<DIM, PP, DIM == 3 ? 2 : 1>(k, X, d[AM], dF, ok0, ok1);
+      pknx::dflux<DIM, PP, DIM == 3 ? 2 : 1>(k, X, d[AM], dF, ok0, ok1);
 #pragma unroll
       for (int f = 0; f < NF; ++f) div[f] = pk::add(div[f], dF[f]);
     }
@@ -257,7 +258,7 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
     // the cells' media (2D map: frozen cells have no source)
     const bool act0 = active(j0), act1 = active(j1);
     f2 yE, yEv;
-    pkn::source<DIM, PP, SRC>(k, X, yE, yEv);
+    pknx::source<DIM, PP, SRC>(k, X, yE, yEv);
     if (!act0) yE.x = yEv.x = 0.0f;
     if (!act1) yE.y = yEv.y = 0.0f;
     f2 uh[NF];
@@ -266,7 +267,7 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
     if (SRC == 2) uh[1 + DIM] = pk::fma(dt_22, yE, uh[1 + DIM]);
     if (SRC != 0) uh[2 + DIM] = pk::fma(dt_22, yEv, uh[2 + DIM]);
     f2 yEh, yEvh;
-    pkn::source<DIM, PP, SRC>(k, uh, yEh, yEvh);
+    pknx::source<DIM, PP, SRC>(k, uh, yEh, yEvh);
     if (!act0) yEh.x = yEvh.x = 0.0f;
     if (!act1) yEh.y = yEvh.y = 0.0f;
 
@@ -288,7 +289,7 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
         Rr[f] = pk::fma(nhalf, d[0][f], uh[f]);
         fl[f] = pk::pair(sU[0][f][oy][tx], sU[1][f][oy][tx]);
       }
-      pkn::hll<DIM, PP, 0>(k, L, Rr, fl, X, Fx);
+      pknx::hll<DIM, PP, 0>(k, L, Rr, fl, X, Fx);
       if (DIM == 3) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
@@ -296,7 +297,7 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
           Rr[f] = pk::fma(nhalf, d[1][f], uh[f]);
           fl[f] = pk::pair(sU[0][f][oy > 0 ? oy - 1 : oy][tx + 1], sU[1][f][oy > 0 ? oy - 1 : oy][tx + 1]);
         }
-        pkn::hll<DIM, PP, DIM == 3 ? 1 : 0>(k, L, Rr, fl, X, Fy);
+        pknx::hll<DIM, PP, DIM == 3 ? 1 : 0>(k, L, Rr, fl, X, Fy);
       }
     }
 #pragma unroll
@@ -328,7 +329,7 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
         fl[f] = pk::pair(um[f], u0[f]);
         wpm_next[f] = wp.y;
       }
-      pkn::hll<DIM, PP, AM>(k, L, Rr, fl, X, Hq);
+      pknx::hll<DIM, PP, AM>(k, L, Rr, fl, X, Hq);
     }
 
     // f. update of planes q-2 and q-1 (interior planes: no ghosts)
@@ -350,7 +351,8 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
         const bool d0 = gx >= __ldg(kp.pul_lo + (q - 2)) && gx < __ldg(kp.pul_hi + (q - 2));
         const bool d1 = two && gx >= __ldg(kp.pul_lo + (q - 1)) && gx < __ldg(kp.pul_hi + (q - 1));
         if (d0 || d1) {
-          pulse_state<float, NF>(kp, sc.t + sc.dt, pu);
+          if constexpr (PP == 3) pulse_state_ps<NF>(kp, sc.t + sc.dt, pu);
+          else pulse_state<float, NF>(kp, sc.t + sc.dt, pu);
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
             if (d0) Nw[f].x = pu[f];
@@ -365,7 +367,7 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
         Uout[f * ncell + oa] = Nw[f].x;
         if (two) Uout[f * ncell + ob] = Nw[f].y;
       }
-      pkn::cfl<DIM, PP, SRC>(k, Nw, two ? 3 : 1, smax, akey, flags);
+      pknx::cfl<DIM, PP, SRC>(k, Nw, two ? 3 : 1, smax, akey, flags);
     }
 
 #pragma unroll
@@ -446,8 +448,11 @@ int stepnd_pair_default_seg(int) { return PairCfg<2>::SEG; }
 cudaError_t stepnd_pair_launch(int dim, int precision, const KParams& kp, void* a, void* b, Ctl* ctl,
                                const int64_t* n, int seg, cudaStream_t st) {
   if (dim == 2)
-    return precision == PREC_FP32_PC ? pair_by_kind<2, 2>(kp, a, b, ctl, n, seg, st)
-                                     : pair_by_kind<0, 2>(kp, a, b, ctl, n, seg, st);
+    switch (precision) {
+      case PREC_FP32_PC: return pair_by_kind<2, 2>(kp, a, b, ctl, n, seg, st);
+      case PREC_FP32_PS: return pair_by_kind<3, 2>(kp, a, b, ctl, n, seg, st);
+      default: return pair_by_kind<0, 2>(kp, a, b, ctl, n, seg, st);
+    }
   return cudaErrorInvalidValue;
 }
 

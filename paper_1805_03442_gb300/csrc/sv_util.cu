@@ -3,7 +3,7 @@
 // conversion and the compensated conservation sums.
 #include "sv_internal.h"
 #include "sv_reduce.cuh"
-#include "sv_pert1d.cuh"
+#include "sv_pertnd.cuh"
 
 namespace sv {
 
@@ -64,11 +64,21 @@ __global__ void __launch_bounds__(NTU) dt_reduce_kernel(const KParams kp, const 
   const P<R> k(kp);
   R smax = 0, akey = -INFINITY;
   uint32_t flags = 0;
-  if constexpr (PP == 3) {        // 1D perturbation layout
+  if constexpr (PP == 3) {        // perturbation layout
     for (int64_t i = (int64_t)blockIdx.x * NTU + threadIdx.x; i < ncell;
          i += (int64_t)gridDim.x * NTU) {
-      const R u[4] = {U[i], U[ncell + i], U[2 * ncell + i], U[3 * ncell + i]};
-      cell_bound<R, 3, 1>(k, u, smax, akey, flags);
+      if (dim == 1) {
+        const R u[4] = {U[i], U[ncell + i], U[2 * ncell + i], U[3 * ncell + i]};
+        cell_bound<R, 3, 1>(k, u, smax, akey, flags);
+      } else if (dim == 2) {
+        float u[5];
+        for (int f = 0; f < 5; ++f) u[f] = U[f * ncell + i];
+        psn::bound<2, 1>(k, u, smax, akey, flags);
+      } else {
+        float u[6];
+        for (int f = 0; f < 6; ++f) u[f] = U[f * ncell + i];
+        psn::bound<3, 1>(k, u, smax, akey, flags);
+      }
     }
     reduce_and_finalize<R, NTU>(ctl, kp, smax, akey, flags, false);
     return;
@@ -173,23 +183,30 @@ __global__ void from_state_kernel(const R* a, const R* b, const Ctl* ctl, double
 }
 
 // The perturbation layout (SV_FP32_PS): element i of field f = i / ncell holds
-// (float)(U - ref[f]) (the difference taken in double).
-struct Ref4 {
-  double v[4];
+// (float)(U - ref[f]) (the difference taken in double); nf = 4, 5 or 6 fields.
+struct RefN {
+  double v[6];
 };
 
+RefN ref_of(const double* ref, int nf) {
+  RefN r{};
+  const double four[4] = {ref[0], ref[1], ref[2], ref[3]};
+  for (int f = 0; f < nf; ++f) r.v[f] = ref_field(four, f, nf);
+  return r;
+}
+
 __global__ void to_state_ps_kernel(const double* src, float* a, float* b, const Ctl* ctl,
-                                   int64_t ncell, Ref4 ref) {
+                                   int64_t count, int64_t ncell, RefN ref) {
   float* U = vload(&ctl->cur) ? b : a;
-  for (int64_t i = (int64_t)blockIdx.x * NTU + threadIdx.x; i < 4 * ncell;
+  for (int64_t i = (int64_t)blockIdx.x * NTU + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * NTU)
     U[i] = (float)(src[i] - ref.v[i / ncell]);
 }
 
 __global__ void from_state_ps_kernel(const float* a, const float* b, const Ctl* ctl, double* dst,
-                                     int64_t ncell, Ref4 ref) {
+                                     int64_t count, int64_t ncell, RefN ref) {
   const float* U = vload(&ctl->cur) ? b : a;
-  for (int64_t i = (int64_t)blockIdx.x * NTU + threadIdx.x; i < 4 * ncell;
+  for (int64_t i = (int64_t)blockIdx.x * NTU + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * NTU)
     dst[i] = ref.v[i / ncell] + (double)U[i];
 }
@@ -215,11 +232,11 @@ cudaError_t raw_state_launch(void* a, void* b, const Ctl* ctl, void* other, int6
 }
 
 cudaError_t to_state_launch(int precision, const double* src, void* a, void* b, Ctl* ctl,
-                            int64_t count, cudaStream_t st, const double* ref) {
+                            int64_t count, cudaStream_t st, const double* ref, int nf) {
   const int g = grid_small(count);
   if (precision == PREC_FP32_PS) {
-    Ref4 r{{ref[0], ref[1], ref[2], ref[3]}};
-    to_state_ps_kernel<<<g, NTU, 0, st>>>(src, (float*)a, (float*)b, ctl, count / 4, r);
+    to_state_ps_kernel<<<g, NTU, 0, st>>>(src, (float*)a, (float*)b, ctl, count, count / nf,
+                                          ref_of(ref, nf));
     return cudaGetLastError();
   }
   if (precision == PREC_FP64)
@@ -230,12 +247,12 @@ cudaError_t to_state_launch(int precision, const double* src, void* a, void* b, 
 }
 
 cudaError_t from_state_launch(int precision, const void* a, const void* b, const Ctl* ctl,
-                              double* dst, int64_t count, cudaStream_t st, const double* ref) {
+                              double* dst, int64_t count, cudaStream_t st, const double* ref,
+                              int nf) {
   const int g = grid_small(count);
   if (precision == PREC_FP32_PS) {
-    Ref4 r{{ref[0], ref[1], ref[2], ref[3]}};
-    from_state_ps_kernel<<<g, NTU, 0, st>>>((const float*)a, (const float*)b, ctl, dst, count / 4,
-                                            r);
+    from_state_ps_kernel<<<g, NTU, 0, st>>>((const float*)a, (const float*)b, ctl, dst, count,
+                                            count / nf, ref_of(ref, nf));
     return cudaGetLastError();
   }
   if (precision == PREC_FP64)

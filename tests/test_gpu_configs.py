@@ -72,7 +72,7 @@ def test_1d_other_solvers_have_one_config(sv):
                 s.set_config(1)
 
 
-@pytest.mark.parametrize("prec", ["FP32", "FP64"])
+@pytest.mark.parametrize("prec", ["FP32", "FP64", "FP32_PS"])
 def test_2d_configs_bitwise(sv, prec):
     nx, ny = 130, 300                 # several x tiles and a ragged x tile; 300 planes
     P = sv.Params(precision=getattr(sv, prec))

@@ -121,8 +121,6 @@ def test_conservation_and_equilibrium(sv):
     assert np.array_equal(U, Ue)
 
 
-def test_rejected_outside_1d_hancock(sv):
-    with pytest.raises(sv.SvError):
-        sv.Solver(sv.Params(precision=sv.FP32_PS), (32, 32))
+def test_rejected_with_heun(sv):
     with pytest.raises(sv.SvError):
         sv.Solver(sv.Params(precision=sv.FP32_PS, method=sv.HEUN), (1024,))
