@@ -124,3 +124,46 @@ def test_conservation_and_equilibrium(sv):
 def test_rejected_with_heun(sv):
     with pytest.raises(sv.SvError):
         sv.Solver(sv.Params(precision=sv.FP32_PS, method=sv.HEUN), (1024,))
+
+
+@pytest.mark.parametrize("N", [1000, 5000])
+@pytest.mark.parametrize("bc", [(1, 1), (2, 2), (1, 2)])
+def test_walls_and_outflow_against_fp64(sv, N, bc):
+    """Wall ghosts (reversed momentum) and outflow copies of perturbations, on
+    the sliding warps (1000 cells) and the block tiles (5000): against the
+    FP64 kernels at the same time, relative to the perturbation."""
+    out = {}
+    for prec in ("FP32_PS", "FP64"):
+        P = sv.Params(precision=getattr(sv, prec), tau0=0.3)
+        U0, d = _perturbed(P, N, seed=N + bc[0], amp=1e-3)
+        with sv.Solver(P, (N,), (1.0,), bc=bc) as s:
+            s.write_state(U0)
+            rc, _ = s.run_to(0.05)
+            U, t = s.read_state()
+            assert rc == 0 and t == 0.05
+        out[prec] = U
+    err = np.max(np.abs(out["FP32_PS"] - out["FP64"]), axis=1)
+    assert np.all(err <= 3e-4 * np.max(np.abs(d), axis=1)), err
+
+
+@pytest.mark.parametrize("N", [2000, 5000])
+def test_driven_boundary_against_fp64(sv, N):
+    """The driven boundary's ghost states (full states in double, minus the
+    reference) on both kernels: against the FP64 kernels, relative to the
+    wave the boundary drives in."""
+    from test_gpu_driven import setup
+    out = {}
+    for prec in ("FP32_PS", "FP64"):
+        P = sv.Params(precision=getattr(sv, prec), S=0.5, tau0=0.0135)
+        w, k, base, amp = setup(oracle_params(P))
+        U0 = np.repeat(base[:, None], N, axis=1)
+        with sv.Solver(P, (N,), (1.0,), bc=(sv.BC_DRIVEN, sv.BC_OUTFLOW)) as s:
+            s.set_drive(w, k, base, amp)
+            s.write_state(U0)
+            rc, _ = s.run_to(0.1)
+            U, t = s.read_state()
+            assert rc == 0 and t == 0.1
+        out[prec] = U
+    wave = np.max(np.abs(out["FP64"] - U0), axis=1)
+    err = np.max(np.abs(out["FP32_PS"] - out["FP64"]), axis=1)
+    assert np.all(wave > 0) and np.all(err <= 1e-3 * wave), (err, wave)
