@@ -26,7 +26,7 @@ template <> struct TauKey<float> {
 };
 template <> struct TauKey<double> {
   static __device__ __forceinline__ double of(const P<double>& k, double rho, double T) {
-    return -(k.tau0 * pow(rho, k.tau_rho) * pow(T, k.tau_T));
+    return -(k.tau0 * exp(fma(k.tau_rho, log(rho), k.tau_T * log(T))));
   }
 };
 
