@@ -44,15 +44,6 @@ __device__ __forceinline__ Prim prim(const P<float>& k, const float (&u)[4]) {
   return q;
 }
 
-// F(U) - F(U_ref) of eq. 13's flux.
-__device__ __forceinline__ void flux(const P<float>& k, const float (&u)[4], const Prim& q,
-                                     float (&F)[4]) {
-  F[0] = u[1];
-  F[1] = q.kin2 + q.dp;
-  F[2] = q.v * (k.h0 + (u[2] + q.dp));
-  F[3] = q.v * (k.ev0 + u[3]);
-}
-
 // ln(1 + x) and exp(y) - 1 with relative accuracy near 0.  Perturbations of
 // the linear stage are small, so the Mercator series of ln(1 + x) and the
 // exponential series (textbook Taylor coefficients 1/n and 1/n!, Horner form)
@@ -83,24 +74,6 @@ __device__ __forceinline__ float em1(float y) {
   return expm1f(y);
 }
 
-// Components E and E_nu of Y at the perturbed state u (SRC as Src<R, SRC>).
-template <int SRC>
-__device__ __forceinline__ void source(const P<float>& k, const float (&u)[4], const Prim& q,
-                                       float& yE, float& yEv) {
-  yE = yEv = 0.0f;
-  if (SRC == 0) return;
-  const float lr = ln1p(u[0]);
-  const float lT = ln1p((q.dp - u[0]) * q.ir);
-  // 1/tau = (1/tau0) rho^-tau_rho T^-tau_T: a rate, so the SFU exp2 suffices
-  const float inv_tau =
-      Ar<float>::ex2(fmaf(1.44269504f, fmaf(k.ntau_rho, lr, k.ntau_T * lT), k.l2_inv_tau0));
-  const float a = 1.0f + k.Q_rho + k.tau_rho, b = k.Q_T + k.tau_T;
-  const float relax = fmaf(k.Ck, q.dp, -u[3]) + k.S * em1(fmaf(a, lr, b * lT));
-  yEv = relax * inv_tau;
-  if (SRC == 2)
-    yE = q.rho * k.Q0 * (em1(fmaf(k.Q_rho, lr, k.Q_T * lT)) - em1(fmaf(k.I_rho, lr, k.I_T * lT)));
-}
-
 // eq. 16 bound and physicality of one perturbed state.
 template <int SRC>
 __device__ __forceinline__ void bound(const P<float>& k, const float (&u)[4], float& smax,
@@ -116,85 +89,13 @@ __device__ __forceinline__ void bound(const P<float>& k, const float (&u)[4], fl
   if (SRC != 0) akey = fmaxf(akey, TauKey<float>::of(k, q.rho, q.p * q.ir));
 }
 
-// Slopes, positivity guard, predictor and face states of one cell (as the
-// full-state predict() of sv_step1d.cuh).
-template <int LIM, int SRC>
-__device__ __forceinline__ void predict(const P<float>& k, const float (&u)[4],
-                                        const float (&um)[4], const float (&up)[4], float dt_2h,
-                                        float dt_2, float (&wp)[4], float (&wm)[4], float& yEh,
-                                        float& yEvh) {
-  float d[4], a[4], b[4];
-#pragma unroll
-  for (int f = 0; f < 4; ++f) {
-    d[f] = limit<LIM, float>(u[f] - um[f], up[f] - u[f]);
-    a[f] = u[f] + 0.5f * d[f];
-    b[f] = u[f] - 0.5f * d[f];
-  }
-  const Prim qa = prim(k, a), qb = prim(k, b);
-  float Fa[4], Fb[4], dF[4];
-  flux(k, a, qa, Fa);
-  flux(k, b, qb, Fb);
-#pragma unroll
-  for (int f = 0; f < 4; ++f) dF[f] = Fa[f] - Fb[f];
-  if (!(fminf(fminf(qa.rho, qa.p), fminf(qb.rho, qb.p)) > 0.0f)) {
-#pragma unroll
-    for (int f = 0; f < 4; ++f) d[f] = dF[f] = 0.0f;
-  }
-  float yE = 0.0f, yEv = 0.0f;
-  if (SRC != 0) source<SRC>(k, u, prim(k, u), yE, yEv);
-  float uh[4];
-  uh[0] = u[0] - dt_2h * dF[0];
-  uh[1] = u[1] - dt_2h * dF[1];
-  uh[2] = u[2] - dt_2h * dF[2] + dt_2 * yE;
-  uh[3] = u[3] - dt_2h * dF[3] + dt_2 * yEv;
-#pragma unroll
-  for (int f = 0; f < 4; ++f) {
-    wp[f] = uh[f] + 0.5f * d[f];
-    wm[f] = uh[f] - 0.5f * d[f];
-  }
-  yEh = yEvh = 0.0f;
-  if (SRC != 0) source<SRC>(k, uh, prim(k, uh), yEh, yEvh);
-}
-
-// eq. 13 at one face (as hll() of sv_step1d.cuh), on perturbed states and
-// the reduced fluxes.
-__device__ __forceinline__ void hll(const P<float>& k, const float (&l)[4], const float (&r)[4],
-                                    const float (&fl)[4], const float (&fr)[4], float (&F)[4]) {
-  float L[4], Rr[4];
-#pragma unroll
-  for (int f = 0; f < 4; ++f) {
-    L[f] = l[f];
-    Rr[f] = r[f];
-  }
-  Prim qL = prim(k, L), qR = prim(k, Rr);
-  if (!(fminf(fminf(qL.rho, qL.p), fminf(qR.rho, qR.p)) > 0.0f)) {
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      L[f] = fl[f];
-      Rr[f] = fr[f];
-    }
-    qL = prim(k, L);
-    qR = prim(k, Rr);
-  }
-  const float cL = Ar<float>::sqrt_pos(k.gamma * qL.p * qL.ir);
-  const float cR = Ar<float>::sqrt_pos(k.gamma * qR.p * qR.ir);
-  const float sl = fminf(fminf(qL.v - cL, qR.v - cR), 0.0f);
-  const float sr = fmaxf(fmaxf(qL.v + cL, qR.v + cR), 0.0f);
-  float FL[4], FR[4];
-  flux(k, L, qL, FL);
-  flux(k, Rr, qR, FR);
-  const float inv = Ar<float>::rcp(sr - sl);
-  const float wl = sr * inv, wr = -sl * inv, wd = sl * sr * inv;
-#pragma unroll
-  for (int f = 0; f < 4; ++f) F[f] = wl * FL[f] + wr * FR[f] + wd * (Rr[f] - L[f]);
-}
-
 }  // namespace ps
 
 // ------------------------------------------------------------------ packed
-// The same arithmetic on a lane's two cells in packed f32x2 operations (as
+// The step itself runs on a lane's two cells in packed f32x2 operations (as
 // sv_pair1d.cuh does for the full-state policies): component .x the even
-// cell, .y the odd one.
+// cell, .y the odd one.  The one-cell ps:: functions above serve the eq. 16
+// bound of an uploaded state and the per-component fallback of the series.
 namespace pkps {
 
 using pk::add;

@@ -75,10 +75,6 @@ template <typename R, int PP, int LIM, int SRC>
 __device__ __forceinline__ void predict(const P<R>& k, const R (&u)[4], const R (&um)[4],
                                         const R (&up)[4], R dt_2h, R dt_2, R (&wp)[4], R (&wm)[4],
                                         R& yEh, R& yEvh) {
-  if constexpr (PP == 3) {          // perturbation layout (sv_pert1d.cuh)
-    ps::predict<LIM, SRC>(k, u, um, up, dt_2h, dt_2, wp, wm, yEh, yEvh);
-    return;
-  }
   R d[4], a[4], b[4];
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
@@ -161,10 +157,6 @@ __device__ __forceinline__ void level_states(const P<R>& k, const R (&u)[4], con
 template <typename R, int PP>
 __device__ __forceinline__ void hll(const P<R>& k, const R (&l)[4], const R (&r)[4],
                                     const R (&fl)[4], const R (&fr)[4], R (&F)[4]) {
-  if constexpr (PP == 3) {
-    ps::hll(k, l, r, fl, fr, F);
-    return;
-  }
   R L[4], Rr[4];
 #pragma unroll
   for (int f = 0; f < 4; ++f) { L[f] = l[f]; Rr[f] = r[f]; }
