@@ -59,11 +59,18 @@ __device__ __forceinline__ void load_tile(float (*dst)[SPAN], const float* Uin, 
                                           const P<float>& k, const KParams& kp, double t) {
   const int lo = b - 2;
   if ((N & 3) == 0 && lo >= 0 && lo + SPAN <= N) {
-    // lo = b - 2 is a multiple of 4 (b = OUT i - 2 with OUT a multiple of 4)
-    for (int e = threadIdx.x; e < 4 * (SPAN / 4); e += NTT) {
-      const int f = e / (SPAN / 4), q = e - f * (SPAN / 4);
-      cp16(&dst[f][4 * q], Uin + (size_t)f * N + lo + 4 * q);
-    }
+    // lo = b - 2 is a multiple of 4 (b = OUT i - 2 with OUT a multiple of 4).
+    // A quarter of the block per field: thread q of it copies 16-byte chunks
+    // q, q + NTT/4, ... of the SPAN/4 = 1 + R NTT/4 chunks, and thread 0 the
+    // last one, so no thread divides an index.
+    constexpr int C4 = SPAN / 4, TPF = NTT / 4, R = (C4 - 1) / TPF;
+    static_assert(C4 == 1 + R * TPF, "span of whole quarter-block rounds plus one chunk");
+    const int f = threadIdx.x / TPF, q = threadIdx.x % TPF;
+    const float* src = Uin + (size_t)f * N + lo + 4 * q;
+    float* d = &dst[f][4 * q];
+#pragma unroll
+    for (int r = 0; r < R; ++r) cp16(d + 4 * TPF * r, src + 4 * TPF * r);
+    if (q == 0) cp16(d + 4 * (C4 - 1), src + 4 * (C4 - 1));
   } else {
     for (int e = threadIdx.x; e < SPAN; e += NTT) {
       const int j = lo + e;
