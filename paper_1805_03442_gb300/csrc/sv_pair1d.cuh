@@ -154,21 +154,22 @@ __device__ __forceinline__ void predict(const P<float>& k, const f2 (&X)[4], con
   }
 }
 
-// eq. 13 at two faces with left states L and right states R; a face with a
-// non-physical state uses the cell values (fl, fr) instead.  Written with
+// eq. 13 at the two faces of a pair, with left states L and right states R;
+// a face with a non-physical state uses the cell values instead: those of the
+// pair's cells X and of the cell xl left of it (per field).  Written with
 // -S_L >= 0 so that every weight is non-negative:
 //   F = (S_R F_L + (-S_L) F_R + (-S_L) S_R (L - R)) / (S_R - S_L).
 template <int PP>
-__device__ __forceinline__ void hll(const P<float>& k, f2 (&L)[4], f2 (&R)[4], const f2 (&fl)[4],
-                                    const f2 (&fr)[4], f2 (&F)[4]) {
+__device__ __forceinline__ void hll(const P<float>& k, f2 (&L)[4], f2 (&R)[4], const float (&xl)[4],
+                                    const f2 (&X)[4], f2 (&F)[4]) {
   Prim pl = prim<PP>(k, L), pr = prim<PP>(k, R);
   const bool g0 = fminf(fminf(L[0].x, pl.p.x), fminf(R[0].x, pr.p.x)) > 0.0f;
   const bool g1 = fminf(fminf(L[0].y, pl.p.y), fminf(R[0].y, pr.p.y)) > 0.0f;
   if (!(g0 && g1)) {
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-      if (!g0) { L[f].x = fl[f].x; R[f].x = fr[f].x; }
-      if (!g1) { L[f].y = fl[f].y; R[f].y = fr[f].y; }
+      if (!g0) { L[f].x = xl[f]; R[f].x = X[f].x; }
+      if (!g1) { L[f].y = X[f].x; R[f].y = X[f].y; }
     }
     pl = prim<PP>(k, L);
     pr = prim<PP>(k, R);

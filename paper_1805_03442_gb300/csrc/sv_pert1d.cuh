@@ -218,16 +218,16 @@ __device__ __forceinline__ void predict(const P<float>& k, const f2 (&X)[4], con
   if (SRC != 0) source<SRC>(k, uh, prim(k, uh), yEh, yEvh);
 }
 
-__device__ __forceinline__ void hll(const P<float>& k, f2 (&L)[4], f2 (&R)[4], const f2 (&fl)[4],
-                                    const f2 (&fr)[4], f2 (&F)[4]) {
+__device__ __forceinline__ void hll(const P<float>& k, f2 (&L)[4], f2 (&R)[4], const float (&xl)[4],
+                                    const f2 (&X)[4], f2 (&F)[4]) {
   Prim ql = prim(k, L), qr = prim(k, R);
   const bool g0 = fminf(fminf(ql.rho.x, ql.p.x), fminf(qr.rho.x, qr.p.x)) > 0.0f;
   const bool g1 = fminf(fminf(ql.rho.y, ql.p.y), fminf(qr.rho.y, qr.p.y)) > 0.0f;
   if (!(g0 && g1)) {
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-      if (!g0) { L[f].x = fl[f].x; R[f].x = fr[f].x; }
-      if (!g1) { L[f].y = fl[f].y; R[f].y = fr[f].y; }
+      if (!g0) { L[f].x = xl[f]; R[f].x = X[f].x; }
+      if (!g1) { L[f].y = X[f].x; R[f].y = X[f].y; }
     }
     ql = prim(k, L);
     qr = prim(k, R);
@@ -292,10 +292,9 @@ __device__ __forceinline__ void predict(const P<float>& k, const pk::f2 (&X)[4],
 
 template <int PP>
 __device__ __forceinline__ void hll(const P<float>& k, pk::f2 (&L)[4], pk::f2 (&R)[4],
-                                    const pk::f2 (&fl)[4], const pk::f2 (&fr)[4],
-                                    pk::f2 (&F)[4]) {
-  if constexpr (PP == 3) pkps::hll(k, L, R, fl, fr, F);
-  else pk::hll<PP>(k, L, R, fl, fr, F);
+                                    const float (&xl)[4], const pk::f2 (&X)[4], pk::f2 (&F)[4]) {
+  if constexpr (PP == 3) pkps::hll(k, L, R, xl, X, F);
+  else pk::hll<PP>(k, L, R, xl, X, F);
 }
 
 template <int PP, int SRC>

@@ -323,21 +323,25 @@ __device__ __forceinline__ void step1d_warp(const P<R>& k, const R* __restrict__
     issue(kk + RS - 2);          // reuses the slot of chunk kk-2
     const int pos = (kk & (RS - 1)) * 64 + 2 * lane;
     if constexpr (PACKED) {
-      f2 X[4], XM[4], A[4], B[4], Qp[4];
+      f2 X[4], A[4], B[4], Qp[4];
+      float xl[4];
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
         const float* rf = reinterpret_cast<const float*>(ring) + f * RN;
         X[f] = *reinterpret_cast<const f2*>(rf + pos);
         Qp[f] = *reinterpret_cast<const f2*>(rf + ((pos - 64) & MASK));   // previous chunk's pair
-        XM[f] = pk::pair(rf[(pos - 1) & MASK], X[f].x);
-        A[f] = pk::sub(X[f], XM[f]);
-        B[f] = pk::sub(pk::pair(X[f].y, rf[(pos + 2) & MASK]), X[f]);
+        xl[f] = rf[(pos - 1) & MASK];
+        // one-sided differences, the inner one shared by both cells (scalar:
+        // the limiter takes them component by component)
+        const float c = X[f].y - X[f].x;
+        A[f] = pk::pair(X[f].x - xl[f], c);
+        B[f] = pk::pair(c, rf[(pos + 2) & MASK] - X[f].y);
       }
       f2 WP[4], WM[4], YE, YEv, L[4], F[4];
       pkx::predict<PPK, LIM, SRC>(k, X, A, B, ndt_2h2, dt_22, WP, WM, YE, YEv);
 #pragma unroll
       for (int f = 0; f < 4; ++f) L[f] = pk::pair(shfl(lane == 31 ? Wy_prev[f] : WP[f].y, src_m), WP[f].x);
-      pkx::hll<PPK>(k, L, WM, XM, X, F);            // faces 2i - 1/2 and 2i + 1/2
+      pkx::hll<PPK>(k, L, WM, xl, X, F);            // faces 2i - 1/2 and 2i + 1/2
       if (kk > c0) {
         // update of the pair of chunk kk-1: left faces F_prev, right faces
         // (inner face, next lane's left face)

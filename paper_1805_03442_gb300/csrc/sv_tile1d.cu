@@ -130,7 +130,8 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
       load_tile<SPAN, PP>(S.u[buf ^ 1], Uin, N, OUT * (tile + gridDim.x) - 2, k, kp, t);
 
     // pair p of the thread sits at span offsets 2 + 2 (NPT t + p) and the next
-    f2 X[NPT][4], XM[NPT][4], WP[NPT][4], WM[NPT][4], YE[NPT], YEv[NPT];
+    f2 X[NPT][4], WP[NPT][4], WM[NPT][4], YE[NPT], YEv[NPT];
+    float XL[NPT][4];                             // the cell left of each pair
 #pragma unroll
     for (int p = 0; p < NPT; ++p) {
       const int pos = 2 + 2 * (NPT * (int)threadIdx.x + p);
@@ -139,9 +140,12 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
       for (int f = 0; f < 4; ++f) {
         const float* rf = S.u[buf][f];
         X[p][f] = *reinterpret_cast<const f2*>(rf + pos);
-        XM[p][f] = pk::pair(rf[pos - 1], X[p][f].x);
-        A[f] = pk::sub(X[p][f], XM[p][f]);
-        B[f] = pk::sub(pk::pair(X[p][f].y, rf[pos + 2]), X[p][f]);
+        XL[p][f] = rf[pos - 1];
+        // one-sided differences, the inner one shared by both cells (scalar:
+        // the limiter takes them component by component)
+        const float c = X[p][f].y - X[p][f].x;
+        A[f] = pk::pair(X[p][f].x - XL[p][f], c);
+        B[f] = pk::pair(c, rf[pos + 2] - X[p][f].y);
       }
       pkx::predict<PP, LIM, SRC>(k, X[p], A, B, ndt_2h2, dt_22, WP[p], WM[p], YE[p], YEv[p]);
     }
@@ -165,7 +169,7 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
       f2 L[4];
 #pragma unroll
       for (int f = 0; f < 4; ++f) L[f] = pk::pair(p ? WP[p - 1][f].y : nb[f], WP[p][f].x);
-      pkx::hll<PP>(k, L, WM[p], XM[p], X[p], F[p]);  // the pair's left and inner faces
+      pkx::hll<PP>(k, L, WM[p], XL[p], X[p], F[p]);  // the pair's left and inner faces
     }
 
     if (lane == 0) {
