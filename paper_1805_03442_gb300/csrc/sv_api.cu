@@ -195,9 +195,11 @@ void build_configs(sv_solver* s) {
          s->p.precision == SV_FP32_PS) &&
         s->ncell >= kTile1dMinCells) {
       s->cfgs.push_back({CFG_TILE, 13,
-                         "1D: 512-cell block tiles, 2 cells per thread, 80 registers, 3 blocks/SM"});
+                         "1D: 512-cell block tiles, 2 cells per thread, 78 registers, 3 blocks/SM"});
       s->cfgs.push_back({CFG_TILE, 12, "1D: 512-cell block tiles, 2 cells per thread, 2 blocks/SM"});
       s->cfgs.push_back({CFG_TILE, 22, "1D: 1024-cell block tiles, 4 cells per thread, 2 blocks/SM"});
+      s->cfgs.push_back({CFG_TILE, 14,
+                         "1D: 512-cell block tiles, 2 cells per thread, 64 registers, 4 blocks/SM"});
     }
     s->cfgs.push_back({CFG_SLIDE, 0, "1D: warps sliding over 64-cell chunks, 2 cells per thread"});
   } else {

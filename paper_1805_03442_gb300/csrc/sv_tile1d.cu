@@ -212,14 +212,15 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
 }
 
 // Variants (tile1d_grid / tile1d_launch `var` = 10 NPT + MINB): one cell pair
-// per thread at a register budget of 3 blocks per SM (80 registers, 24 warps
-// per SM) or 2 (its natural ~94 registers), or two pairs per thread (1024-cell
-// tiles: half the barriers and exchanges per cell, two independent chains)
-// at 2 blocks per SM.  PP: the pressure policy (0 float, 2 compensated float)
+// per thread at a register budget of 3 blocks per SM (78 registers, 24 warps
+// per SM), 4 (64 registers, 32 warps, a few bytes of spills) or 2 (its
+// natural ~96 registers), or two pairs per thread (1024-cell tiles: half the
+// barriers and exchanges per cell, two independent chains) at 2 blocks per SM.  PP: the pressure policy (0 float, 2 compensated float)
 // or the perturbation layout (3).
 template <int PP, int LIM, int SRC>
 struct KT {
   static constexpr auto fn13 = tile1d_kernel<PP, LIM, SRC, 3, 1>;
+  static constexpr auto fn14 = tile1d_kernel<PP, LIM, SRC, 4, 1>;
   static constexpr auto fn12 = tile1d_kernel<PP, LIM, SRC, 2, 1>;
   static constexpr auto fn22 = tile1d_kernel<PP, LIM, SRC, 2, 2>;
 };
@@ -228,6 +229,7 @@ template <int PP, int LIM, int SRC>
 void* pick_var(int var) {
   if (var == 12) return (void*)KT<PP, LIM, SRC>::fn12;
   if (var == 22) return (void*)KT<PP, LIM, SRC>::fn22;
+  if (var == 14) return (void*)KT<PP, LIM, SRC>::fn14;
   return (void*)KT<PP, LIM, SRC>::fn13;
 }
 
@@ -261,7 +263,7 @@ size_t smem_of(int var) { return var == 22 ? sizeof(TileSmem<2>) : sizeof(TileSm
 }  // namespace
 
 // Sets the kernel's shared-memory limit (host side, outside any capture) and
-// returns the persistent grid size of variant `var` (13, 12 or 22), 0 on failure.
+// returns the persistent grid size of variant `var` (13, 14, 12 or 22), 0 on failure.
 int tile1d_grid(const KParams& kp, int precision, int var) {
   int dev = 0, sms = 0, per = 0;
   const void* fn = pick(kp, precision, var);

@@ -49,8 +49,8 @@ def assert_all_equal(out):
 def test_1d_float_configs_bitwise(sv, N, prec):
     P = sv.Params(precision=getattr(sv, prec))
     descs, out = run_each_config(sv, P, (N,), wave_1d(N, seed=N), 30)
-    assert len(descs) == 4 and "block tiles" in descs[0] and "4 cells per thread" in descs[2]
-    assert "sliding" in descs[3]
+    assert len(descs) == 5 and "block tiles" in descs[0] and "4 cells per thread" in descs[2]
+    assert "4 blocks/SM" in descs[3] and "sliding" in descs[4]
     assert_all_equal(out)
 
 
