@@ -11,15 +11,17 @@ namespace sv {
 // wall mirror (flip: the normal momentum is reversed) or outflow copy.
 // Positions further out than the two ghost layers are clamped into the grid;
 // their values reach no updated cell.
-__device__ __forceinline__ int64_t map_axis(int64_t j, int64_t n, int bc_lo, int bc_hi,
-                                            bool& flip) {
+// In the type of j, as wrap.
+template <typename I>
+__device__ __forceinline__ I map_axis(I j, typename index_of<I>::type n, int bc_lo, int bc_hi,
+                                      bool& flip) {
   flip = false;
   if (j >= 0 && j < n) return j;
   const int bc = j < 0 ? bc_lo : bc_hi;
   if (bc == BC_PERIODIC) return wrap(j, n);
   if (bc == BC_REFLECT) {
     flip = true;
-    const int64_t m = j < 0 ? -1 - j : 2 * n - 1 - j;
+    const I m = j < 0 ? -1 - j : 2 * n - 1 - j;
     return m < 0 ? 0 : (m >= n ? n - 1 : m);
   }
   return j < 0 ? 0 : n - 1;

@@ -199,8 +199,13 @@ __device__ __forceinline__ void reduce_and_finalize(Ctl* ctl, const KParams& kp,
   if (last && threadIdx.x == 0) finalize<R>(ctl, kp, advance, flip);
 }
 
-// Periodic index for |j| within a few periods of [0, N).
-__device__ __forceinline__ int64_t wrap(int64_t j, int64_t N) {
+// The index type of a call, taken from its first argument only.
+template <typename T> struct index_of { using type = T; };
+
+// Periodic index for |j| within a few periods of [0, N), in the type of j
+// (int64_t, or int where the caller's grid fits).
+template <typename I>
+__device__ __forceinline__ I wrap(I j, typename index_of<I>::type N) {
   if (j >= 0 && j < N) return j;
   j %= N;
   return j < 0 ? j + N : j;

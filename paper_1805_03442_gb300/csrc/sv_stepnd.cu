@@ -214,29 +214,33 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
   const int seg = blockIdx.x % nseg;
   const int tile = blockIdx.x / nseg;
   const int tile_x = tile % tiles_x, tile_y = tile / tiles_x;
-  const int64_t gx = (int64_t)tile_x * (TX - 2) - 1 + tx;
-  const int64_t gy = DIM == 3 ? (int64_t)tile_y * (TY - 2) - 1 + ty : 0;
-  const int64_t M = DIM == 3 ? nz : ny;                     // planes
-  const int64_t plane = DIM == 3 ? nx * ny : nx;            // cells per plane
-  const int64_t ncell = plane * M;
-  const int64_t q0 = seg * M / nseg, q1 = (seg + 1) * M / nseg;
-  const bool interior = tx >= 1 && tx <= TX - 2 && gx < nx &&
-                        (DIM == 2 || (ty >= 1 && ty <= TY - 2 && gy < ny));
+  // Cell and field offsets in 32 bits: the launch admits grids whose fields
+  // hold fewer than 2^31 values in all (stepnd_launch).
+  using I = int;
+  const I gx = (I)tile_x * (TX - 2) - 1 + tx;
+  const I gy = DIM == 3 ? (I)tile_y * (TY - 2) - 1 + ty : 0;
+  const I M = (I)(DIM == 3 ? nz : ny);                      // planes
+  const I plane = (I)(DIM == 3 ? nx * ny : nx);             // cells per plane
+  const I ncell = plane * M;
+  const I q0 = (I)((int64_t)seg * M / nseg), q1 = (I)((int64_t)(seg + 1) * M / nseg);
+  const I nxi = (I)nx, nyi = (I)ny;
+  const bool interior = tx >= 1 && tx <= TX - 2 && gx < nxi &&
+                        (DIM == 2 || (ty >= 1 && ty <= TY - 2 && gy < nyi));
   // 2D boundaries: x sides kp.bc_lo / bc_hi, y sides (the marching axis)
   // kp.bc_ylo / bc_yhi; 3D is periodic.  Ghost positions load the mapped cell;
   // the reversed momenta of wall ghosts are applied when the planes are read.
   static_assert(!BND || DIM == 2, "boundaries and media are 2D only");
   bool fx_own = false, fx_rx = false;
-  const int64_t wx = BND ? map_axis(gx, nx, kp.bc_lo, kp.bc_hi, fx_own) : wrap(gx, nx);
-  const int64_t wy = DIM == 3 ? wrap(gy, ny) : 0;
-  const int64_t col = DIM == 3 ? wy * nx + wx : wx;          // index within a plane
+  const I wx = BND ? map_axis(gx, nxi, kp.bc_lo, kp.bc_hi, fx_own) : wrap(gx, nxi);
+  const I wy = DIM == 3 ? wrap(gy, nyi) : 0;
+  const I col = DIM == 3 ? wy * nxi + wx : wx;               // index within a plane
   // second-ring positions loaded by the halo threads
   const bool ringx = (tx == 0) || (tx == TX - 1);
-  const int64_t col_rx = (DIM == 3 ? wy * nx : 0) +
-                         (BND ? map_axis(gx + (tx == 0 ? -1 : 1), nx, kp.bc_lo, kp.bc_hi, fx_rx)
-                              : wrap(gx + (tx == 0 ? -1 : 1), nx));
+  const I col_rx = (DIM == 3 ? wy * nxi : 0) +
+                   (BND ? map_axis(gx + (tx == 0 ? -1 : 1), nxi, kp.bc_lo, kp.bc_hi, fx_rx)
+                        : wrap(gx + (tx == 0 ? -1 : 1), nxi));
   // plane of the marching axis holding position p, and whether it is a wall ghost
-  auto plane_of = [&](int64_t p, bool& fy) -> int64_t {
+  auto plane_of = [&](I p, bool& fy) -> I {
     if (!BND) {
       fy = false;
       return wrap(p, M);
@@ -246,7 +250,7 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
   const bool medium = BND && kp.act_lo != nullptr;
   const bool pulses = BND && kp.pul_lo != nullptr;
   const bool ringy = DIM == 3 && ((ty == 0) || (ty == TY - 1));
-  const int64_t col_ry = DIM == 3 ? wrap(gy + (ty == 0 ? -1 : 1), ny) * nx + wx : 0;
+  const I col_ry = DIM == 3 ? wrap(gy + (ty == 0 ? -1 : 1), nyi) * nxi + wx : 0;
   const int oy = DIM == 3 ? ty + 1 : 0;
 
   R smax = 0, akey = -INFINITY;
@@ -257,11 +261,11 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
   const int hy = 2 * TY + tx * 2 + (ty == 0 ? 0 : 1);                     // y-ring slot
   // copy plane p of the own column (p <= q1 + 1) and of the second ring
   // (p <= q1) into ring slot p mod D; always commit a group
-  auto issue = [&](int64_t p) {
+  auto issue = [&](I p) {
     const int sl = (int)(p & (D - 1));
     if (p <= q1 + 1) {
       bool fy;
-      const int64_t o = plane_of(p, fy) * plane;
+      const I o = plane_of(p, fy) * plane;
 #pragma unroll
       for (int f = 0; f < NF; ++f) cp_async<sizeof(R)>(&sR[sl][f][tid], Uin + f * ncell + o + col);
       if (p <= q1) {
@@ -280,19 +284,19 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
   R Wm_prev[NF], D_prev[NF], H_prev[NF], yE_prev = 0, yEv_prev = 0;
 #pragma unroll
   for (int f = 0; f < NF; ++f) Wm_prev[f] = D_prev[f] = H_prev[f] = (R)0;
-  auto pidx = [&](int64_t q) {
+  auto pidx = [&](I q) {
     bool fy;
     return plane_of(q, fy) * plane;
   };
-  for (int64_t p = q0 - 2; p <= q0 + D - 4; ++p) issue(p);    // D - 1 planes ahead
+  for (I p = q0 - 2; p <= q0 + D - 4; ++p) issue(p);    // D - 1 planes ahead
 
-  for (int64_t q = q0 - 1; q <= q1; ++q) {
+  for (I q = q0 - 1; q <= q1; ++q) {
     // a. planes q-1, q, q+1 of the own column and plane q's second ring have
     //    landed; publish plane q
     cp_async_wait<D - 4>();
     const int sm = (int)((q - 1) & (D - 1)), s0 = (int)(q & (D - 1)), sp = (int)((q + 1) & (D - 1));
     bool fym, fy0, fyp;
-    const int64_t jq = plane_of(q, fy0);
+    const I jq = plane_of(q, fy0);
     plane_of(q - 1, fym);
     plane_of(q + 1, fyp);
 #pragma unroll
@@ -421,7 +425,7 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
         if constexpr (PP == 3) pulse_state_ps<NF>(kp, sc.t + sc.dt, un);
         else pulse_state<R, NF>(kp, sc.t + sc.dt, un);
       }
-      const int64_t o = pidx(q - 1) + col;
+      const I o = pidx(q - 1) + col;
 #pragma unroll
       for (int f = 0; f < NF; ++f) Uout[f * ncell + o] = un[f];
       if constexpr (PP == 3) {

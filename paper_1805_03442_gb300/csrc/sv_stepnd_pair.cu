@@ -86,26 +86,31 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
   const int seg = blockIdx.x % nseg;
   const int tile = blockIdx.x / nseg;
   const int tile_x = tile % tiles_x, tile_y = tile / tiles_x;
-  const int64_t gx = (int64_t)tile_x * (TX - 2) - 1 + tx;
-  const int64_t gy = DIM == 3 ? (int64_t)tile_y * (TY - 2) - 1 + ty : 0;
-  const int64_t M = DIM == 3 ? nz : ny;                     // planes
-  const int64_t plane = DIM == 3 ? nx * ny : nx;            // cells per plane
-  const int64_t ncell = plane * M;
-  const int64_t q0 = seg * M / nseg, q1 = (seg + 1) * M / nseg;
-  const bool interior = tx >= 1 && tx <= TX - 2 && gx < nx &&
-                        (DIM == 2 || (ty >= 1 && ty <= TY - 2 && gy < ny));
+  // Cell and field offsets in 32 bits: the launch admits grids whose fields
+  // hold fewer than 2^31 values in all (stepnd_launch), and 64-bit offsets
+  // cost the issue-bound kernel a tenth of its instructions.
+  using I = int;
+  const I gx = (I)tile_x * (TX - 2) - 1 + tx;
+  const I gy = DIM == 3 ? (I)tile_y * (TY - 2) - 1 + ty : 0;
+  const I M = (I)(DIM == 3 ? nz : ny);                      // planes
+  const I plane = (I)(DIM == 3 ? nx * ny : nx);             // cells per plane
+  const I ncell = plane * M;
+  const I q0 = (I)((int64_t)seg * M / nseg), q1 = (I)((int64_t)(seg + 1) * M / nseg);
+  const I nxi = (I)nx, nyi = (I)ny;
+  const bool interior = tx >= 1 && tx <= TX - 2 && gx < nxi &&
+                        (DIM == 2 || (ty >= 1 && ty <= TY - 2 && gy < nyi));
   bool fx_own = false, fx_rx = false;
-  const int64_t wx = BND ? map_axis(gx, nx, kp.bc_lo, kp.bc_hi, fx_own) : wrap(gx, nx);
-  const int64_t wy = DIM == 3 ? wrap(gy, ny) : 0;
-  const int64_t col = DIM == 3 ? wy * nx + wx : wx;
+  const I wx = BND ? map_axis(gx, nxi, kp.bc_lo, kp.bc_hi, fx_own) : wrap(gx, nxi);
+  const I wy = DIM == 3 ? wrap(gy, nyi) : 0;
+  const I col = DIM == 3 ? wy * nxi + wx : wx;
   const bool ringx = (tx == 0) || (tx == TX - 1);
-  const int64_t col_rx = (DIM == 3 ? wy * nx : 0) +
-                         (BND ? map_axis(gx + (tx == 0 ? -1 : 1), nx, kp.bc_lo, kp.bc_hi, fx_rx)
-                              : wrap(gx + (tx == 0 ? -1 : 1), nx));
+  const I col_rx = (DIM == 3 ? wy * nxi : 0) +
+                   (BND ? map_axis(gx + (tx == 0 ? -1 : 1), nxi, kp.bc_lo, kp.bc_hi, fx_rx)
+                        : wrap(gx + (tx == 0 ? -1 : 1), nxi));
   const bool ringy = DIM == 3 && ((ty == 0) || (ty == TY - 1));
-  const int64_t col_ry = DIM == 3 ? wrap(gy + (ty == 0 ? -1 : 1), ny) * nx + wx : 0;
+  const I col_ry = DIM == 3 ? wrap(gy + (ty == 0 ? -1 : 1), nyi) * nxi + wx : 0;
   const int oy = DIM == 3 ? ty + 1 : 0;
-  auto plane_of = [&](int64_t p, bool& fy) -> int64_t {
+  auto plane_of = [&](I p, bool& fy) -> I {
     if (!BND) {
       fy = false;
       return wrap(p, M);
@@ -114,7 +119,7 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
   };
   const bool medium = BND && kp.act_lo != nullptr;
   const bool pulses = BND && kp.pul_lo != nullptr;
-  auto active = [&](int64_t jrow) {
+  auto active = [&](I jrow) {
     return !medium || (wx >= __ldg(kp.act_lo + jrow) && wx < __ldg(kp.act_hi + jrow));
   };
 
@@ -126,11 +131,11 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
   const int hy = 2 * TY + tx * 2 + (ty == 0 ? 0 : 1);
   // copy plane p of the own column (p <= q1 + 3) and of the second ring
   // (p <= q1 + 2) into ring slot p mod D; always commit a group
-  auto issue = [&](int64_t p) {
+  auto issue = [&](I p) {
     const int sl = (int)(p & (D - 1));
     if (p <= q1 + 3) {
       bool fy;
-      const int64_t o = plane_of(p, fy) * plane;
+      const I o = plane_of(p, fy) * plane;
 #pragma unroll
       for (int f = 0; f < NF; ++f) cp_async<4>(&sR[sl][f][tid], Uin + f * ncell + o + col);
       if (p <= q1 + 2) {
@@ -145,7 +150,7 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
     cp_async_commit();
   };
   // the column's state at position p, wall ghosts with their momenta reversed
-  auto column = [&](int64_t p, float (&u)[NF]) {
+  auto column = [&](I p, float (&u)[NF]) {
     bool fy;
     plane_of(p, fy);
     const int sl = (int)(p & (D - 1));
@@ -168,9 +173,9 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
   for (int f = 0; f < NF; ++f) H_prev[f] = D_prev[f] = pk::splat(0.0f);
 
   // invariant at the top of iteration q: planes up to q + 3 issued
-  for (int64_t p = q0 - 3; p <= q0 + 1; ++p) issue(p);
+  for (I p = q0 - 3; p <= q0 + 1; ++p) issue(p);
 
-  for (int64_t q = q0 - 2; q - 2 < q1; q += 2) {
+  for (I q = q0 - 2; q - 2 < q1; q += 2) {
     // a. planes q-1 .. q+2 of the own column and q, q+1 of the second ring
     //    have landed; publish planes q and q+1
     cp_async_wait<1>();
@@ -180,7 +185,7 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
     column(q + 1, u1);
     column(q + 2, u2);
     bool fy0, fy1;
-    const int64_t j0 = plane_of(q, fy0), j1 = plane_of(q + 1, fy1);
+    const I j0 = plane_of(q, fy0), j1 = plane_of(q + 1, fy1);
     const int s0 = (int)(q & (D - 1)), s1 = (int)((q + 1) & (D - 1));
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -361,7 +366,7 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
         }
       }
       bool fy;
-      const int64_t oa = plane_of(q - 2, fy) * plane + col, ob = plane_of(q - 1, fy) * plane + col;
+      const I oa = plane_of(q - 2, fy) * plane + col, ob = plane_of(q - 1, fy) * plane + col;
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         Uout[f * ncell + oa] = Nw[f].x;
