@@ -41,10 +41,30 @@ L2_FLUSH_BYTES = 256 << 20
 # workload, precision and launch configuration; other lines report null.
 TRAFFIC_1D_FP32_N22 = 86.8e6
 
+# FP64 flops one updated cell costs in the FP64 step kernels (2 DFMA + DMUL + DADD, ncu
+# warp-instruction counts x 32 lanes): step1d_kernel at N = 2^22, stepnd_kernel at 2048^2 and
+# 128^3 (the 3D figure includes the tile halo's 18 % of redundant work).  These kernels are bound
+# by GB300's FP64 pipe (ncu: 86-87 % of its peak busy), so FP64 lines report an "alu" roofline.
+FP64_FLOPS_PER_CELL = {1: 681.4, 2: 1066.6, 3: 2314.9}
+# FP64 rate of one GB300: 2 FMA lanes per SM per clock (ncu: one warp-wide FP64 instruction per
+# SM every 16 cycles at full pipe) x 2 flops x 152 SMs x 2.07 GHz = 1.259 TFLOP/s
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
+
 # --precision names -> sv_params.precision (SV_FP32, SV_FP64, SV_FP32_P64,
 # SV_FP32_PC, SV_FP32_PS of include/sv.h) and the arithmetic type reported as "dtype"
 PRECISIONS = {"fp32": 0, "fp64": 1, "fp32_p64": 2, "fp32_pc": 3, "fp32_ps": 4}
 DTYPES = {"fp32": "f32", "fp64": "f64", "fp32_p64": "f32", "fp32_pc": "f32", "fp32_ps": "f32"}
+
+
+def fp64_roofline(dim: int, ncell: int, step_s: float, hbm_frac: float) -> dict:
+    """The FP64 step as an ALU-bound kernel: FP64 flops per launch over the
+    GB300's FP64 rate (FP64_FLOPS_PER_CELL, FP64_PEAK_TFLOPS)."""
+    flops = FP64_FLOPS_PER_CELL[dim] * ncell
+    achieved = flops / step_s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+            "peak_src": "derived FP64 rate: 2 FMA lanes/SM/clk x 2 flops x 152 SMs x 2.07 GHz",
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "flops_per_launch": flops, "hbm_frac": hbm_frac}
 
 
 def workload(n_cells: int, gamma: float, Ck: float, S: float):
@@ -492,6 +512,8 @@ def run_ours(args):
                                                          and "512-cell" in tuned["config"])
                                  else None),
                      "alg_bytes_per_launch": alg_bytes},
+        **({"roofline": fp64_roofline(len(dims), ncell, step_s, achieved / pk["hbm_gbs"])}
+           if args.precision == "fp64" else {}),
         "e2e": {"value": ws * ncell * e2e_steps / e2e_t, "unit": METRIC,
                 "h2d_bytes_per_step": int(host_in.numel() * 8),
                 "d2h_bytes_per_step": int(host_out.numel() * 8)},
