@@ -34,12 +34,24 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s"
 L2_FLUSH_BYTES = 256 << 20
 
-# DRAM bytes (read + write) of one launch of the 1D FP32 step kernel at N = 2^22
-# (the 512-cell block-tile configuration of tile1d_kernel), from one ncu capture
-# of the current kernel (67.2 MB read + 19.6 MB written during the launch; the
-# remaining writes are still dirty in L2 when it ends).  Only valid for that
-# workload, precision and launch configuration; other lines report null.
-TRAFFIC_1D_FP32_N22 = 86.8e6
+# DRAM bytes (read + write) of one launch of the 1D FP32 step at N = 2^22, per launch
+# configuration (a substring of its description), from one ncu capture of the current kernels:
+# the block tiles read the state once (67.2 MB) and write part of it back during the launch
+# (the rest is still dirty in L2 when it ends); the sliding warps re-read their chunk halos.
+# Only valid for that workload and precision; other lines, and configurations without a
+# capture, report null.
+TRAFFIC_1D_FP32_N22 = {
+    "512-cell block tiles, 2 cells per thread, 78 registers, 3 blocks/SM": 86.8e6,
+    "512-cell block tiles, 2 cells per thread, 2 blocks/SM": 87.2e6,
+    "512-cell block tiles, 2 cells per thread, 64 registers, 4 blocks/SM": 86.5e6,
+    "warps sliding over 64-cell chunks": 91.7e6,
+}
+
+
+def traffic_of(workload: str, ncell: int, precision: str, config: str):
+    if workload != "1d" or ncell != 1 << 22 or precision != "fp32":
+        return None
+    return next((v for k, v in TRAFFIC_1D_FP32_N22.items() if k in config), None)
 
 # FP64 flops one updated cell costs in the FP64 step kernels (2 DFMA + DMUL + DADD, ncu
 # warp-instruction counts x 32 lanes): step1d_kernel at N = 2^22, stepnd_kernel at 2048^2 and
@@ -438,7 +450,12 @@ def run_ours(args):
     # launch configuration from the autotuner (timed on the initial state, which
     # it restores), outside the timed region
     from paper_1805_03442_gb300 import tune
-    tuned = tune.tune_solver(solver, tune.solver_key(P, dims), tune.device_name())
+    if args.config >= 0:                     # a configuration named on the command line
+        solver.set_config(args.config)
+        tuned = {"config": solver.configs()[args.config], "index": args.config, "us": None,
+                 "cached": False}
+    else:
+        tuned = tune.tune_solver(solver, tune.solver_key(P, dims), tune.device_name())
     torch.cuda.synchronize()
     for _ in range(args.warmup):
         with torch.cuda.stream(stream):
@@ -507,10 +524,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
                      "peak_src": f"{pk['src']} hbm_gbs (burst copy)", "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"],
-                     "traffic": (TRAFFIC_1D_FP32_N22 if (args.workload == "1d" and ncell == 1 << 22
-                                                         and args.precision == "fp32"
-                                                         and "512-cell" in tuned["config"])
-                                 else None),
+                     "traffic": traffic_of(args.workload, ncell, args.precision, tuned["config"]),
                      "alg_bytes_per_launch": alg_bytes},
         **({"roofline": fp64_roofline(len(dims), ncell, step_s, achieved / pk["hbm_gbs"])}
            if args.precision == "fp64" else {}),
@@ -843,6 +857,8 @@ def main():
     ap.add_argument("--subset", type=int, default=64, help="looped comparison subset of the sweep")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", type=int, default=-1,
+                    help="launch configuration index of the grid workloads (default: autotuner)")
     ap.add_argument("--err-steps", type=int, default=0,
                     help="steps of the per-field error run against FP64 (0: workload default, "
                          "-1: skip)")
