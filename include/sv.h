@@ -182,9 +182,9 @@ int sv_get_launch(sv_solver* s, int* mode);
  * in a few launch configurations that compute bitwise the same states and
  * differ only in speed:
  *   1D float MUSCL-Hancock, >= 4096 cells: 512-cell block tiles at a register
- *     budget of 3 blocks/SM (default) or 2 blocks/SM, 1024-cell tiles with two
- *     cell pairs per thread, or warps sliding over 64-cell chunks (the kernel
- *     of every other 1D solver, its only config);
+ *     budget of 3 blocks/SM (default), 2 or 4 blocks/SM, 1024-cell tiles with
+ *     two cell pairs per thread, or warps sliding over 64-cell chunks (the
+ *     kernel of every other 1D solver, its only config);
  *   2D / 3D: planes per block along the marching axis, 64 / 128 / 256 / 512.
  * sv_autotune times each configuration on the solver's current state and
  * keeps the fastest; the state, time and status are restored afterwards.
@@ -209,7 +209,11 @@ int sv_set_config(sv_solver* s, int index);
    (may be NULL) receives its index; us_per_step (may be NULL, else
    sv_num_configs entries) the microseconds per step of each configuration,
    +inf where the trial stopped early (t_end reached or a non-physical
-   state).  Synchronous. */
+   state).  steps < 0 times -steps launches one by one, each after a write
+   of a 256 MiB scratch buffer (allocated for the call) that evicts the state
+   from L2: the conditions of a measurement that flushes L2 between steps,
+   where back-to-back steps find part of the state still in L2.
+   Synchronous. */
 int sv_autotune(sv_solver* s, int steps, int* best, double* us_per_step);
 
 /* Advance until t_end, the last step clamped to land on t_end, or until

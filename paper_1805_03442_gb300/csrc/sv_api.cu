@@ -516,6 +516,8 @@ int sv_set_config(sv_solver* s, int index) {
 }
 
 int sv_autotune(sv_solver* s, int steps, int* best, double* us_per_step) {
+  const bool cold = steps < 0;
+  if (cold) steps = -steps;
   if (!s || steps < 1) return SV_EINVAL;
   const int ncfg = (int)s->cfgs.size();
   const size_t count = (size_t)s->nf * (size_t)s->ncell;
@@ -539,6 +541,14 @@ int sv_autotune(sv_solver* s, int steps, int* best, double* us_per_step) {
     if (e0) cudaEventDestroy(e0);
     return SV_ECUDA;
   }
+  // cold trials: an L2-sized write before every timed launch
+  constexpr size_t kFlushBytes = size_t(256) << 20;
+  void* flush = nullptr;
+  if (cold && cudaMalloc(&flush, kFlushBytes) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return SV_ENOMEM;
+  }
   const int warm = 2;
   const int start = s->config;
   int pick = start, rc = SV_OK;
@@ -548,15 +558,29 @@ int sv_autotune(sv_solver* s, int steps, int* best, double* us_per_step) {
     rc = apply_config(s, c);
     for (int i = 0; i < warm && rc == SV_OK; ++i)
       if (launch_step(s, s->stream) != cudaSuccess) rc = SV_ECUDA;
-    if (rc == SV_OK && cudaEventRecord(e0, s->stream) != cudaSuccess) rc = SV_ECUDA;
-    for (int i = 0; i < steps && rc == SV_OK; ++i)
-      if (launch_step(s, s->stream) != cudaSuccess) rc = SV_ECUDA;
-    if (rc == SV_OK && (cudaEventRecord(e1, s->stream) != cudaSuccess ||
-                        cudaEventSynchronize(e1) != cudaSuccess))
-      rc = SV_ECUDA;
+    float ms = 0.0f;
+    if (!cold) {
+      if (rc == SV_OK && cudaEventRecord(e0, s->stream) != cudaSuccess) rc = SV_ECUDA;
+      for (int i = 0; i < steps && rc == SV_OK; ++i)
+        if (launch_step(s, s->stream) != cudaSuccess) rc = SV_ECUDA;
+      if (rc == SV_OK && (cudaEventRecord(e1, s->stream) != cudaSuccess ||
+                          cudaEventSynchronize(e1) != cudaSuccess ||
+                          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = SV_ECUDA;
+    } else {
+      for (int i = 0; i < steps && rc == SV_OK; ++i) {
+        float one = 0.0f;
+        if (cudaMemsetAsync(flush, i & 0xff, kFlushBytes, s->stream) != cudaSuccess ||
+            cudaEventRecord(e0, s->stream) != cudaSuccess ||
+            launch_step(s, s->stream) != cudaSuccess ||
+            cudaEventRecord(e1, s->stream) != cudaSuccess ||
+            cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&one, e0, e1) != cudaSuccess)
+          rc = SV_ECUDA;
+        ms += one;
+      }
+    }
     if (rc == SV_OK) {
-      float ms = 0.0f;
-      if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = SV_ECUDA;
       // a trial whose steps stopped (t_end reached, non-physical state) timed
       // nothing useful
       if (rc == SV_OK) rc = read_ctl(s);
@@ -573,6 +597,7 @@ int sv_autotune(sv_solver* s, int steps, int* best, double* us_per_step) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (flush) cudaFree(flush);
   const int ra = apply_config(s, rc == SV_OK ? pick : start);
   if (rc == SV_OK) rc = ra;
   if (best) *best = s->config;

@@ -370,14 +370,15 @@ class Solver:
     def set_config(self, index: int):
         _check(lib().sv_set_config(self._h, int(index)), "sv_set_config")
 
-    def autotune(self, steps: int = 10) -> tuple[int, list[float]]:
+    def autotune(self, steps: int = 10, cold: bool = False) -> tuple[int, list[float]]:
         """Time every configuration on the current state (restored after each
-        trial) and keep the fastest.  Returns (index, microseconds per step of
-        each configuration)."""
+        trial) and keep the fastest; cold: each timed step after an L2-evicting
+        write.  Returns (index, microseconds per step of each configuration)."""
         n = len(self.configs())
         us = (ctypes.c_double * n)()
         best = ctypes.c_int()
-        _check(lib().sv_autotune(self._h, int(steps), ctypes.byref(best), us), "sv_autotune")
+        k = -int(steps) if cold else int(steps)
+        _check(lib().sv_autotune(self._h, k, ctypes.byref(best), us), "sv_autotune")
         return best.value, list(us)
 
     def time(self) -> tuple[float, int]:

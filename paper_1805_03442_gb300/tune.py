@@ -86,11 +86,15 @@ class Cache:
 
 
 def tune_solver(solver, key: str, device: str, cache: Cache | None = None, steps: int = 10,
-                force: bool = False) -> dict:
+                force: bool = False, cold: bool = False) -> dict:
     """Give `solver` the cached configuration of its class, or time all of its
-    configurations (``solver.autotune``) and cache the fastest.  Returns
+    configurations (``solver.autotune``) and cache the fastest.  cold: time
+    each step after an L2-evicting write (its own cache entry, key + "/cold"),
+    for runs measured that way.  Returns
     ``{"config": description, "index": i, "us": [...], "cached": bool}``."""
     cache = cache or Cache()
+    if cold:
+        key = key + "/cold"
     descs = solver.configs()
     hit = None if force else cache.get(device, key)
     if hit is not None and hit.get("config") in descs:
@@ -100,7 +104,7 @@ def tune_solver(solver, key: str, device: str, cache: Cache | None = None, steps
     if len(descs) == 1:
         solver.set_config(0)
         return {"config": descs[0], "index": 0, "us": None, "cached": False}
-    best, us = solver.autotune(steps)
+    best, us = solver.autotune(steps, cold=True) if cold else solver.autotune(steps)
     cache.put(device, key, descs[best], us)
     return {"config": descs[best], "index": best, "us": us, "cached": False}
 

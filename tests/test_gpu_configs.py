@@ -118,6 +118,24 @@ def test_autotune_restores_state(sv, n):
     assert np.array_equal(U1, U2) and t1 == t2
 
 
+def test_cold_autotune_restores_state(sv):
+    """Trials with an L2-evicting write before every timed step leave the
+    state, time and step count exactly as they were, and time every
+    configuration."""
+    N = 1 << 20
+    P = sv.Params(precision=sv.FP32)
+    with sv.Solver(P, (N,), None) as s:
+        s.write_state(wave_1d(N, seed=5), t=0.25)
+        s.step(2)
+        before, tb = s.read_state()
+        kb = s.time()[1]
+        best, us = s.autotune(steps=3, cold=True)
+        after, ta = s.read_state()
+        assert np.array_equal(before, after) and ta == tb and s.time()[1] == kb
+        assert s.status() == 0 and s.config == best
+        assert len(us) == len(s.configs()) and all(np.isfinite(us)) and us[best] == min(us)
+
+
 def test_autotune_stopped_trials(sv):
     """A solver whose next dt is 0 (run ended) times nothing: every entry is
     +inf and the configuration stays."""

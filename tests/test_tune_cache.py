@@ -9,8 +9,9 @@ from paper_1805_03442_gb300.sv import Params, FP64, VANLEER
 
 
 class FakeSolver:
-    def __init__(self, descs, times):
+    def __init__(self, descs, times, cold_times=None):
         self.descs, self.times = descs, times
+        self.cold_times = cold_times or times
         self.config, self.tuned = 0, 0
 
     def configs(self):
@@ -20,11 +21,13 @@ class FakeSolver:
         assert 0 <= i < len(self.descs)
         self.config = i
 
-    def autotune(self, steps):
+    def autotune(self, steps, cold=False):
         self.tuned += 1
-        best = min(range(len(self.times)), key=lambda i: self.times[i])
+        self.cold = cold
+        times = self.cold_times if cold else self.times
+        best = min(range(len(times)), key=lambda i: times[i])
         self.config = best
-        return best, list(self.times)
+        return best, list(times)
 
 
 class FakeBatch:
@@ -137,3 +140,20 @@ def test_batch_chooser(tmp_path):
     log.clear()
     r2 = tune.tune_batch(lambda: FakeBatch(log), "bk", "dev", tune.Cache(str(path)))
     assert r2["cached"] and r2["index"] == 1 and not log
+
+
+def test_cold_tuning_has_its_own_entry(tmp_path):
+    """Tuning with L2 flushed before every step (the benchmark's conditions) is
+    cached apart from back-to-back tuning, and each keeps its own pick."""
+    path = tmp_path / "c.json"
+    descs = ["tiles", "sliding"]
+    s = FakeSolver(descs, [2.0, 1.0], cold_times=[1.0, 2.0])
+    warm = tune.tune_solver(s, "k", "dev", tune.Cache(str(path)))
+    assert warm["config"] == "sliding" and not s.cold
+    cold = tune.tune_solver(s, "k", "dev", tune.Cache(str(path)), cold=True)
+    assert cold["config"] == "tiles" and s.cold and not cold["cached"]
+    data = json.loads(path.read_text())["dev"]
+    assert data["k"]["config"] == "sliding" and data["k/cold"]["config"] == "tiles"
+    s2 = FakeSolver(descs, [5.0, 5.0])
+    assert tune.tune_solver(s2, "k", "dev", tune.Cache(str(path)), cold=True)["config"] == "tiles"
+    assert s2.tuned == 0
