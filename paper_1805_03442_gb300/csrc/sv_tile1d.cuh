@@ -218,8 +218,9 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
 // per SM (78 registers, 24 warps per SM), 4 (64 registers, 32 warps, a few
 // bytes of spills) or 2 (its natural ~94 registers, 16 warps), or two pairs
 // per thread (1024-cell tiles: half the barriers and exchanges per cell, two
-// independent chains) at 2 blocks per SM.  (Smaller blocks at the natural
-// register count, 192 threads x 3 and 160 threads x 4, measured 4-5% slower.)
+// independent chains) at 2 blocks per SM.  (Other block sizes at the natural
+// register count, 192 threads x 3, 160 threads x 4 and 320 threads x 2,
+// measured 4-6% slower.)
 // PP: the pressure policy (0 float, 2 compensated float) or the perturbation
 // layout (3).
 template <int PP, int LIM, int SRC>
