@@ -8,7 +8,7 @@ from dataclasses import dataclass, replace
 import numpy as np
 import pytest
 
-from gpu_util import need_gpu, oracle_params, rel_linf
+from gpu_util import assert_fp64_parity, need_gpu, oracle_params, rel_linf
 from oracle import dispersion as D
 from oracle import orc as O
 from paper_1805_03442_gb300 import inputs
@@ -213,3 +213,49 @@ def test_flags_are_per_run(sv):
     assert flags[1] & sv.FLAG_NONPHYS
     for i in (0, 2, 3):
         assert flags[i] in (0, sv.FLAG_MAXSTEPS)
+
+
+def test_batch_fp64_full_range_matches_oracle(sv):
+    """FP64 batch against the oracle at 1e-12 on 24 runs drawn from the whole
+    ranges of the stability sweep (N in [256, 16384], tau0 log-uniform down to
+    1e-3 where the source cap c_tau min tau sets dt, S up to 2, every eq. 6
+    exponent of either sign), van Leer, over each run's first ~20 steps: short
+    enough that the unstable draws have not yet amplified rounding noise."""
+    raw = inputs.sweep_runs(31, 20)
+    # and four draws from the corner of those ranges where the cap binds
+    # (coarse grids, tau0 near 1e-3)
+    raw += [replace(r, tau0=1e-3 * (1.0 + 0.1 * i))
+            for i, r in enumerate(inputs.sweep_runs(32, 4, n_lo=256, n_hi=320))]
+    P = sv.Params(precision=sv.FP64, limiter=1)
+    runs, states, params = [], [], []
+    shape = inputs.acoustic_shape(1.4)
+    for r in raw:
+        U0 = inputs.waves_1d(1.4, r.N, 1.0, inputs.equilibrium_primitive(0.1, r.S),
+                             [inputs.Mode(m=r.m, shape=shape, scale=1e-3)])
+        Po = oracle_params(P, S=r.S, tau0=r.tau0, tau_rho=r.tau_rho, tau_T=r.tau_T,
+                           Q_rho=r.Q_rho, Q_T=r.Q_T, I_rho=r.I_rho, I_T=r.I_T)
+        t_end = 20.5 * O.dt_cfl(Po, U0, r.N, 1.0 / r.N)
+        while O.run(Po, U0, r.N, 1.0 / r.N, t_end)[3] != 0:
+            t_end *= 0.5                     # the most unstable draw blows up within ~24 steps
+        runs.append(Run(n=r.N, t_end=t_end, S=r.S, tau0=r.tau0, tau_rho=r.tau_rho,
+                        tau_T=r.tau_T, Q_rho=r.Q_rho, Q_T=r.Q_T, I_rho=r.I_rho, I_T=r.I_T,
+                        m=r.m))
+        states.append(U0)
+        params.append(Po)
+    # the draws reach the regimes this test is for: a binding source cap and
+    # strongly unstable media (e-folding within a few wave periods)
+    capped = sum(O.dt_cfl(Po, U0, run.n, 1.0 / run.n)
+                 < 0.9 * O.dt_cfl(oracle_params(P, **{**Po.__dict__, "c_tau": 1e30}), U0, run.n,
+                                  1.0 / run.n)
+                 for Po, U0, run in zip(params, states, runs))
+    growth = [D.max_growth(Po, 2 * math.pi * run.m)[0] / (2 * math.pi * run.m * math.sqrt(1.4))
+              for Po, run in zip(params, runs)]
+    assert capped >= 3 and max(growth) > 0.2 and min(growth) < 0
+    with sv.Batch(P, runs, states) as b:
+        b.run()
+        for i, (run, U0, Po) in enumerate(zip(runs, states, params)):
+            U, t, k, f = b.read(i)
+            ref, tr, kr, rc = O.run(Po, U0, run.n, run.L / run.n, run.t_end)
+            assert rc == 0 and f == 0, (i, rc, f)
+            assert k == kr and t == tr, (i, k, kr, t, tr)
+            assert_fp64_parity(U, ref)

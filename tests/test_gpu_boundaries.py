@@ -8,7 +8,7 @@ import os
 import numpy as np
 import pytest
 
-from gpu_util import need_gpu, oracle_params, rel_linf
+from gpu_util import assert_fp64_parity, need_gpu, oracle_params, rel_linf
 from oracle import orc as O
 from paper_1805_03442_gb300 import inputs
 
@@ -48,7 +48,7 @@ def test_fp64_matches_oracle(sv, bc, N):
     for _ in range(3):
         ref, rc = O.step_bc1(Po, ref, N, h, O.dt_cfl(Po, ref, N, h), bc[0], bc[1])
         assert rc == 0
-    assert rel_linf(U, ref) <= 1e-12
+    assert_fp64_parity(U, ref)
 
 
 @pytest.mark.parametrize("bc", [(1, 1), (2, 2)])
@@ -101,6 +101,8 @@ def test_colliding_shocks(sv, prec):
     ref2, _, _, _ = O.run_bc1(Po, ref1, N, 1.0 / N, g["comparison_time"], 1, 1,
                               t0=g["collision_time"])
     if prec == "FP64":
-        assert rel_linf(U2, ref2) <= 1e-9
+        # through the strong shocks the oracle's own one-ulp sensitivity stays
+        # at 4e-14 (relative to max(|field|, 1)): the FP64 gate holds as is
+        assert_fp64_parity(U2, ref2)
     else:
         assert np.mean(np.abs(U2[0] - ref2[0])) <= 1e-3 * np.mean(ref2[0])

@@ -5,7 +5,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_util import need_gpu, oracle_params, rel_linf
+from gpu_util import assert_fp64_parity, need_gpu, oracle_params, rel_linf
 from oracle import dispersion as D
 from oracle import orc as O
 from paper_1805_03442_gb300 import inputs
@@ -39,7 +39,7 @@ def test_fp64_driven_matches_oracle(sv):
         U, t = s.read_state()
     ref, tr, kr, rc = O.run_driven(Po, U0, N, 1.0 / N, 0.1, O.drive(w, k, base, amp))
     assert rc == 0 and t == tr
-    assert rel_linf(U, ref) <= 1e-12
+    assert_fp64_parity(U, ref)
 
 
 @pytest.mark.parametrize("prec", ["FP64", "FP32"])

@@ -6,7 +6,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_util import need_gpu, oracle_params, rel_linf
+from gpu_util import assert_fp64_parity, need_gpu, oracle_params, rel_linf
 from oracle import dispersion as D
 from oracle import orc as O
 from paper_1805_03442_gb300 import inputs
@@ -37,7 +37,7 @@ def test_fp64_heun_matches_oracle(sv, N, params):
     for _ in range(3):
         ref, rc = O.step_heun(Po, ref, N, h, O.dt_cfl(Po, ref, N, h))
         assert rc == 0
-    assert rel_linf(U, ref) <= 1e-12
+    assert_fp64_parity(U, ref)
 
 
 def test_fp32_heun_one_step(sv):

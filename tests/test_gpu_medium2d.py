@@ -8,7 +8,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_util import need_gpu, oracle_params, rel_linf
+from gpu_util import assert_fp64_parity, need_gpu, oracle_params, rel_linf
 from oracle import orc as O
 from paper_1805_03442_gb300 import inputs
 
@@ -57,7 +57,7 @@ def test_fp64_boundaries_match_oracle(sv, bc, n):
     U, t, dts = gpu_steps(sv, P, U0, n, h, bc, 3)
     assert dts[0] == pytest.approx(O.dt_cfl(Po, U0, n, h), rel=1e-13)
     ref = oracle_steps(Po, U0, n, h, bc, dts)
-    assert rel_linf(U, ref) <= 1e-12
+    assert_fp64_parity(U, ref)
 
 
 @pytest.mark.parametrize("bc", BCS[:2])
@@ -92,7 +92,7 @@ def test_fp64_sector_problem_matches_oracle(sv, nx):
         U, t = s.read_state()
     ref, tr, kr, rcr = O.run2m(Po, U0, pb.nx, pb.ny, pb.h, 0.1, pb.bc, M)
     assert rc == 0 and rcr == 0 and k == kr and t == tr == 0.1
-    assert rel_linf(U, ref) <= 1e-12
+    assert_fp64_parity(U, ref)
     # the source has been pulsing: the state is no longer at rest
     assert np.max(np.abs(U[0] - 1.0)) > 1e-4
 

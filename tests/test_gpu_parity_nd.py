@@ -7,7 +7,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_util import need_gpu, oracle_params, rel_linf
+from gpu_util import assert_fp64_parity, need_gpu, oracle_params, rel_linf
 from oracle import orc as O
 from paper_1805_03442_gb300 import inputs
 
@@ -58,7 +58,7 @@ def test_fp64_matches_oracle(sv, n, params):
     ref_dt = O.dt_cfl(Po, U0, n, h)
     assert dts[0] == pytest.approx(ref_dt, rel=1e-13)
     ref = _oracle_steps(Po, U0, n, h, dts)
-    assert rel_linf(U, ref) <= 1e-12
+    assert_fp64_parity(U, ref)
 
 
 @pytest.mark.parametrize("limiter", [1, 2])
@@ -69,7 +69,7 @@ def test_fp64_other_limiters(sv, n, limiter):
     h = 1.0 / n[0]
     U0 = inputs.random_states(len(n), int(np.prod(n)), seed=4, smooth=True)
     U, _, dts = _gpu_steps(sv, P, U0, n, tuple(x * h for x in n), 2)
-    assert rel_linf(U, _oracle_steps(Po, U0, n, h, dts)) <= 1e-12
+    assert_fp64_parity(U, _oracle_steps(Po, U0, n, h, dts))
 
 
 @pytest.mark.parametrize("precision", ["FP32", "FP32_P64", "FP32_PC"])
