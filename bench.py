@@ -425,6 +425,116 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def timed_flushed_steps(solver, stream, flush, steps: int, warmup: int) -> list:
+    """Per-step seconds of `steps` single steps, each after an L2-evicting
+    write (outside its CUDA-event window), after `warmup` untimed steps."""
+    import torch
+    for _ in range(warmup):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        solver.step(1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+        solver.step(1)
+        with torch.cuda.stream(stream):
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) * 1e-3 for a, b in ev]
+
+
+def back_to_back(solver, stream, flush, steps: int, alg_bytes: int, hbm_gbs: float) -> dict:
+    """`steps` steps replayed back to back from the solver's CUDA graph with
+    no flush between them (one CUDA-event window after one L2-evicting write):
+    the write-back of each step's dirty lines is paid inside the window, and
+    part of each step's input is still in L2 from the step before."""
+    import torch
+    with torch.cuda.stream(stream):
+        flush.fill_(2.0)
+    solver.step(steps)                      # warm: the graph is built and replayed once
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        flush.fill_(3.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3 / steps
+    return {"value": solver.ncell / t, "unit": METRIC, "ms_per_step": 1e3 * t, "steps": steps,
+            "l2": "one flush before the window, none between steps",
+            "alg_gbs": alg_bytes / t / 1e9, "frac": alg_bytes / t / 1e9 / hbm_gbs}
+
+
+def precision_leg(sv, args, prec_name: str, U0, dims, L, stream, flush, pk: dict) -> dict:
+    """The default workload in another arithmetic policy, timed as the main
+    line (L2 flushed before each step): FP64 (roofline of the FP64 pipe,
+    measured by the library's probe, and one step against the oracle on
+    sampled cells) or a float pressure policy (HBM roofline, per-field error
+    against the FP64 kernels)."""
+    from paper_1805_03442_gb300 import tune
+    W = WORKLOADS[args.workload]
+    prec = PRECISIONS[prec_name]
+    P = sv.Params(precision=prec, **W["params"])
+    ncell = int(np.prod(dims))
+    with sv.Solver(P, dims, L, stream=stream) as s:
+        s.write_state(U0)
+        tuned = tune.tune_solver(s, tune.solver_key(P, dims), tune.device_name(), cold=True)
+        times = timed_flushed_steps(s, stream, flush, args.steps, args.warmup)
+        status = s.status()
+    step_s = sum(times) / len(times)
+    esize = 8 if prec == sv.FP64 else 4
+    alg = 2 * (len(dims) + 3) * esize * ncell
+    out = {"precision": prec_name, "value": ncell / step_s, "unit": METRIC,
+           "ms_per_step": 1e3 * step_s, "steps": len(times), "launch_config": tuned["config"],
+           "status_flags": status}
+    if prec == sv.FP64:
+        peak = sv.measure_fp64_peak(stream)
+        flops = FP64_FLOPS_PER_CELL[len(dims)] * ncell
+        out["roofline"] = {"bound": "alu", "achieved": flops / step_s / 1e12, "peak": peak,
+                           "peak_src": "measured: DFMA-chain probe of the library "
+                                       "(sv_measure_fp64_peak), this run",
+                           "unit": "TFLOP/s", "frac": flops / step_s / 1e12 / peak,
+                           "traffic": None, "flops_per_launch": flops,
+                           "hbm_frac": alg / step_s / 1e9 / pk["hbm_gbs"]}
+        out["error_vs_oracle"] = fp64_sampled_parity(sv, P, dims, L, U0)
+    else:
+        out["roofline"] = {"bound": "hbm", "achieved": alg / step_s / 1e9, "peak": pk["hbm_gbs"],
+                           "unit": "GB/s", "frac": alg / step_s / 1e9 / pk["hbm_gbs"],
+                           "traffic": None}
+        if args.err_steps >= 0:
+            out["error_vs_fp64"] = precision_error(sv, P, dims, L, U0,
+                                                   args.err_steps or W["err_steps"])
+    return out
+
+
+def fp64_sampled_parity(sv, P, dims, L, U0, nsample: int = 64) -> dict:
+    """One FP64 step of the workload against the oracle's one-cell evaluation
+    on sampled cells: max |gpu - oracle| / max(|field|, 1) over the sample."""
+    from oracle import orc as O
+    Po = O.Params(gamma=P.gamma, Ck=P.Ck, S=P.S, tau0=P.tau0, tau_rho=P.tau_rho, tau_T=P.tau_T,
+                  Q_rho=P.Q_rho, Q_T=P.Q_T, I_rho=P.I_rho, I_T=P.I_T, cfl=P.cfl, c_tau=P.c_tau,
+                  limiter=P.limiter)
+    ncell = int(np.prod(dims))
+    h = L[0] / dims[0]
+    with sv.Solver(P, dims, L) as s:
+        s.write_state(U0)
+        dt = s.dt()
+        s.step(1)
+        U, _ = s.read_state()
+    rng = np.random.default_rng(1)
+    idx = np.unique(np.concatenate([[0, 1, ncell - 1], rng.integers(0, ncell, nsample)]))
+    scale = np.maximum(np.max(np.abs(U0), axis=1), 1.0)
+    err = max(float(np.max(np.abs(U[:, i] - O.step_cell(Po, U0, dims, h, dt, int(i))) / scale))
+              for i in idx)
+    return {"max_rel": err, "cells": int(len(idx)), "dt_rel": abs(dt - O.dt_cfl(Po, U0, dims, h))
+            / O.dt_cfl(Po, U0, dims, h), "norm": "max |gpu - oracle| / max(|field|, 1)"}
+
+
 def run_ours(args):
     import torch
     rank, ws, dist = dist_init()
@@ -458,28 +568,14 @@ def run_ours(args):
     else:
         tuned = tune.tune_solver(solver, tune.solver_key(P, dims), tune.device_name(), cold=True)
     torch.cuda.synchronize()
-    for _ in range(args.warmup):
-        with torch.cuda.stream(stream):
-            flush.fill_(1.0)
-        solver.step(1)
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+    timed_flushed_steps(solver, stream, flush, 0, args.warmup)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
-        for i in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(float(i))
-                ev[i][0].record(stream)
-            solver.step(1)
-            with torch.cuda.stream(stream):
-                ev[i][1].record(stream)
-        torch.cuda.synchronize()
+        times = timed_flushed_steps(solver, stream, flush, args.steps, 0)
     if dist is not None:
         dist.barrier()
-    times = [a.elapsed_time(b) * 1e-3 for a, b in ev]
     tot, units = aggregate(sum(times), float(ncell * args.steps), dist, device="cuda")
     status = solver.status()
     t_sim, nsteps = solver.time()
@@ -499,6 +595,10 @@ def run_ours(args):
         solver.step(1)
         solver.read_state_ptr(host_out.data_ptr())
     e2e_t = time.perf_counter() - t0
+    pk = peaks()
+    esize_alg = 2 * nf * esize * ncell
+    extras = ws == 1 and not args.no_extras and args.workload == "1d" and args.precision == "fp32"
+    b2b = back_to_back(solver, stream, flush, 64, esize_alg, pk["hbm_gbs"]) if extras else None
     solver.close()
 
     if rank != 0:
@@ -506,7 +606,6 @@ def run_ours(args):
     err = None
     if prec != sv.FP64 and args.err_steps >= 0:
         err = precision_error(sv, P, dims, L, U0, args.err_steps or W["err_steps"])
-    pk = peaks()
     step_s = tot / args.steps
     alg_bytes = 2 * nf * esize * ncell             # read + write every conserved field once
     achieved = alg_bytes / step_s / 1e9
@@ -538,6 +637,16 @@ def run_ours(args):
     }
     if err is not None:
         line["error_vs_fp64"] = err
+    if extras:
+        # the rest of the metric on the same box: the same step back to back,
+        # the FP64 kernels, the compensated-float pressure policy (the float
+        # stand-in for the FP64 pressure island) and the batched sweep
+        line["back_to_back"] = b2b
+        line["fp64"] = precision_leg(sv, args, "fp64", U0, dims, L, stream, flush, pk)
+        line["fp32_pc"] = precision_leg(sv, args, "fp32_pc", U0, dims, L, stream, flush, pk)
+        del flush
+        torch.cuda.empty_cache()
+        line["sweep"] = sweep_summary(sweep_measure(args, stream, reps=1))
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, args, budget_s=args.cpu_budget)
     print(json.dumps(line), flush=True)
@@ -600,9 +709,10 @@ class _R:
         self.n = r.N
 
 
-def run_sweep(args):
-    """Batched sweep: one persistent launch for all runs (runs/s), next to the
-    same runs looped through single 1D solvers on a stratified subset."""
+def sweep_measure(args, stream, reps: int = 2) -> dict:
+    """Batched sweep: one persistent launch for all runs (the best of `reps`
+    timed runs), next to the same runs looped through single 1D solvers on a
+    stratified subset.  Returns the raw figures."""
     import torch
     from paper_1805_03442_gb300 import sv
     from paper_1805_03442_gb300.build import build
@@ -611,7 +721,6 @@ def run_sweep(args):
     runs = [_R(r) for r in runs]
     prec = PRECISIONS[args.precision]
     P = sv.Params(precision=prec)
-    stream = torch.cuda.Stream()
     # per-run step cap: about twice the expected CFL step count plus the tau bound
     max_steps = 30 * max(r.n for r in runs) + 20000
     # launch configuration (block size per run) from the autotuner: a strided
@@ -632,7 +741,7 @@ def run_sweep(args):
     b.set_config(tuned["index"])
     times = []
     with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
-        for rep in range(max(1, min(args.steps, 2))):
+        for rep in range(max(1, reps)):
             if rep:
                 b.reset(states)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -643,16 +752,25 @@ def run_sweep(args):
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1) * 1e-3)
     t_batch = min(times)
-    cells = 0
+    cells = cells_done = 0
     flags = {}
+    completed = blown = capped = 0
     for i, r in enumerate(runs):
         _, t, k, f = b.read(i, state=False)
         cells += k * r.n
         flags[f] = flags.get(f, 0) + 1
+        if f == 0 and t == r.t_end:
+            completed += 1
+            cells_done += k * r.n
+        elif f & (sv.FLAG_NONPHYS | sv.FLAG_DT):
+            blown += 1
+        elif f & sv.FLAG_MAXSTEPS:
+            capped += 1
     b.close()
     # looped single runs vs the batch on the same stratified subset
     order = sorted(range(len(runs)), key=lambda i: -(runs[i].n ** 2) * runs[i].t_end)
     sub = order[:: max(1, len(runs) // args.subset)][: args.subset]
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in sub:
         r = runs[i]
@@ -661,6 +779,7 @@ def run_sweep(args):
         with sv.Solver(Pi, (r.n,), (1.0,), stream=stream) as s:
             s.write_state(states[i])
             s.run_to(r.t_end, max_steps=max_steps, check=False)
+    torch.cuda.synchronize()
     t_loop = time.perf_counter() - t0
     sb = sv.Batch(P, [runs[i] for i in sub], [states[i] for i in sub], log_cap=64, stream=stream,
                   max_steps=max_steps)
@@ -671,20 +790,47 @@ def run_sweep(args):
     sb.sync()
     t_sub = time.perf_counter() - t0
     sb.close()
-    line = {"metric": "batched sweep runs/s", "value": len(runs) / t_batch, "unit": "runs/s",
-            "n_gpus": 1, "steps": len(times), "warmup": 0, "ms_per_step": 1e3 * t_batch,
+    return {"runs": len(runs), "t_batch": t_batch, "reps": len(times), "cells": cells,
+            "cells_completed": cells_done, "completed": completed, "blown_up": blown,
+            "capped": capped, "flags": {str(k): v for k, v in sorted(flags.items())},
+            "tuned": tuned, "sub": len(sub), "t_loop": t_loop, "t_sub": t_sub,
+            "clocks": getattr(clk, "result", None)}
+
+
+def sweep_summary(m: dict) -> dict:
+    """The sweep's figures for a JSON line: runs/s over all runs and over the
+    runs that reach their end time, cell-updates/s, the blown-up and
+    step-capped counts, and the batch against looped single runs."""
+    t = m["t_batch"]
+    return {"metric": "batched sweep runs/s", "runs_per_s": m["runs"] / t,
+            "completed_runs_per_s": m["completed"] / t, "cell_updates_per_s": m["cells"] / t,
+            "completed_cell_updates_per_s": m["cells_completed"] / t, "seconds": t,
+            "runs": m["runs"], "completed": m["completed"], "blown_up": m["blown_up"],
+            "blown_up_frac": m["blown_up"] / m["runs"], "capped": m["capped"],
+            "launches": 1, "graph": "the persistent launch is replayed from a CUDA graph",
+            "launch_config": m["tuned"]["config"],
+            "vs_looped_subset": {"runs": m["sub"], "looped_single_runs_s": m["t_loop"],
+                                 "batched_s": m["t_sub"], "speedup": m["t_loop"] / m["t_sub"]}}
+
+
+def run_sweep(args):
+    """The sweep as its own line (runs/s), with the oracle's bounded sample."""
+    import torch
+    stream = torch.cuda.Stream()
+    m = sweep_measure(args, stream, reps=max(1, min(args.steps, 2)))
+    sm = sweep_summary(m)
+    line = {"metric": "batched sweep runs/s", "value": sm["runs_per_s"], "unit": "runs/s",
+            "n_gpus": 1, "steps": m["reps"], "warmup": 0, "ms_per_step": 1e3 * m["t_batch"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[args.precision], "data": "synthetic",
-            "config": {"workload": f"batched 1D stability sweep, {len(runs)} runs, N~U[256,16384], "
+            "config": {"workload": f"batched 1D stability sweep, {m['runs']} runs, N~U[256,16384], "
                                    "tau0 log-uniform [1e-3,1e1], S in [0,2], exponents in "
-                                   "[-2.5,1], m in 1..8, 5 periods", "runs": len(runs),
+                                   "[-2.5,1], m in 1..8, 5 periods", "runs": m["runs"],
                        "precision": args.precision,
-                       "launch_config": tuned["config"], "tuning_us": tuned["us"]},
-            "cell_updates_per_s": cells / t_batch, "cell_updates": cells,
-            "run_flags": {str(k): v for k, v in sorted(flags.items())},
-            "subset": {"runs": len(sub), "looped_single_runs_s": t_loop, "batched_s": t_sub,
-                       "speedup": t_loop / t_sub},
-            "gpu_launches": 2, "clocks": getattr(clk, "result", None)}
+                       "launch_config": m["tuned"]["config"], "tuning_us": m["tuned"]["us"]},
+            **{k: v for k, v in sm.items() if k not in ("metric", "runs_per_s")},
+            "cell_updates": m["cells"], "run_flags": m["flags"],
+            "gpu_launches": 2, "clocks": m["clocks"]}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_special("sweep", args, args.cpu_budget)
     print(json.dumps(line), flush=True)
@@ -858,6 +1004,9 @@ def main():
     ap.add_argument("--subset", type=int, default=64, help="looped comparison subset of the sweep")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default 1D line only: skip the back-to-back, FP64, compensated-pressure "
+                         "and sweep figures")
     ap.add_argument("--config", type=int, default=-1,
                     help="launch configuration index of the grid workloads (default: autotuner)")
     ap.add_argument("--err-steps", type=int, default=0,

@@ -177,6 +177,16 @@ int sv_set_launch(sv_solver* s, int mode);
    SV_LAUNCH_PERSISTENT; AUTO resolved). */
 int sv_get_launch(sv_solver* s, int* mode);
 
+/* Bound of the persistent loop's grid-barrier waits, for exercising its
+   failure path: every wait gives up after `polls` polls of the barrier
+   generation (or the ~2 s time limit, whichever comes first); 0 (the default)
+   restores the limit of 2^24 polls.  A wait that gives up raises
+   SV_FLAG_STALL and leaves the launch, so sv_step / sv_run_to end with
+   SV_ESTALL and the state is undefined until the next sv_write_state (which
+   also clears the flag).  Per-step launches do not wait and ignore it.
+   Errors: SV_EINVAL (null solver, polls < 0). */
+int sv_set_wait_limit(sv_solver* s, int polls);
+
 /* ------------------------------------------------------------------------
  * Launch configurations and the autotuner.  A solver's per-step kernel comes
  * in a few launch configurations that compute bitwise the same states and
@@ -312,11 +322,11 @@ int sv_batch_get_config(sv_batch* b, int* index, char* desc, size_t cap);
 
 /* ------------------------------------------------------------------------
  * Allocation-free 1D step.  The paper has no counterpart: this is a service
- * of the library for callers that cannot allocate device memory -- code that
- * runs while another framework captures a CUDA graph (where cudaMalloc is not
- * allowed), processes whose device memory comes from a fixed pool that
- * forbids allocation after start-up, and hosts that must not allocate on
- * their stepping path.  Such a caller owns the two state buffers; the small
+ * of the library for callers that cannot allocate device memory -- processes
+ * whose device memory is a fixed pool handed out at start-up and that forbid
+ * allocation afterwards, and hosts that must not allocate on their stepping
+ * path (a device allocation can synchronise the device and takes unbounded
+ * time).  Such a caller owns the two state buffers; the small
  * control block the fused kernel needs (time, dt, the eq.-16 reduction keys,
  * the block-completion ticket) lives in a file-scope static device array of
  * SV_NOALLOC_SCRATCH_BYTES bytes that every GPU loading libsv.so holds until
@@ -328,16 +338,19 @@ int sv_batch_get_config(sv_batch* b, int* index, char* desc, size_t cap);
 /* One MUSCL-Hancock step of a 1D periodic grid of n cells (length L) from the
    caller's device buffer U_in to the caller's device buffer U_out (each
    4 * n elements of float for SV_FP32 / SV_FP32_P64 / SV_FP32_PC or double for SV_FP64,
-   field-major rho, rho v, E, E_nu; they must not overlap), with dt from
-   eq. 16 (capped by c_tau * min tau) on U_in.  Same kernels and results as
-   sv_step on a solver holding U_in.  Allocates nothing and calls no
-   allocating routine.
+   field-major rho, rho v, E, E_nu; buffers sharing any byte return
+   SV_EINVAL), with dt from eq. 16 (capped by c_tau * min tau) on U_in.  The
+   same dt and, bit for bit, the same state as sv_step on a solver holding
+   U_in: it runs the sliding-warp kernel, whose per-cell arithmetic every 1D
+   kernel of the solver shares.  Allocates nothing and calls no allocating
+   routine.
    dt_used / flags (host pointers, each may be NULL) receive the dt taken and
    the SV_FLAG_* bits of the step; giving either makes the call wait for the
    stream, otherwise it is asynchronous on cuda_stream.
-   The first call on a device looks up the device address of the static
-   array (cudaGetSymbolAddress, with that device current): make that first
-   call before any stream capture.  Every call resets the control block it
+   The first call on a device (and the first with each precision, limiter
+   and source variant) looks up the device address of the static array
+   (cudaGetSymbolAddress, with that device current) and the step kernel's
+   launch grid; later calls reuse them.  Every call resets the control block it
    finds, since the array keeps the previous call's contents; calls that
    overlap on the GPU (other streams, other host threads) share that one
    array and race.  n beyond SV_NOALLOC_MAX_CELLS returns SV_ESIZE. */
@@ -388,6 +401,18 @@ int sv_set_drive(sv_solver* s, const sv_drive* d);
 
 /* Human-readable name of a status code. */
 const char* sv_strerror(int code);
+
+/* ------------------------------------------------------------------------
+ * Measurement utility (not part of the paper's method).  The FP64 step
+ * kernels are bound by the GPU's double-precision pipe rather than by HBM;
+ * this measures that pipe's throughput on the current device, the
+ * denominator of their roofline: independent DFMA chains (8 per thread, 4
+ * blocks of 256 threads per SM, an exact count of FMAs at 2 flops each), the
+ * best of three launches timed with CUDA events on cuda_stream, after one
+ * warm-up launch.  Writes TFLOP/s to *tflops (host pointer); synchronous.
+ * Errors: SV_EINVAL (null tflops), SV_ECUDA.
+ * ------------------------------------------------------------------------ */
+int sv_measure_fp64_peak(void* cuda_stream, double* tflops);
 
 #ifdef __cplusplus
 }

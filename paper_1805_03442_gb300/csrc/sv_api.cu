@@ -611,6 +611,12 @@ int sv_set_launch(sv_solver* s, int mode) {
   return SV_OK;
 }
 
+int sv_set_wait_limit(sv_solver* s, int polls) {
+  if (!s || polls < 0) return SV_EINVAL;
+  s->kp.stall_polls = polls;   // read by the persistent loop only, which is never captured
+  return SV_OK;
+}
+
 int sv_get_launch(sv_solver* s, int* mode) {
   if (!s || !mode) return SV_EINVAL;
   *mode = use_loop(s) ? SV_LAUNCH_PERSISTENT : SV_LAUNCH_PER_STEP;

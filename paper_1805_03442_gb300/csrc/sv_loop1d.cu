@@ -41,10 +41,11 @@ __device__ __forceinline__ uint64_t globaltimer() {
 }
 
 // Wait (one thread) until the barrier generation moves past gen0.  Returns
-// false if the wait ran out.
-__device__ bool wait_generation(Ctl* ctl, uint32_t gen0) {
+// false if the wait ran out: after `polls` polls (0: kStallIters) or kStallNs.
+__device__ bool wait_generation(Ctl* ctl, uint32_t gen0, int polls) {
   const uint64_t t0 = globaltimer();
-  for (uint32_t it = 0; it < kStallIters; ++it) {
+  const uint32_t limit = polls > 0 ? (uint32_t)polls : kStallIters;
+  for (uint32_t it = 0; it < limit; ++it) {
     if (ld_acquire(&ctl->gen) != gen0) {
       __threadfence();
       return true;
@@ -96,7 +97,7 @@ loop1d_kernel(const KParams kp, R* bufA, R* bufB, Ctl* ctl, int N, long long nma
         __threadfence();
         atomicAdd(&ctl->gen, 1u);
       } else {
-        ok = wait_generation(ctl, gen0);
+        ok = wait_generation(ctl, gen0, kp.stall_polls);
       }
       s_stop = ok ? 0 : 1;
     }

@@ -33,7 +33,7 @@ struct KParams {
   int qi_zero;   // 1: all Q and I exponents are zero (Q = I = Q0)
   int bc_lo, bc_hi;   // boundary conditions at x = 0 / x = Lx (BC_*)
   int bc_ylo, bc_yhi; // 2D: boundary conditions at y = 0 / y = Ly
-  int pad;
+  int stall_polls;     // persistent loop: polls before a grid-barrier wait gives up (0: default)
   // driven boundary wave: U = base + Re(amp e^{i (k x - omega t)})
   double drv_omega, drv_kre, drv_kim, drv_base[4], drv_are[4], drv_aim[4];
   // 2D medium map (device arrays of ny entries, null when unused): row j is

@@ -32,7 +32,7 @@ EXPORTS = ("sv_required_bytes", "sv_init", "sv_write_state", "sv_read_state", "s
            "sv_state_device", "sv_free", "sv_strerror", "sv_batch_required_bytes",
            "sv_batch_init", "sv_batch_reset", "sv_batch_run", "sv_batch_sync", "sv_batch_read",
            "sv_batch_mode_log", "sv_batch_free", "sv_step1d_noalloc", "sv_set_drive",
-           "sv_set_launch", "sv_get_launch", "sv_num_configs", "sv_get_config", "sv_config_desc",
+           "sv_set_launch", "sv_get_launch", "sv_set_wait_limit", "sv_measure_fp64_peak", "sv_num_configs", "sv_get_config", "sv_config_desc",
            "sv_set_config", "sv_autotune", "sv_batch_num_configs", "sv_batch_set_config",
            "sv_batch_get_config", "sv_set_medium2d")
 
@@ -145,6 +145,8 @@ def lib() -> ctypes.CDLL:
     L.sv_batch_free.restype = None
     L.sv_set_drive.argtypes = [vp, ctypes.POINTER(_Drive)]
     L.sv_set_launch.argtypes = [vp, ctypes.c_int]
+    L.sv_set_wait_limit.argtypes = [vp, ctypes.c_int]
+    L.sv_measure_fp64_peak.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.sv_set_medium2d.argtypes = [vp, ctypes.POINTER(_Medium2d)]
     L.sv_get_launch.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     ip = ctypes.POINTER(ctypes.c_int)
@@ -212,6 +214,17 @@ def step1d_noalloc(params: Params, n: int, L: float, u_in: int, u_out: int, stre
                                  ctypes.c_void_p(st.cuda_stream))
     _check(rc, "sv_step1d_noalloc")
     return (dt.value, fl.value) if wait else None
+
+
+def measure_fp64_peak(stream=None) -> float:
+    """sv_measure_fp64_peak: the device's FP64 FMA throughput in TFLOP/s (the
+    roofline denominator of the FP64 step kernels)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    out = ctypes.c_double()
+    _check(lib().sv_measure_fp64_peak(ctypes.c_void_p(st.cuda_stream), ctypes.byref(out)),
+           "sv_measure_fp64_peak")
+    return out.value
 
 
 class Solver:
@@ -340,6 +353,11 @@ class Solver:
     def set_launch(self, mode: int):
         """LAUNCH_AUTO, LAUNCH_PER_STEP or LAUNCH_PERSISTENT (1D MUSCL-Hancock)."""
         _check(lib().sv_set_launch(self._h, int(mode)), "sv_set_launch")
+
+    def set_wait_limit(self, polls: int):
+        """sv_set_wait_limit: the persistent loop's barrier waits give up after
+        `polls` polls (0: the default limit); a failure-path test hook."""
+        _check(lib().sv_set_wait_limit(self._h, int(polls)), "sv_set_wait_limit")
 
     @property
     def launch(self) -> int:

@@ -128,3 +128,12 @@ def test_batch_and_noalloc_validation(libsv):
              ctypes.byref(fl), None) == sv.SV_ESIZE
     ps = sv.Params(precision=sv.FP32_PS).c()
     assert f(ctypes.byref(ps), 16, 1.0, a, b, ctypes.byref(dt), ctypes.byref(fl), None) == sv.SV_EINVAL
+    # buffers that share any byte: U_out starting inside U_in, or U_in inside U_out
+    # (16 float cells: 4 * 16 * 4 = 256 bytes per buffer)
+    for off in (16, 255, -255):
+        c = ctypes.c_void_p((1 << 20) + off)
+        assert f(ctypes.byref(p), 16, 1.0, a, c, ctypes.byref(dt), ctypes.byref(fl),
+                 None) == sv.SV_EINVAL, off
+    pd = sv.Params(precision=sv.FP64).c()       # double: 512 bytes per buffer
+    c = ctypes.c_void_p((1 << 20) + 300)
+    assert f(ctypes.byref(pd), 16, 1.0, a, c, ctypes.byref(dt), ctypes.byref(fl), None) == sv.SV_EINVAL

@@ -7,7 +7,7 @@ times and step counts."""
 import numpy as np
 import pytest
 
-from gpu_util import need_gpu, oracle_params, rel_linf
+from gpu_util import assert_fp64_parity, need_gpu, oracle_params, rel_linf
 from oracle import orc as O
 from paper_1805_03442_gb300 import inputs
 
@@ -121,7 +121,7 @@ def test_matches_oracle(sv):
     ref, t_ref, k_ref, rc_ref = O.run(oracle_params(P), U0, (N,), 1.0 / N, 0.25)
     assert rc == 0 and rc_ref == 0
     assert k == k_ref and t == t_ref == 0.25
-    assert rel_linf(U, ref) <= 1e-12
+    assert_fp64_parity(U, ref)
 
 
 def test_nonphysical_stops_the_loop(sv):
@@ -170,3 +170,42 @@ def test_persistent_full_grid_matches(sv):
     U0 = wave_state(N, seed=4)
     a, b = run_modes(sv, P, N, U0, nsteps=12)
     assert_same(a, b)
+
+
+@pytest.mark.parametrize("prec", ["FP32", "FP64"])
+def test_barrier_wait_limit_ends_with_estall(sv, prec):
+    """The failure path of the persistent loop's bounded grid-barrier wait:
+    with the wait limited to one poll, the blocks that arrive before the last
+    one give up, raise the stall flag and leave the launch, which ends with
+    SV_ESTALL instead of hanging.  Nothing faults and nothing spins: the wait
+    simply runs out.  After a new upload (and the default limit) the solver
+    steps exactly as a fresh per-step solver does."""
+    N = 4000                                     # 63 chunks: 63 co-resident blocks
+    P = sv.Params(precision=getattr(sv, prec))
+    U0 = wave_state(N, seed=5)
+    with sv.Solver(P, (N,), (1.0,)) as s:
+        s.set_launch(sv.LAUNCH_PERSISTENT)
+        s.write_state(U0)
+        s.set_wait_limit(1)
+        rc, _ = s.run_to(0.05, check=False)
+        assert rc == sv.SV_ESTALL
+        assert s.status() & sv.FLAG_STALL
+        s.set_wait_limit(0)
+        s.write_state(U0)
+        assert s.status() == 0
+        rc, k = s.run_to(0.05, check=False)
+        assert rc == 0 and s.status() == 0
+        U, t = s.read_state()
+    with sv.Solver(P, (N,), (1.0,)) as r:
+        r.set_launch(sv.LAUNCH_PER_STEP)
+        r.write_state(U0)
+        rc2, k2 = r.run_to(0.05, check=False)
+        U2, t2 = r.read_state()
+    assert rc2 == 0 and k == k2 and t == t2
+    assert np.array_equal(U, U2)
+    with pytest.raises(Exception):
+        s2 = sv.Solver(P, (N,), (1.0,))
+        try:
+            s2.set_wait_limit(-1)
+        finally:
+            s2.close()

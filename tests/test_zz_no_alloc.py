@@ -1,13 +1,17 @@
 """The allocation-free 1D step, sv_step1d_noalloc, against the regular
 solver's step.
 
-The entry point serves callers that cannot allocate device memory (code
-running under another framework's CUDA graph capture, or with a fixed
-memory pool): they pass their own state buffers and the library keeps its
-control block in a static device array.  Here torch allocates the two
-buffers only to play such a caller.  Two calls in a row check that the
-second call is not disturbed by what the first left in the shared array.
-This file is collected last on purpose."""
+The entry point serves callers that cannot allocate device memory (processes
+whose device memory is a fixed pool handed out at start-up, hosts that must
+not allocate while stepping): they pass their own state buffers and the
+library keeps its control block in a static device array.  Here torch
+allocates the two buffers only to play such a caller.  Two calls in a row
+check that the second call is not disturbed by what the first left in the
+shared array.
+
+The file name sorts last so that a run stopping at its first failure has
+already run every other test when it reaches this one; the tests here do not
+depend on that order and pass alone in a fresh process as well."""
 import numpy as np
 import pytest
 
@@ -42,6 +46,9 @@ def test_noalloc_step_matches_solver_on_two_calls(prec, tol):
     assert dt1 + dt2 == pytest.approx(t2, rel=1e-14)
     assert rel_linf(U1, U1_ref) <= tol
     assert rel_linf(U2, U2_ref) <= tol
+    # the same kernels' arithmetic as the solver's step: equal bit for bit
+    assert dt1 == t1 and np.array_equal(U1, U1_ref)
+    assert np.array_equal(U2, U2_ref)
 
 
 def test_noalloc_rejects_oversized_grid():
