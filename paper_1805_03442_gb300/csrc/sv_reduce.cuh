@@ -111,23 +111,40 @@ __device__ __forceinline__ T vload(const T* p) {
   return *(const volatile T*)p;
 }
 
+// Ticket of a block: atomic add with acquire-release semantics at GPU scope.
+// Release: this block's folds of the maxima and flags (and, through the block
+// barrier before it, every thread's stores) are visible to whoever acquires a
+// later ticket; acquire: the block that takes the last ticket sees every other
+// block's folds.  One round trip instead of a fence followed by an atomic.
+__device__ __forceinline__ uint32_t ticket_acq_rel(uint32_t* p) {
+  uint32_t v;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Turn the reduced maxima into the next dt (eq. 16 capped by c_tau tau and by
-// t_end).  `advance` = the kernel just completed a step.
+// t_end).  `advance` = the kernel just completed a step.  Runs on one thread
+// of the block that took the last ticket (ticket_acq_rel): every other block
+// has folded its maxima, so the keys, the flags and the time are read with
+// plain loads issued together (one round trip) and reset with plain stores;
+// the next launch (kernel boundary) or, in the persistent loop, the caller's
+// fence before the barrier bump publishes them.
 template <typename R>
 __device__ void finalize(Ctl* ctl, const KParams& kp, bool advance, bool flip = true) {
-  __threadfence();
-  const double smax = key_to_double(atomicExch((unsigned long long*)&ctl->smax_key,
-                                               (unsigned long long)key_of(0.0)));
-  const double akey = key_to_double(atomicExch((unsigned long long*)&ctl->tau_key,
-                                               (unsigned long long)key_of(-INFINITY)));
-  uint32_t flags = atomicOr(&ctl->flags, 0u);
-  const double dt = dt_from_maxima(kp, (R)smax, (R)akey, flags);
+  const uint64_t sk = vload(&ctl->smax_key), tk = vload(&ctl->tau_key);
+  uint32_t flags = vload(&ctl->flags);
   double t = vload(&ctl->t);
   const double t_end = vload(&ctl->t_end);
+  const uint32_t was_last = vload(&ctl->last), cur = vload(&ctl->cur);
+  const double dt_taken = vload(&ctl->dt);
+  const int64_t nsteps = vload(&ctl->nsteps);
+  ctl->smax_key = key_of(0.0);
+  ctl->tau_key = key_of(-INFINITY);
+  const double dt = dt_from_maxima(kp, (R)key_to_double(sk), (R)key_to_double(tk), flags);
   if (advance) {
-    t = vload(&ctl->last) ? t_end : t + vload(&ctl->dt);
-    if (flip) ctl->cur = vload(&ctl->cur) ^ 1u;
-    ctl->nsteps = vload(&ctl->nsteps) + 1;
+    t = was_last ? t_end : t + dt_taken;
+    if (flip) ctl->cur = cur ^ 1u;
+    ctl->nsteps = nsteps + 1;
   }
   uint32_t last = 0;
   double dtn = dt;
@@ -144,8 +161,7 @@ __device__ void finalize(Ctl* ctl, const KParams& kp, bool advance, bool flip = 
   set_step_dt<R>(ctl, dtn, kp);
   ctl->last = last;
   ctl->flags = flags;
-  __threadfence();
-  atomicExch(&ctl->ticket, 0u);
+  ctl->ticket = 0u;
 }
 
 // Block-wide fold of (smax, akey, flags) into the control block, then this
@@ -182,8 +198,7 @@ __device__ __forceinline__ bool block_arrive(Ctl* ctl, T smax, T akey, uint32_t 
     atomicMax((unsigned long long*)&ctl->smax_key, (unsigned long long)key_of((double)smax));
     atomicMax((unsigned long long*)&ctl->tau_key, (unsigned long long)key_of((double)akey));
     if (flags) atomicOr(&ctl->flags, flags);
-    __threadfence();
-    const uint32_t ticket = atomicAdd(&ctl->ticket, 1u);
+    const uint32_t ticket = ticket_acq_rel(&ctl->ticket);
     s_last = (ticket == gridDim.x - 1);
   }
   __syncthreads();

@@ -54,23 +54,38 @@ __device__ __forceinline__ void cp16(void* smem, const void* gmem) {
 // of a grid whose fields start on 16-byte boundaries use 16-byte copies; the
 // others go cell by cell through the boundary mapping (periodic wrap, wall
 // mirror, outflow copy, driven ghost state).  Commits one cp.async group.
+// Whether tile b is copied with 16-byte chunks: its span lies inside the grid
+// and the fields start on 16-byte boundaries.
+template <int SPAN>
+__device__ __forceinline__ bool tile_interior(int N, int b) {
+  const int lo = b - 2;
+  return (N & 3) == 0 && lo >= 0 && lo + SPAN <= N;
+}
+
+// The 16-byte copies of an interior tile (no boundary mapping, no time).
+template <int SPAN, int NT>
+__device__ __forceinline__ void copy_interior(float (*dst)[SPAN], const float* Uin, int N, int b) {
+  // lo = b - 2 is a multiple of 4 (b = OUT i - 2 with OUT a multiple of 4).
+  // A quarter of the block per field: thread q of it copies 16-byte chunks
+  // q, q + NT/4, ... of the SPAN/4 = 1 + R NT/4 chunks, and thread 0 the
+  // last one, so no thread divides an index.
+  const int lo = b - 2;
+  constexpr int C4 = SPAN / 4, TPF = NT / 4, R = (C4 - 1) / TPF;
+  static_assert(C4 == 1 + R * TPF, "span of whole quarter-block rounds plus one chunk");
+  const int f = threadIdx.x / TPF, q = threadIdx.x % TPF;
+  const float* src = Uin + (f * N + lo + 4 * q);
+  float* d = &dst[f][4 * q];
+#pragma unroll
+  for (int r = 0; r < R; ++r) cp16(d + 4 * TPF * r, src + 4 * TPF * r);
+  if (q == 0) cp16(d + 4 * (C4 - 1), src + 4 * (C4 - 1));
+}
+
 template <int SPAN, int PP, int NT>
 __device__ __forceinline__ void load_tile(float (*dst)[SPAN], const float* Uin, int N, int b,
                                           const P<float>& k, const KParams& kp, double t) {
   const int lo = b - 2;
-  if ((N & 3) == 0 && lo >= 0 && lo + SPAN <= N) {
-    // lo = b - 2 is a multiple of 4 (b = OUT i - 2 with OUT a multiple of 4).
-    // A quarter of the block per field: thread q of it copies 16-byte chunks
-    // q, q + NT/4, ... of the SPAN/4 = 1 + R NT/4 chunks, and thread 0 the
-    // last one, so no thread divides an index.
-    constexpr int C4 = SPAN / 4, TPF = NT / 4, R = (C4 - 1) / TPF;
-    static_assert(C4 == 1 + R * TPF, "span of whole quarter-block rounds plus one chunk");
-    const int f = threadIdx.x / TPF, q = threadIdx.x % TPF;
-    const float* src = Uin + (f * N + lo + 4 * q);
-    float* d = &dst[f][4 * q];
-#pragma unroll
-    for (int r = 0; r < R; ++r) cp16(d + 4 * TPF * r, src + 4 * TPF * r);
-    if (q == 0) cp16(d + 4 * (C4 - 1), src + 4 * (C4 - 1));
+  if (tile_interior<SPAN>(N, b)) {
+    copy_interior<SPAN, NT>(dst, Uin, N, b);
   } else {
     for (int e = threadIdx.x; e < SPAN; e += NT) {
       const int j = lo + e;
@@ -101,8 +116,26 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
   using pk::f2;
   constexpr int CELLS = Tile<NPT, NT>::CELLS, OUT = Tile<NPT, NT>::OUT, SPAN = Tile<NPT, NT>::SPAN;
   constexpr int NWT = NT / 32;
+  extern __shared__ __align__(16) unsigned char smem_tile[];
+  TileSmem<NPT, NT>& S = *reinterpret_cast<TileSmem<NPT, NT>*>(smem_tile);
+  const int ntile = (N + OUT - 1) / OUT;
+  int tile = blockIdx.x;
+  // An interior first tile needs nothing from the control block: its copies
+  // from both state buffers go out before the control block is read (slot 0
+  // from bufA, slot 1 from bufB), so that read's round trip overlaps the
+  // tile's; the slot of the buffer that is not the input takes the next tile.
+  const bool early = tile < ntile && tile_interior<SPAN>(N, OUT * tile - 2);
+  if (early) {
+    copy_interior<SPAN, NT>(S.u[0], bufA, N, OUT * tile - 2);
+    cp_async_commit();
+    copy_interior<SPAN, NT>(S.u[1], bufB, N, OUT * tile - 2);
+    cp_async_commit();
+  }
   const StepCtl sc = block_step_ctl(ctl);
-  if (!(sc.dt > 0.0)) return;                     // stopped, or t_end reached
+  if (!(sc.dt > 0.0)) {                           // stopped, or t_end reached
+    cp_async_wait<0>();                           // no copy may outlive the block
+    return;
+  }
   const float* __restrict__ Uin = sc.cur ? bufB : bufA;
   float* __restrict__ Uout = sc.cur ? bufA : bufB;
   const double t = sc.t;
@@ -112,19 +145,16 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
   const f2 dt2 = pk::splat(sd.dt), ndtdx2 = pk::splat(-sd.dtdx);
   const f2 ndt_2h2 = pk::splat(-sd.dt_2h), dt_22 = pk::splat(sd.dt_2);
 
-  extern __shared__ __align__(16) unsigned char smem_tile[];
-  TileSmem<NPT, NT>& S = *reinterpret_cast<TileSmem<NPT, NT>*>(smem_tile);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int src_m = (lane + 31) & 31, src_p = (lane + 1) & 31;
-  const int ntile = (N + OUT - 1) / OUT;
 
   float smax = 0.0f, akey = -INFINITY;
   uint32_t flags = 0;
 
-  int tile = blockIdx.x;
-  if (tile < ntile) load_tile<SPAN, PP, NT>(S.u[0], Uin, N, OUT * tile - 2, k, kp, t);
+  const int first = early ? (int)sc.cur : 0;      // slot of the first tile
+  if (!early && tile < ntile) load_tile<SPAN, PP, NT>(S.u[0], Uin, N, OUT * tile - 2, k, kp, t);
   for (int it = 0; tile < ntile; ++it, tile += gridDim.x) {
-    const int buf = it & 1;
+    const int buf = (it + first) & 1;
     const int b = OUT * tile - 2;
     cp_async_wait<0>();
     __syncthreads();                              // tile in place; the other buffer is free
