@@ -286,20 +286,62 @@ __device__ __forceinline__ R pressure(const P<R>& k, R kin2, R E, R Ev) {
 
 // ---------------------------------------------------------------- limiter
 
+// minmod(a, b): the argument of smaller magnitude when a and b have the same
+// sign, else 0.
+// float: min.xorsign.abs gives min(|a|, |b|) with the sign of a xor b, i.e.
+// negative exactly when the signs differ; max with 0 clears that case and the
+// sign of a is put back (three ALU instructions).
+__device__ __forceinline__ float minmod(float a, float b) {
+  float m;
+  asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(m) : "f"(a), "f"(b));
+  return copysignf(fmaxf(m, 0.0f), a);
+}
+// double: the same decision on the bit patterns (for doubles of one sign the
+// integer order of the magnitudes' bits is their order), on the integer pipe
+// rather than GB300's narrow FP64 pipe.  A zero argument gives a zero of a's
+// sign.
+__device__ __forceinline__ double minmod(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  if ((ia ^ ib) < 0) return 0.0;
+  const long long ma = ia & 0x7fffffffffffffffll, mb = ib & 0x7fffffffffffffffll;
+  return __longlong_as_double((ma < mb ? ma : mb) | (ia & (long long)0x8000000000000000ull));
+}
+
+// Whether four values (densities and pressures of two states) are all > 0.
+// float: the minimum against 0.  double: the signed high words of the bit
+// patterns are all > 0 (integer pipe; a positive double below ~1e-313 counts
+// as not positive, far below any density or pressure of a state).
+__device__ __forceinline__ bool all_positive(float a, float b, float c, float d) {
+  return fminf(fminf(a, b), fminf(c, d)) > 0.0f;
+}
+__device__ __forceinline__ bool all_positive(double a, double b, double c, double d) {
+  const int ha = __double2hiint(a), hb = __double2hiint(b);
+  const int hc = __double2hiint(c), hd = __double2hiint(d);
+  return min(min(ha, hb), min(hc, hd)) > 0;
+}
+__device__ __forceinline__ bool both_positive(float a, float b) { return (a > 0.0f) && (b > 0.0f); }
+__device__ __forceinline__ bool both_positive(double a, double b) {
+  return min(__double2hiint(a), __double2hiint(b)) > 0;
+}
+
 // TVD slope limiters on the two one-sided differences a, b (eq. 14 asks for
 // "limiter functions" without naming one): LIM 0 minmod, 1 van Leer, 2 MC.
 template <int LIM, typename R>
 __device__ __forceinline__ R limit(R a, R b) {
-  const R ab = a * b;
-  R m;
-  if (LIM == 1) {
-    if constexpr (std::is_same<R, float>::value) m = __fdividef(2.0f * ab, fabsf(a + b));
-    else m = (R)2 * ab / fabs(a + b);
+  if constexpr (LIM == 0) {
+    return minmod(a, b);
   } else {
-    m = fmin(fabs(a), fabs(b));
-    if (LIM == 2) m = fmin((R)2 * m, (R)0.5 * fabs(a + b));
+    const R ab = a * b;
+    R m;
+    if (LIM == 1) {
+      if constexpr (std::is_same<R, float>::value) m = __fdividef(2.0f * ab, fabsf(a + b));
+      else m = (R)2 * ab / fabs(a + b);
+    } else {
+      m = fmin(fabs(a), fabs(b));
+      m = fmin((R)2 * m, (R)0.5 * fabs(a + b));
+    }
+    return ab > (R)0 ? copysign(m, a) : (R)0;
   }
-  return ab > (R)0 ? copysign(m, a) : (R)0;
 }
 
 // ---------------------------------------------------------------- source Y

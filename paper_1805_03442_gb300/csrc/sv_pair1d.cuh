@@ -39,11 +39,9 @@ __device__ __forceinline__ f2 sqrt_pos(f2 a) {
   return mul(a, pair(Ar<float>::rsqrt(a.x), Ar<float>::rsqrt(a.y)));
 }
 
-// minmod as the median of (a, b, 0): the argument of smaller magnitude when a
-// and b have the same sign, else 0 (four min/max, no multiply or select).
+// the limiter per component (minmod: three ALU instructions, sv_model.cuh)
 template <int LIM>
 __device__ __forceinline__ float slope(float a, float b) {
-  if (LIM == 0) return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.0f));
   return limit<LIM, float>(a, b);
 }
 

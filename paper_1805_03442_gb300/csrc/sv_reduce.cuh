@@ -48,7 +48,7 @@ __device__ __forceinline__ void cfl_cell(const P<R>& k, R rho, R kin2, R vmag, R
                                          R& smax, R& akey, uint32_t& flags) {
   const R p = pressure<R, PP>(k, kin2, E, Ev);
   const R ir = Ar<R>::rcp(rho);
-  if (!((rho > (R)0) && (p > (R)0))) {
+  if (!both_positive(rho, p)) {
     flags |= FLAG_NONPHYS;
     return;
   }

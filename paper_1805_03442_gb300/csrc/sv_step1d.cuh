@@ -91,7 +91,7 @@ __device__ __forceinline__ void predict(const P<R>& k, const R (&u)[4], const R 
   dF[2] = va * (a[2] + pa) - vb * (b[2] + pb);
   dF[3] = va * a[3] - vb * b[3];
   // positivity guard: a non-physical extrapolated state drops the slopes
-  if (!(fmin(fmin(a[0], pa), fmin(b[0], pb)) > (R)0)) {
+  if (!all_positive(a[0], pa, b[0], pb)) {
 #pragma unroll
     for (int f = 0; f < 4; ++f) d[f] = dF[f] = (R)0;
   }
@@ -135,7 +135,7 @@ __device__ __forceinline__ void level_states(const P<R>& k, const R (&u)[4], con
   R ira, va, ka, pa, irb, vb, kb, pb;
   prim1<R, PP>(k, a, ira, va, ka, pa);
   prim1<R, PP>(k, b, irb, vb, kb, pb);
-  if (!(fmin(fmin(a[0], pa), fmin(b[0], pb)) > (R)0)) {
+  if (!all_positive(a[0], pa, b[0], pb)) {
 #pragma unroll
     for (int f = 0; f < 4; ++f) a[f] = b[f] = u[f];
   }
@@ -163,7 +163,7 @@ __device__ __forceinline__ void hll(const P<R>& k, const R (&l)[4], const R (&r)
   R irL, uL, kL, pL, irR, uR, kR, pR;
   prim1<R, PP>(k, L, irL, uL, kL, pL);
   prim1<R, PP>(k, Rr, irR, uR, kR, pR);
-  if (!(fmin(fmin(L[0], pL), fmin(Rr[0], pR)) > (R)0)) {
+  if (!all_positive(L[0], pL, Rr[0], pR)) {
 #pragma unroll
     for (int f = 0; f < 4; ++f) { L[f] = fl[f]; Rr[f] = fr[f]; }
     prim1<R, PP>(k, L, irL, uL, kL, pL);

@@ -88,7 +88,7 @@ struct Nd {
     flux<A>(b, vb, pb, Fb);
 #pragma unroll
     for (int f = 0; f < NF; ++f) dF[f] = Fa[f] - Fb[f];
-    return fmin(fmin(a[0], pa), fmin(b[0], pb)) > (R)0;
+    return all_positive(a[0], pa, b[0], pb);
   }
 
   // Y of a cell of the active medium; a frozen cell (active = false) has none.
@@ -139,7 +139,7 @@ struct Nd {
     R irL, pL, vL[DIM], irR, pR, vR[DIM];
     prim(k, L, irL, vL, pL);
     prim(k, Rr, irR, vR, pR);
-    if (!(fmin(fmin(L[0], pL), fmin(Rr[0], pR)) > (R)0)) {
+    if (!all_positive(L[0], pL, Rr[0], pR)) {
 #pragma unroll
       for (int f = 0; f < NF; ++f) { L[f] = fl[f]; Rr[f] = fr[f]; }
       prim(k, L, irL, vL, pL);
