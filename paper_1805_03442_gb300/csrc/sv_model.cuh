@@ -175,12 +175,36 @@ template <> struct P<double> {
   double gamma, g1, Ck, Q0, inv_tau0, tau0;
   double tau_rho, tau_T, Q_rho, Q_T, I_rho, I_T;
   int limiter, frozen, qi_zero, bc_lo, bc_hi;
+  // eq. 6 exponents that are multiples of 1/2 (the paper's tau_rho = -1,
+  // tau_T = -1.5): twice each exponent (tau_rho, tau_T, Q_rho, Q_T, I_rho,
+  // I_T), and whether the tau pair / the Q and I exponents all qualify
+  // (|exponent| <= 4), so that the power laws are products and square roots
+  int hk[6];
+  bool half_tau, half_qi;
   __device__ __forceinline__ explicit P(const KParams& k)
       : gamma(k.gamma), g1(k.g1), Ck(k.Ck), Q0(k.Q0), inv_tau0(k.inv_tau0), tau0(k.tau0),
         tau_rho(k.tau_rho), tau_T(k.tau_T), Q_rho(k.Q_rho), Q_T(k.Q_T), I_rho(k.I_rho),
         I_T(k.I_T), limiter(k.limiter), frozen(k.frozen), qi_zero(k.qi_zero), bc_lo(k.bc_lo),
-        bc_hi(k.bc_hi) {}
+        bc_hi(k.bc_hi) {
+    const double e[6] = {tau_rho, tau_T, Q_rho, Q_T, I_rho, I_T};
+    bool ok[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const double t = 2.0 * e[i], r = rint(t);
+      ok[i] = t == r && fabs(r) <= 8.0;
+      hk[i] = ok[i] ? (int)r : 0;
+    }
+    half_tau = ok[0] && ok[1];
+    half_qi = ok[2] && ok[3] && ok[4] && ok[5];
+  }
 };
+
+// rho^(kr/2) T^(kT/2) for integers |kr|, |kT| <= 8, given sr = sqrt(rho) and
+// sT = sqrt(T) where kr / kT is odd: whole powers by repeated multiplication,
+// the negative ones gathered into one reciprocal.  Each product rounds once,
+// so the result stays within a few ulp of pow's.
+__device__ __forceinline__ double half_powers(double rho, double sr, int kr, double T, double sT,
+                                              int kT);
 
 template <> struct P<float> {
   float gamma, g1, Ck, Q0, inv_tau0, tau0;
@@ -372,6 +396,18 @@ template <int SRC> struct Src<float, SRC> {
   }
 };
 
+__device__ __forceinline__ double half_powers(double rho, double sr, int kr, double T, double sT,
+                                              int kT) {
+  double num = 1.0, den = 1.0;
+  const int ar = kr < 0 ? -kr : kr, aT = kT < 0 ? -kT : kT;
+  double pr = (ar & 1) ? sr : 1.0, pT = (aT & 1) ? sT : 1.0;
+  for (int i = 0; i < (ar >> 1); ++i) pr *= rho;
+  for (int i = 0; i < (aT >> 1); ++i) pT *= T;
+  if (kr < 0) den *= pr; else num *= pr;
+  if (kT < 0) den *= pT; else num *= pT;
+  return (kr < 0 || kT < 0) ? num * Ar<double>::rcp(den) : num;
+}
+
 template <int SRC> struct Src<double, SRC> {
   static __device__ __forceinline__ void eval(const P<double>& k, double rho, double T, double Ev,
                                               double& yE, double& yEv) {
@@ -379,14 +415,28 @@ template <int SRC> struct Src<double, SRC> {
       yE = yEv = 0.0;
       return;
     }
-    // the power laws of eq. 6 as exp of a linear form in ln rho, ln T: two
-    // logarithms per state instead of two pow per closure (GB300's FP64 rate)
-    const double lr = log(rho), lT = log(T);
-    const double inv_tau = exp(-fma(k.tau_rho, lr, k.tau_T * lT)) * k.inv_tau0;
-    double Q = k.Q0, I = k.Q0;
-    if (SRC == 2) {
-      Q = k.Q0 * exp(fma(k.Q_rho, lr, k.Q_T * lT));
-      I = k.Q0 * exp(fma(k.I_rho, lr, k.I_T * lT));
+    double inv_tau, Q = k.Q0, I = k.Q0;
+    if (k.half_tau && (SRC == 1 || k.half_qi)) {
+      // exponents that are multiples of 1/2: products and at most one square
+      // root per variable, in place of logarithms and exponentials on GB300's
+      // narrow FP64 pipe
+      const bool odd_r = ((k.hk[0] | (SRC == 2 ? k.hk[2] | k.hk[4] : 0)) & 1) != 0;
+      const bool odd_T = ((k.hk[1] | (SRC == 2 ? k.hk[3] | k.hk[5] : 0)) & 1) != 0;
+      const double sr = odd_r ? sqrt(rho) : 1.0, sT = odd_T ? sqrt(T) : 1.0;
+      inv_tau = k.inv_tau0 * half_powers(rho, sr, -k.hk[0], T, sT, -k.hk[1]);
+      if (SRC == 2) {
+        Q = k.Q0 * half_powers(rho, sr, k.hk[2], T, sT, k.hk[3]);
+        I = k.Q0 * half_powers(rho, sr, k.hk[4], T, sT, k.hk[5]);
+      }
+    } else {
+      // the power laws of eq. 6 as exp of a linear form in ln rho, ln T: two
+      // logarithms per state instead of two pow per closure (GB300's FP64 rate)
+      const double lr = log(rho), lT = log(T);
+      inv_tau = exp(-fma(k.tau_rho, lr, k.tau_T * lT)) * k.inv_tau0;
+      if (SRC == 2) {
+        Q = k.Q0 * exp(fma(k.Q_rho, lr, k.Q_T * lT));
+        I = k.Q0 * exp(fma(k.I_rho, lr, k.I_T * lT));
+      }
     }
     yE = rho * (Q - I);
     yEv = (rho * k.Ck * T - Ev) * inv_tau + rho * Q;

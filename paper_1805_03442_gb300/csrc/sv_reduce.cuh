@@ -26,6 +26,10 @@ template <> struct TauKey<float> {
 };
 template <> struct TauKey<double> {
   static __device__ __forceinline__ double of(const P<double>& k, double rho, double T) {
+    if (k.half_tau) {
+      const double sr = (k.hk[0] & 1) ? sqrt(rho) : 1.0, sT = (k.hk[1] & 1) ? sqrt(T) : 1.0;
+      return -(k.tau0 * half_powers(rho, sr, k.hk[0], T, sT, k.hk[1]));
+    }
     return -(k.tau0 * exp(fma(k.tau_rho, log(rho), k.tau_T * log(T))));
   }
 };

@@ -4,16 +4,20 @@ oracle's statistics stored in tests/golden/nonlinear_stage.json (written by
 oracle/nonlinear_stage.py --golden).
 
 The run ends, in the oracle and on the GPU alike, when the pumped shocks have
-steepened the density spikes until the pressure goes negative; that collapse
-time converges under changes of CFL, grid and limiter (13.3-14.5 over N =
-1024 / 2048, CFL 0.4 / 0.2, minmod / van Leer), so it is a property of the
-model's solution that the GPU must reproduce.
+steepened the density spikes until the pressure goes negative: every setting
+of N = 1024 / 2048, CFL 0.4 / 0.2 and minmod / van Leer collapses between
+t = 13.3 and 14.5, so the collapse is a property of the model's solution that
+the GPU must reproduce.  With van Leer its time is reproducible: one-ulp
+perturbations of the initial state move the oracle's collapse by 1e-4
+(14.0228-14.0229).  With minmod it is not: the limiter's grid-scale noise
+amplification (tests/test_oracle_noise.py) moves it across 13.3-14.5 under the
+same perturbations, so for minmod only that band is a prediction.
 
 Bounds.  FP64: the same shock count and spacing at t = 10, mean velocity jump
-and max density within 3%, collapse time within 0.05 -- not bitwise: minmod
-amplifies rounding differences at the grid scale (tests/test_oracle_noise.py),
-and after ~40000 steps two correct FP64 codes differ at the percent level in
-the shock amplitudes (measured: 1% with minmod, 0.01% with van Leer).
+and max density within 3% (after ~30000 steps two correct FP64 codes that
+round differently differ at the percent level in the shock amplitudes with
+minmod, at 1e-4 with van Leer); collapse within 0.05 of the oracle with van
+Leer, inside 13.0-15.0 with minmod.
 Float: the perturbation layout (FP32_PS) follows the same shock train within
 5%; the full-state float policy is seeded by its own rounding noise (a float
 state rounds the O(1) background at 6e-8 each step, which the medium's
@@ -77,7 +81,10 @@ def test_fp64_shock_train_and_collapse(sv, limiter):
     assert r[10.0]["jump"] == pytest.approx(g["t10"]["jump"], rel=0.03)
     assert r[10.0]["max_rho"] == pytest.approx(g["t10"]["max_rho"], rel=0.03)
     assert r["rc"] in (sv.SV_ENONPHYS, sv.SV_EDT)
-    assert abs(r["collapse_t"] - g["collapse_t"]) <= 0.05
+    if limiter == 1:
+        assert abs(r["collapse_t"] - g["collapse_t"]) <= 0.05
+    else:
+        assert 13.0 <= r["collapse_t"] <= 15.0
 
 
 def test_fp32_perturbation_layout_shock_train(sv):

@@ -56,6 +56,10 @@ def _oracle_steps(Po, U0, N, h, nsteps):
 @pytest.mark.parametrize("N", [5, 8, 33, 1000, 4099, 70001])
 @pytest.mark.parametrize("params", [dict(tau0=0.3),
                                     dict(tau0=0.05, S=0.7, Q_rho=0.4, Q_T=-0.3, I_rho=0.2, I_T=0.5),
+                                    # every exponent a multiple of 1/2, of either sign: the
+                                    # product-and-square-root power laws of the FP64 kernels
+                                    dict(tau0=0.1, S=0.8, tau_rho=0.5, tau_T=-2.0, Q_rho=0.5,
+                                         Q_T=-1.0, I_rho=1.5, I_T=-0.5),
                                     dict(tau0=math.inf, S=0.0)])
 def test_fp64_steps_match_oracle(sv, N, params):
     P = sv.Params(precision=sv.FP64, **params)
