@@ -35,17 +35,24 @@ METRIC = "cell-updates/s"
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM bytes (read + write) of one launch of the 1D FP32 step at N = 2^22, per launch
-# configuration (a substring of its description), from one ncu capture of the current kernels:
-# the block tiles read the state once (67.2 MB) and write part of it back during the launch
-# (the rest is still dirty in L2 when it ends); the sliding warps re-read their chunk halos.
-# Only valid for that workload and precision; other lines, and configurations without a
-# capture, report null.
+# configuration (a substring of its description), from one ncu capture of the current kernels
+# with ncu's default cache control (caches flushed before the launch, as the benchmark's steps):
+# the block tiles read the state once (plus the first tile of the other buffer, 2.5 MB) and write
+# part of it back during the launch (the rest is still dirty in L2 when it ends); the sliding warps
+# re-read their chunk halos.  Only valid for that workload and precision; other lines, and
+# configurations without a capture, report null.
 TRAFFIC_1D_FP32_N22 = {
-    "512-cell block tiles, 2 cells per thread, 78 registers, 3 blocks/SM": 86.8e6,
-    "512-cell block tiles, 2 cells per thread, 2 blocks/SM": 87.2e6,
-    "512-cell block tiles, 2 cells per thread, 64 registers, 4 blocks/SM": 86.5e6,
-    "warps sliding over 64-cell chunks": 91.7e6,
+    "512-cell block tiles, 2 cells per thread, 78 registers, 3 blocks/SM": 89.7e6,
+    "512-cell block tiles, 2 cells per thread, 2 blocks/SM": 89.9e6,
+    "1024-cell block tiles, 4 cells per thread, 2 blocks/SM": 86.2e6,
+    "512-cell block tiles, 2 cells per thread, 64 registers, 4 blocks/SM": 90.0e6,
+    "warps sliding over 64-cell chunks": 91.6e6,
 }
+# The same launch in steady state back to back (ncu --cache-control none on launches 100-102 of
+# `bench.py --b2b --steps 64`, 3-blocks/SM tiles): each step writes back the previous step's dirty
+# lines and finds ~5 MB of its input still in L2, 129.2 MB per launch against the algorithmic
+# 134.2 MB.
+TRAFFIC_B2B_1D_FP32_N22 = 129.2e6
 
 
 def traffic_of(workload: str, ncell: int, precision: str, config: str):
@@ -54,13 +61,11 @@ def traffic_of(workload: str, ncell: int, precision: str, config: str):
     return next((v for k, v in TRAFFIC_1D_FP32_N22.items() if k in config), None)
 
 # FP64 flops one updated cell costs in the FP64 step kernels (2 DFMA + DMUL + DADD, ncu
-# warp-instruction counts x 32 lanes): step1d_kernel at N = 2^22, stepnd_kernel at 2048^2 and
-# 128^3 (the 3D figure includes the tile halo's 18 % of redundant work).  These kernels are bound
+# warp-instruction counts x 32 lanes): step1d_kernel at N = 2^20, stepnd_kernel at 1024^2 and
+# 128^3 (the 3D figure includes the tile halo's redundant work), with the paper's closure
+# exponents (tau_rho = -1, tau_T = -1.5: the power laws of eq. 6 as products).  These kernels are bound
 # by GB300's FP64 pipe (ncu: 86-87 % of its peak busy), so FP64 lines report an "alu" roofline.
-FP64_FLOPS_PER_CELL = {1: 681.4, 2: 1066.6, 3: 2314.9}
-# FP64 rate of one GB300: 2 FMA lanes per SM per clock (ncu: one warp-wide FP64 instruction per
-# SM every 16 cycles at full pipe) x 2 flops x 152 SMs x 2.07 GHz = 1.259 TFLOP/s
-FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
+FP64_FLOPS_PER_CELL = {1: 455.7, 2: 855.9, 3: 1938.3}
 
 # --precision names -> sv_params.precision (SV_FP32, SV_FP64, SV_FP32_P64,
 # SV_FP32_PC, SV_FP32_PS of include/sv.h) and the arithmetic type reported as "dtype"
@@ -68,14 +73,15 @@ PRECISIONS = {"fp32": 0, "fp64": 1, "fp32_p64": 2, "fp32_pc": 3, "fp32_ps": 4}
 DTYPES = {"fp32": "f32", "fp64": "f64", "fp32_p64": "f32", "fp32_pc": "f32", "fp32_ps": "f32"}
 
 
-def fp64_roofline(dim: int, ncell: int, step_s: float, hbm_frac: float) -> dict:
-    """The FP64 step as an ALU-bound kernel: FP64 flops per launch over the
-    GB300's FP64 rate (FP64_FLOPS_PER_CELL, FP64_PEAK_TFLOPS)."""
+def fp64_roofline(dim: int, ncell: int, step_s: float, hbm_frac: float, peak: float) -> dict:
+    """The FP64 step as an ALU-bound kernel: FP64 flops per launch
+    (FP64_FLOPS_PER_CELL) over the FP64 FMA rate the library's probe measured
+    in this run (`peak`, TFLOP/s)."""
     flops = FP64_FLOPS_PER_CELL[dim] * ncell
     achieved = flops / step_s / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-            "peak_src": "derived FP64 rate: 2 FMA lanes/SM/clk x 2 flops x 152 SMs x 2.07 GHz",
-            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+    return {"bound": "alu", "achieved": achieved, "peak": peak,
+            "peak_src": "measured: DFMA-chain probe of the library (sv_measure_fp64_peak), this run",
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
             "flops_per_launch": flops, "hbm_frac": hbm_frac}
 
 
@@ -465,9 +471,12 @@ def back_to_back(solver, stream, flush, steps: int, alg_bytes: int, hbm_gbs: flo
     e1.record(stream)
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) * 1e-3 / steps
-    return {"value": solver.ncell / t, "unit": METRIC, "ms_per_step": 1e3 * t, "steps": steps,
-            "l2": "one flush before the window, none between steps",
-            "alg_gbs": alg_bytes / t / 1e9, "frac": alg_bytes / t / 1e9 / hbm_gbs}
+    out = {"value": solver.ncell / t, "unit": METRIC, "ms_per_step": 1e3 * t, "steps": steps,
+           "l2": "one flush before the window, none between steps",
+           "alg_gbs": alg_bytes / t / 1e9, "frac": alg_bytes / t / 1e9 / hbm_gbs}
+    if solver.ncell == 1 << 22 and solver.params.precision == 0:
+        out["traffic"] = TRAFFIC_B2B_1D_FP32_N22
+    return out
 
 
 def precision_leg(sv, args, prec_name: str, U0, dims, L, stream, flush, pk: dict) -> dict:
@@ -573,7 +582,21 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
-        times = timed_flushed_steps(solver, stream, flush, args.steps, 0)
+        if args.b2b:
+            # diagnostic mode: the K steps replayed back to back from the
+            # solver's graph in one CUDA-event window after one flush (the
+            # graph is built by an untimed replay first)
+            solver.step(args.steps)
+            with torch.cuda.stream(stream):
+                flush.fill_(3.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solver.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times = [e0.elapsed_time(e1) * 1e-3 / args.steps] * args.steps
+        else:
+            times = timed_flushed_steps(solver, stream, flush, args.steps, 0)
     if dist is not None:
         dist.barrier()
     tot, units = aggregate(sum(times), float(ncell * args.steps), dist, device="cuda")
@@ -596,6 +619,7 @@ def run_ours(args):
         solver.read_state_ptr(host_out.data_ptr())
     e2e_t = time.perf_counter() - t0
     pk = peaks()
+    fp64_peak = sv.measure_fp64_peak(stream) if args.precision == "fp64" else None
     esize_alg = 2 * nf * esize * ncell
     extras = ws == 1 and not args.no_extras and args.workload == "1d" and args.precision == "fp32"
     b2b = back_to_back(solver, stream, flush, 64, esize_alg, pk["hbm_gbs"]) if extras else None
@@ -618,7 +642,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": W["desc"].format(cells=ncell, side=dims[0]), "cells": ncell,
                    "precision": args.precision,
-                   "l2": "flushed by a 256 MiB write before every timed step",
+                   "l2": ("one 256 MiB write before the window, steps back to back" if args.b2b
+                          else "flushed by a 256 MiB write before every timed step"),
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "launch_config": tuned["config"]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
@@ -626,7 +651,8 @@ def run_ours(args):
                      "frac": achieved / pk["hbm_gbs"],
                      "traffic": traffic_of(args.workload, ncell, args.precision, tuned["config"]),
                      "alg_bytes_per_launch": alg_bytes},
-        **({"roofline": fp64_roofline(len(dims), ncell, step_s, achieved / pk["hbm_gbs"])}
+        **({"roofline": fp64_roofline(len(dims), ncell, step_s, achieved / pk["hbm_gbs"],
+                                      fp64_peak)}
            if args.precision == "fp64" else {}),
         "e2e": {"value": ws * ncell * e2e_steps / e2e_t, "unit": METRIC,
                 "h2d_bytes_per_step": int(host_in.numel() * 8),
@@ -1004,6 +1030,9 @@ def main():
     ap.add_argument("--subset", type=int, default=64, help="looped comparison subset of the sweep")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--b2b", action="store_true",
+                    help="diagnostic: time the steps back to back (graph replay, no flush between "
+                         "them) instead of one flushed step at a time")
     ap.add_argument("--no-extras", action="store_true",
                     help="default 1D line only: skip the back-to-back, FP64, compensated-pressure "
                          "and sweep figures")
