@@ -128,7 +128,10 @@ Layout layout(const sv_params* p, const sv_grid* g) {
     if (e_ != cudaSuccess) return SV_ECUDA;  \
   } while (0)
 
-cudaError_t launch_step(sv_solver* s, cudaStream_t st) {
+// One step's launches; pdl: the 1D step kernels with the programmatic
+// stream-serialization attribute (recorded so in the step graph: a step may
+// launch while the previous one finishes and waits in pdl_wait).
+cudaError_t launch_step(sv_solver* s, cudaStream_t st, bool pdl = false) {
   if (s->dim == 1 && s->p.method == SV_HEUN) {
     cudaError_t e = heun1d_launch(s->p.precision, 1, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell,
                                   s->grid, st);
@@ -139,9 +142,10 @@ cudaError_t launch_step(sv_solver* s, cudaStream_t st) {
   const SolverConfig& c = s->cfgs[(size_t)s->config];
   if (c.kind == CFG_TILE)
     return tile1d_launch(s->kp, s->p.precision, c.param, s->buf[0], s->buf[1], s->ctl, s->ncell,
-                         s->tile_grid, st);
+                         s->tile_grid, st, pdl);
   if (c.kind == CFG_SLIDE)
-    return step1d_launch(s->p.precision, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell, s->grid, st);
+    return step1d_launch(s->p.precision, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell, s->grid, st,
+                         pdl);
   return stepnd_launch(s->dim, s->p.precision, s->kp, s->buf[0], s->buf[1], s->ctl, s->g.n,
                        c.param, st);
 }
@@ -151,7 +155,7 @@ int ensure_graph(sv_solver* s) {
   cudaGraph_t gr = nullptr;
   SV_TRY(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t le = cudaSuccess;
-  for (int i = 0; i < kGraphLen && le == cudaSuccess; ++i) le = launch_step(s, s->cap_stream);
+  for (int i = 0; i < kGraphLen && le == cudaSuccess; ++i) le = launch_step(s, s->cap_stream, true);
   cudaError_t ee = cudaStreamEndCapture(s->cap_stream, &gr);
   if (le != cudaSuccess || ee != cudaSuccess) {
     if (gr) cudaGraphDestroy(gr);

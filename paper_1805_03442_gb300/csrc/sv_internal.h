@@ -12,10 +12,28 @@ struct Ctl;
 
 enum { PREC_FP32 = 0, PREC_FP64 = 1, PREC_FP32_P64 = 2, PREC_FP32_PC = 3, PREC_FP32_PS = 4 };
 
+// A kernel launch; pdl = with the programmatic stream-serialization
+// attribute (for kernels that call pdl_wait before reading what the previous
+// kernel wrote: the 1D step kernels), as the solver's step graph records them.
+inline cudaError_t launch_kernel(const void* fn, dim3 grid, dim3 block, void** args, size_t smem,
+                                 cudaStream_t st, bool pdl) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? attr : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
 // 1D fused step (sv_step1d.cu)
 int step1d_grid(const KParams& kp, int precision);
 cudaError_t step1d_launch(int precision, const KParams& kp, void* a, void* b, Ctl* ctl, int64_t N,
-                          int grid, cudaStream_t st);
+                          int grid, cudaStream_t st, bool pdl = false);
 
 // Float 1D MUSCL-Hancock step on block tiles (sv_tile1d.cu), grids of at
 // least kTile1dMinCells cells; precision PREC_FP32, PREC_FP32_PC or PREC_FP32_PS
@@ -24,7 +42,7 @@ constexpr int64_t kTile1dMinCells = 4096;
 // 13, 12 or 22
 int tile1d_grid(const KParams& kp, int precision, int var);
 cudaError_t tile1d_launch(const KParams& kp, int precision, int var, void* a, void* b, Ctl* ctl,
-                          int64_t N, int grid, cudaStream_t st);
+                          int64_t N, int grid, cudaStream_t st, bool pdl = false);
 
 // 1D persistent loop of up to nmax steps (sv_loop1d.cu); grid 0 = unavailable
 int loop1d_grid(const KParams& kp, int precision, int64_t N, int* cap);

@@ -94,6 +94,17 @@ __host__ __device__ __forceinline__ double ref_field(const double (&ref)[4], int
   return 0.0;
 }
 
+// Programmatic dependent launch: a step kernel launched with the programmatic
+// stream-serialization attribute (the graph-replayed steps of a solver) may
+// start while the previous step's grid is still finishing.  pdl_wait blocks
+// until that grid has completed and its memory is visible -- every step
+// kernel calls it before reading the control block or the state; launched
+// without the attribute it returns at once.  pdl_trigger lets the next grid
+// launch once every block of this one has called it or exited (its blocks
+// then wait in pdl_wait for this grid to complete).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Device control block: time, step size and the reductions of one solver.
 struct Ctl {
   double t;            // current time

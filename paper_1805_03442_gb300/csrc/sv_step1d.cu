@@ -17,6 +17,7 @@ template <typename R, int PP, int LIM, int SRC, int MINB>
 __global__ void __launch_bounds__(NT1, MINB)
 step1d_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl* __restrict__ ctl,
               int N) {
+  pdl_wait();                                     // the previous step's grid has completed
   const StepCtl sc = block_step_ctl(ctl);
   if (!(sc.dt > 0.0)) return;                     // stopped, or t_end reached
   const R* __restrict__ Uin = sc.cur ? bufB : bufA;
@@ -40,6 +41,7 @@ step1d_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
 
   step1d_warp<R, PP, LIM, SRC>(k, Uin, Uout, N, N, c0, c1, lane, dt, dtdx, dt_2h, dt_2, smax, akey,
                                flags, ring, kp, sc.t);
+  pdl_trigger();                                  // the next step may launch and wait
   reduce_and_finalize<R, NT1>(ctl, kp, smax, akey, flags, true);
 }
 
@@ -101,11 +103,12 @@ int step1d_grid(const KParams& kp, int precision) {
 }
 
 cudaError_t step1d_launch(int precision, const KParams& kp, void* a, void* b, Ctl* ctl, int64_t N,
-                          int grid, cudaStream_t st) {
+                          int grid, cudaStream_t st, bool pdl) {
   if (N >= (1LL << 31) / 4) return cudaErrorInvalidValue;
   int n32 = (int)N;
   void* args[] = {(void*)&kp, &a, &b, &ctl, &n32};
-  return cudaLaunchKernel(pick(kp, precision), dim3(grid), dim3(NT1), args, smem_bytes(precision), st);
+  return launch_kernel(pick(kp, precision), dim3(grid), dim3(NT1), args, smem_bytes(precision), st,
+                       pdl);
 }
 
 }  // namespace sv

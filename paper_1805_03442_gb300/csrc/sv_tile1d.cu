@@ -31,12 +31,12 @@ int tile1d_grid(const KParams& kp, int precision, int var) {
 }
 
 cudaError_t tile1d_launch(const KParams& kp, int precision, int var, void* a, void* b, Ctl* ctl,
-                          int64_t N, int grid, cudaStream_t st) {
+                          int64_t N, int grid, cudaStream_t st, bool pdl) {
   if (N >= (1LL << 31) / 4 || N < kTile1dMinCells || grid < 1) return cudaErrorInvalidValue;
   int n32 = (int)N;
   void* args[] = {(void*)&kp, &a, &b, &ctl, &n32};
-  return cudaLaunchKernel(pick(kp, precision, var), dim3(grid), dim3(threads_of(var)), args,
-                          smem_of(var), st);
+  return launch_kernel(pick(kp, precision, var), dim3(grid), dim3(threads_of(var)), args,
+                       smem_of(var), st, pdl);
 }
 
 }  // namespace sv

@@ -125,6 +125,7 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
   // from bufA, slot 1 from bufB), so that read's round trip overlaps the
   // tile's; the slot of the buffer that is not the input takes the next tile.
   const bool early = tile < ntile && tile_interior<SPAN>(N, OUT * tile - 2);
+  pdl_wait();                                     // the previous step's grid has completed
   if (early) {
     copy_interior<SPAN, NT>(S.u[0], bufA, N, OUT * tile - 2);
     cp_async_commit();
@@ -158,6 +159,7 @@ tile1d_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict__ bu
     const int b = OUT * tile - 2;
     cp_async_wait<0>();
     __syncthreads();                              // tile in place; the other buffer is free
+    if (tile + (int)gridDim.x >= ntile) pdl_trigger();   // this block's last tile
     if (tile + (int)gridDim.x < ntile)
       load_tile<SPAN, PP, NT>(S.u[buf ^ 1], Uin, N, OUT * (tile + gridDim.x) - 2, k, kp, t);
 
