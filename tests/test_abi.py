@@ -137,3 +137,13 @@ def test_batch_and_noalloc_validation(libsv):
     pd = sv.Params(precision=sv.FP64).c()       # double: 512 bytes per buffer
     c = ctypes.c_void_p((1 << 20) + 300)
     assert f(ctypes.byref(pd), 16, 1.0, a, c, ctypes.byref(dt), ctypes.byref(fl), None) == sv.SV_EINVAL
+
+
+def test_wait_limit_and_probe_validation(libsv):
+    """The failure-path hook and the FP64 probe check their arguments before
+    touching the device."""
+    from paper_1805_03442_gb300 import sv
+    sv._lib = None
+    L = sv.lib()
+    assert L.sv_set_wait_limit(None, 1) == sv.SV_EINVAL
+    assert L.sv_measure_fp64_peak(None, None) == sv.SV_EINVAL
