@@ -603,21 +603,33 @@ def run_ours(args):
     status = solver.status()
     t_sim, nsteps = solver.time()
 
-    # end to end through the C ABI: pinned host FP64 state in, one step, state out
+    # end to end through the C ABI: pinned host state in, one step, state out;
+    # float host buffers for the float policies (their device state is float:
+    # exact both ways, half the bytes of double buffers), double for FP64
     nf = len(dims) + 3
-    host_in = torch.from_numpy(U0.reshape(-1)).pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
-    e2e_steps = max(2, min(args.steps, 10))
-    solver.write_state_ptr(host_in.data_ptr())
-    solver.step(1)
-    solver.read_state_ptr(host_out.data_ptr())
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        solver.write_state_ptr(host_in.data_ptr())
+    f32_host = prec != sv.FP64
+
+    def e2e_rate(host_f32: bool, steps: int):
+        dt_ = torch.float32 if host_f32 else torch.float64
+        hin = torch.from_numpy(U0.reshape(-1)).to(dt_).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        wr = solver.write_state_ptr_f32 if host_f32 else solver.write_state_ptr
+        rd = solver.read_state_ptr_f32 if host_f32 else solver.read_state_ptr
+        wr(hin.data_ptr())
         solver.step(1)
-        solver.read_state_ptr(host_out.data_ptr())
-    e2e_t = time.perf_counter() - t0
+        rd(hout.data_ptr())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            wr(hin.data_ptr())
+            solver.step(1)
+            rd(hout.data_ptr())
+        el = time.perf_counter() - t0
+        return el, int(hin.numel() * hin.element_size()), int(hout.numel() * hout.element_size())
+
+    e2e_steps = max(2, min(args.steps, 10))
+    e2e_t, e2e_bi, e2e_bo = e2e_rate(f32_host, e2e_steps)
+    e2e_f64 = e2e_rate(False, e2e_steps) if f32_host else None
     pk = peaks()
     fp64_peak = sv.measure_fp64_peak(stream) if args.precision == "fp64" else None
     esize_alg = 2 * nf * esize * ncell
@@ -655,8 +667,10 @@ def run_ours(args):
                                       fp64_peak)}
            if args.precision == "fp64" else {}),
         "e2e": {"value": ws * ncell * e2e_steps / e2e_t, "unit": METRIC,
-                "h2d_bytes_per_step": int(host_in.numel() * 8),
-                "d2h_bytes_per_step": int(host_out.numel() * 8)},
+                "h2d_bytes_per_step": e2e_bi, "d2h_bytes_per_step": e2e_bo,
+                "host_dtype": "f32" if f32_host else "f64",
+                **({"value_f64_host_buffers": ws * ncell * e2e_steps / e2e_f64[0]}
+                   if e2e_f64 else {})},
         "gpu_launches": args.steps,
         "clocks": getattr(clk, "result", None),
         "status_flags": status, "sim_time": t_sim,

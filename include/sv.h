@@ -142,6 +142,18 @@ int sv_write_state(sv_solver* s, const double* host_soa, double t);
 /* Download the current state into host_soa (nf * ncell doubles) and its time. */
 int sv_read_state(sv_solver* s, double* host_soa, double* t);
 
+/* The same with float host buffers (nf * ncell floats, same layout): half the
+   bytes over the host link.  For the float policies (SV_FP32, SV_FP32_P64,
+   SV_FP32_PC) the device state is float, so a float buffer carries it
+   exactly both ways; SV_FP32_PS forms U - U_ref in double from the float
+   values and adds U_ref back in double before rounding to float; SV_FP64
+   widens on upload and rounds to nearest on download.  Page-locked (mapped)
+   buffers are read / written by the conversion kernels directly, others go
+   through the solver's staging area.  Errors: SV_EINVAL (null argument),
+   SV_ECUDA. */
+int sv_write_state_f32(sv_solver* s, const float* host_soa, double t);
+int sv_read_state_f32(sv_solver* s, float* host_soa, double* t);
+
 /* The dt the next step will take: cfl * h / max_j max(2|v_j|, |v_j| + c_j)
    (eq. 16), capped by c_tau * min_j tau_j and by the pending t_end. */
 int sv_dt_cfl(sv_solver* s, double* dt);

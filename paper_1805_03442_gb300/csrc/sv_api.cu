@@ -280,6 +280,46 @@ int flags_to_status(uint32_t f) {
   return SV_OK;
 }
 
+// Upload / download of the state in host format H (double, or float).
+template <typename H>
+int write_state_host(sv_solver* s, const H* host_soa, double t) {
+  if (!s || !host_soa) return SV_EINVAL;
+  const size_t count = (size_t)s->nf * (size_t)s->ncell;
+  // pinned host memory: the conversion kernel reads it over the host link
+  // itself (one pass instead of a copy into staging and a second pass); the
+  // staging buffer holds count doubles, room for either format
+  const H* src = (const H*)mapped_view(host_soa);
+  if (!src) {
+    SV_TRY(cudaMemcpyAsync(s->staging, host_soa, count * sizeof(H), cudaMemcpyHostToDevice,
+                           s->stream));
+    src = (const H*)s->staging;
+  }
+  SV_TRY(ctl_reset_launch(s->ctl, t, s->stream));
+  SV_TRY(to_state_launch(s->p.precision, src, s->buf[0], s->buf[1], s->ctl, (int64_t)count,
+                         s->stream, s->kp.ref, s->nf));
+  SV_TRY(dt_reduce_launch(s->p.precision, s->dim, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell,
+                          s->stream));
+  return SV_OK;
+}
+
+template <typename H>
+int read_state_host(sv_solver* s, H* host_soa, double* t) {
+  if (!s || !host_soa) return SV_EINVAL;
+  const size_t count = (size_t)s->nf * (size_t)s->ncell;
+  // pinned host memory: the conversion kernel writes it over the host link
+  H* dst = (H*)mapped_view(host_soa);
+  SV_TRY(from_state_launch(s->p.precision, s->buf[0], s->buf[1], s->ctl,
+                           dst ? dst : (H*)s->staging, (int64_t)count, s->stream, s->kp.ref,
+                           s->nf));
+  if (!dst)
+    SV_TRY(cudaMemcpyAsync(host_soa, s->staging, count * sizeof(H), cudaMemcpyDeviceToHost,
+                           s->stream));
+  int rc = read_ctl(s);
+  if (rc != SV_OK) return rc;
+  if (t) *t = s->host_ctl->t;
+  return SV_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -407,38 +447,19 @@ int sv_init(const sv_params* p, const sv_grid* g, void* cuda_stream, void* devic
 }
 
 int sv_write_state(sv_solver* s, const double* host_soa, double t) {
-  if (!s || !host_soa) return SV_EINVAL;
-  const size_t count = (size_t)s->nf * (size_t)s->ncell;
-  // pinned host memory: the conversion kernel reads it over the host link
-  // itself (one pass instead of a copy into staging and a second pass)
-  const double* src = (const double*)mapped_view(host_soa);
-  if (!src) {
-    SV_TRY(cudaMemcpyAsync(s->staging, host_soa, count * sizeof(double), cudaMemcpyHostToDevice,
-                           s->stream));
-    src = s->staging;
-  }
-  SV_TRY(ctl_reset_launch(s->ctl, t, s->stream));
-  SV_TRY(to_state_launch(s->p.precision, src, s->buf[0], s->buf[1], s->ctl, (int64_t)count,
-                         s->stream, s->kp.ref, s->nf));
-  SV_TRY(dt_reduce_launch(s->p.precision, s->dim, s->kp, s->buf[0], s->buf[1], s->ctl, s->ncell,
-                          s->stream));
-  return SV_OK;
+  return write_state_host<double>(s, host_soa, t);
 }
 
 int sv_read_state(sv_solver* s, double* host_soa, double* t) {
-  if (!s || !host_soa) return SV_EINVAL;
-  const size_t count = (size_t)s->nf * (size_t)s->ncell;
-  // pinned host memory: the conversion kernel writes it over the host link
-  double* dst = (double*)mapped_view(host_soa);
-  SV_TRY(from_state_launch(s->p.precision, s->buf[0], s->buf[1], s->ctl, dst ? dst : s->staging,
-                           (int64_t)count, s->stream, s->kp.ref, s->nf));
-  if (!dst)
-    SV_TRY(cudaMemcpyAsync(host_soa, s->staging, count * sizeof(double), cudaMemcpyDeviceToHost,
-                           s->stream));
-  int rc = read_ctl(s);
-  if (rc != SV_OK) return rc;
-  if (t) *t = s->host_ctl->t;
-  return SV_OK;
+  return read_state_host<double>(s, host_soa, t);
+}
+
+int sv_write_state_f32(sv_solver* s, const float* host_soa, double t) {
+  return write_state_host<float>(s, host_soa, t);
+}
+
+int sv_read_state_f32(sv_solver* s, float* host_soa, double* t) {
+  return read_state_host<float>(s, host_soa, t);
 }
 
 int sv_dt_cfl(sv_solver* s, double* dt) {

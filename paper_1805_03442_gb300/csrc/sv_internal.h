@@ -84,6 +84,12 @@ cudaError_t to_state_launch(int precision, const double* src, void* a, void* b, 
 cudaError_t from_state_launch(int precision, const void* a, const void* b, const Ctl* ctl,
                               double* dst, int64_t count, cudaStream_t st,
                               const double* ref = nullptr, int nf = 4);
+// The same with float host-format buffers (sv_write_state_f32 / sv_read_state_f32).
+cudaError_t to_state_launch(int precision, const float* src, void* a, void* b, Ctl* ctl,
+                            int64_t count, cudaStream_t st, const double* ref, int nf);
+cudaError_t from_state_launch(int precision, const void* a, const void* b, const Ctl* ctl,
+                              float* dst, int64_t count, cudaStream_t st, const double* ref,
+                              int nf);
 // Exact copy of the current state buffer's `bytes` to (save) or from `other`.
 cudaError_t raw_state_launch(void* a, void* b, const Ctl* ctl, void* other, int64_t bytes,
                              bool save, cudaStream_t st);

@@ -144,15 +144,16 @@ template <typename R> struct Vec2;
 template <> struct Vec2<float> { using T = float2; };
 template <> struct Vec2<double> { using T = double2; };
 
-template <typename R>
-__global__ void to_state_kernel(const double* src, R* a, R* b, const Ctl* ctl, int64_t count) {
+template <typename H, typename R>
+__global__ void to_state_kernel(const H* src, R* a, R* b, const Ctl* ctl, int64_t count) {
   R* U = vload(&ctl->cur) ? b : a;
   using R2 = typename Vec2<R>::T;
+  using H2 = typename Vec2<H>::T;
   const int64_t i0 = (int64_t)blockIdx.x * NTU + threadIdx.x, di = (int64_t)gridDim.x * NTU;
-  if (((uintptr_t)src & 15) == 0 && ((uintptr_t)U & (sizeof(R2) - 1)) == 0) {
+  if (((uintptr_t)src & (sizeof(H2) - 1)) == 0 && ((uintptr_t)U & (sizeof(R2) - 1)) == 0) {
     const int64_t n2 = count / 2;
     for (int64_t i = i0; i < n2; i += di) {
-      const double2 v = reinterpret_cast<const double2*>(src)[i];
+      const H2 v = reinterpret_cast<const H2*>(src)[i];
       R2 w;
       w.x = (R)v.x;
       w.y = (R)v.y;
@@ -164,21 +165,24 @@ __global__ void to_state_kernel(const double* src, R* a, R* b, const Ctl* ctl, i
   }
 }
 
-template <typename R>
-__global__ void from_state_kernel(const R* a, const R* b, const Ctl* ctl, double* dst,
-                                  int64_t count) {
+template <typename H, typename R>
+__global__ void from_state_kernel(const R* a, const R* b, const Ctl* ctl, H* dst, int64_t count) {
   const R* U = vload(&ctl->cur) ? b : a;
   using R2 = typename Vec2<R>::T;
+  using H2 = typename Vec2<H>::T;
   const int64_t i0 = (int64_t)blockIdx.x * NTU + threadIdx.x, di = (int64_t)gridDim.x * NTU;
-  if (((uintptr_t)dst & 15) == 0 && ((uintptr_t)U & (sizeof(R2) - 1)) == 0) {
+  if (((uintptr_t)dst & (sizeof(H2) - 1)) == 0 && ((uintptr_t)U & (sizeof(R2) - 1)) == 0) {
     const int64_t n2 = count / 2;
     for (int64_t i = i0; i < n2; i += di) {
       const R2 w = reinterpret_cast<const R2*>(U)[i];
-      reinterpret_cast<double2*>(dst)[i] = make_double2((double)w.x, (double)w.y);
+      H2 v;
+      v.x = (H)w.x;
+      v.y = (H)w.y;
+      reinterpret_cast<H2*>(dst)[i] = v;
     }
-    if (i0 == 0 && (count & 1)) dst[count - 1] = (double)U[count - 1];
+    if (i0 == 0 && (count & 1)) dst[count - 1] = (H)U[count - 1];
   } else {
-    for (int64_t i = i0; i < count; i += di) dst[i] = (double)U[i];
+    for (int64_t i = i0; i < count; i += di) dst[i] = (H)U[i];
   }
 }
 
@@ -195,20 +199,22 @@ RefN ref_of(const double* ref, int nf) {
   return r;
 }
 
-__global__ void to_state_ps_kernel(const double* src, float* a, float* b, const Ctl* ctl,
+template <typename H>
+__global__ void to_state_ps_kernel(const H* src, float* a, float* b, const Ctl* ctl,
                                    int64_t count, int64_t ncell, RefN ref) {
   float* U = vload(&ctl->cur) ? b : a;
   for (int64_t i = (int64_t)blockIdx.x * NTU + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * NTU)
-    U[i] = (float)(src[i] - ref.v[i / ncell]);
+    U[i] = (float)((double)src[i] - ref.v[i / ncell]);
 }
 
-__global__ void from_state_ps_kernel(const float* a, const float* b, const Ctl* ctl, double* dst,
+template <typename H>
+__global__ void from_state_ps_kernel(const float* a, const float* b, const Ctl* ctl, H* dst,
                                      int64_t count, int64_t ncell, RefN ref) {
   const float* U = vload(&ctl->cur) ? b : a;
   for (int64_t i = (int64_t)blockIdx.x * NTU + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * NTU)
-    dst[i] = ref.v[i / ncell] + (double)U[i];
+    dst[i] = (H)(ref.v[i / ncell] + (double)U[i]);
 }
 
 // Raw copies of the current state buffer (`words` 4-byte words) to / from
@@ -231,37 +237,57 @@ cudaError_t raw_state_launch(void* a, void* b, const Ctl* ctl, void* other, int6
   return cudaGetLastError();
 }
 
-cudaError_t to_state_launch(int precision, const double* src, void* a, void* b, Ctl* ctl,
-                            int64_t count, cudaStream_t st, const double* ref, int nf) {
+template <typename H>
+cudaError_t to_state_impl(int precision, const H* src, void* a, void* b, Ctl* ctl, int64_t count,
+                          cudaStream_t st, const double* ref, int nf) {
   const int g = grid_small(count);
   if (precision == PREC_FP32_PS) {
-    to_state_ps_kernel<<<g, NTU, 0, st>>>(src, (float*)a, (float*)b, ctl, count, count / nf,
-                                          ref_of(ref, nf));
+    to_state_ps_kernel<H><<<g, NTU, 0, st>>>(src, (float*)a, (float*)b, ctl, count, count / nf,
+                                             ref_of(ref, nf));
     return cudaGetLastError();
   }
   if (precision == PREC_FP64)
-    to_state_kernel<double><<<g, NTU, 0, st>>>(src, (double*)a, (double*)b, ctl, count);
+    to_state_kernel<H, double><<<g, NTU, 0, st>>>(src, (double*)a, (double*)b, ctl, count);
   else
-    to_state_kernel<float><<<g, NTU, 0, st>>>(src, (float*)a, (float*)b, ctl, count);
+    to_state_kernel<H, float><<<g, NTU, 0, st>>>(src, (float*)a, (float*)b, ctl, count);
   return cudaGetLastError();
 }
 
-cudaError_t from_state_launch(int precision, const void* a, const void* b, const Ctl* ctl,
-                              double* dst, int64_t count, cudaStream_t st, const double* ref,
-                              int nf) {
+template <typename H>
+cudaError_t from_state_impl(int precision, const void* a, const void* b, const Ctl* ctl, H* dst,
+                            int64_t count, cudaStream_t st, const double* ref, int nf) {
   const int g = grid_small(count);
   if (precision == PREC_FP32_PS) {
-    from_state_ps_kernel<<<g, NTU, 0, st>>>((const float*)a, (const float*)b, ctl, dst, count,
-                                            count / nf, ref_of(ref, nf));
+    from_state_ps_kernel<H><<<g, NTU, 0, st>>>((const float*)a, (const float*)b, ctl, dst, count,
+                                               count / nf, ref_of(ref, nf));
     return cudaGetLastError();
   }
   if (precision == PREC_FP64)
-    from_state_kernel<double><<<g, NTU, 0, st>>>((const double*)a, (const double*)b, ctl, dst,
-                                                 count);
+    from_state_kernel<H, double><<<g, NTU, 0, st>>>((const double*)a, (const double*)b, ctl, dst,
+                                                    count);
   else
-    from_state_kernel<float><<<g, NTU, 0, st>>>((const float*)a, (const float*)b, ctl, dst,
-                                                count);
+    from_state_kernel<H, float><<<g, NTU, 0, st>>>((const float*)a, (const float*)b, ctl, dst,
+                                                   count);
   return cudaGetLastError();
+}
+
+cudaError_t to_state_launch(int precision, const double* src, void* a, void* b, Ctl* ctl,
+                            int64_t count, cudaStream_t st, const double* ref, int nf) {
+  return to_state_impl<double>(precision, src, a, b, ctl, count, st, ref, nf);
+}
+cudaError_t to_state_launch(int precision, const float* src, void* a, void* b, Ctl* ctl,
+                            int64_t count, cudaStream_t st, const double* ref, int nf) {
+  return to_state_impl<float>(precision, src, a, b, ctl, count, st, ref, nf);
+}
+cudaError_t from_state_launch(int precision, const void* a, const void* b, const Ctl* ctl,
+                              double* dst, int64_t count, cudaStream_t st, const double* ref,
+                              int nf) {
+  return from_state_impl<double>(precision, a, b, ctl, dst, count, st, ref, nf);
+}
+cudaError_t from_state_launch(int precision, const void* a, const void* b, const Ctl* ctl,
+                              float* dst, int64_t count, cudaStream_t st, const double* ref,
+                              int nf) {
+  return from_state_impl<float>(precision, a, b, ctl, dst, count, st, ref, nf);
 }
 
 // Uniform equilibrium rho = p = 1, v = 0, E_nu = ev0 into buffer a.

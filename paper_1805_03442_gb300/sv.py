@@ -32,7 +32,8 @@ EXPORTS = ("sv_required_bytes", "sv_init", "sv_write_state", "sv_read_state", "s
            "sv_state_device", "sv_free", "sv_strerror", "sv_batch_required_bytes",
            "sv_batch_init", "sv_batch_reset", "sv_batch_run", "sv_batch_sync", "sv_batch_read",
            "sv_batch_mode_log", "sv_batch_free", "sv_step1d_noalloc", "sv_set_drive",
-           "sv_set_launch", "sv_get_launch", "sv_set_wait_limit", "sv_measure_fp64_peak", "sv_num_configs", "sv_get_config", "sv_config_desc",
+           "sv_set_launch", "sv_get_launch", "sv_set_wait_limit", "sv_measure_fp64_peak",
+           "sv_write_state_f32", "sv_read_state_f32", "sv_num_configs", "sv_get_config", "sv_config_desc",
            "sv_set_config", "sv_autotune", "sv_batch_num_configs", "sv_batch_set_config",
            "sv_batch_get_config", "sv_set_medium2d")
 
@@ -118,6 +119,9 @@ def lib() -> ctypes.CDLL:
                           ctypes.POINTER(vp)]
     L.sv_write_state.argtypes = [vp, dp, ctypes.c_double]
     L.sv_read_state.argtypes = [vp, dp, dp]
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.sv_write_state_f32.argtypes = [vp, fp, ctypes.c_double]
+    L.sv_read_state_f32.argtypes = [vp, fp, dp]
     L.sv_dt_cfl.argtypes = [vp, dp]
     L.sv_step.argtypes = [vp, ctypes.c_int64]
     L.sv_run_to.argtypes = [vp, ctypes.c_double, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
@@ -303,6 +307,29 @@ class Solver:
         t = ctypes.c_double()
         _check(lib().sv_read_state(self._h, ctypes.cast(host_ptr, ctypes.POINTER(ctypes.c_double)),
                                    ctypes.byref(t)), "sv_read_state")
+        return t.value
+
+    # float host buffers (sv_write_state_f32 / sv_read_state_f32): half the bytes
+    def write_state_f32(self, U: np.ndarray, t: float = 0.0):
+        U = np.ascontiguousarray(U, dtype=np.float32).reshape(self.nf, self.ncell)
+        _check(lib().sv_write_state_f32(self._h, U.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                        float(t)), "sv_write_state_f32")
+
+    def read_state_f32(self) -> tuple[np.ndarray, float]:
+        U = np.empty((self.nf, self.ncell), dtype=np.float32)
+        t = ctypes.c_double()
+        _check(lib().sv_read_state_f32(self._h, U.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                       ctypes.byref(t)), "sv_read_state_f32")
+        return U, t.value
+
+    def write_state_ptr_f32(self, host_ptr: int, t: float = 0.0):
+        _check(lib().sv_write_state_f32(self._h, ctypes.cast(host_ptr, ctypes.POINTER(ctypes.c_float)),
+                                        float(t)), "sv_write_state_f32")
+
+    def read_state_ptr_f32(self, host_ptr: int) -> float:
+        t = ctypes.c_double()
+        _check(lib().sv_read_state_f32(self._h, ctypes.cast(host_ptr, ctypes.POINTER(ctypes.c_float)),
+                                       ctypes.byref(t)), "sv_read_state_f32")
         return t.value
 
     # ------------------------------------------------------------ stepping
