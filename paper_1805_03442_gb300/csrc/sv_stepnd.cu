@@ -463,10 +463,10 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
 template <int DIM, int PREC> struct Cfg;
 template <> struct Cfg<2, PREC_FP32_P64> { static constexpr int TX = 256, TY = 1, MINB = 2, SEG = 256; };
 template <> struct Cfg<2, PREC_FP64> { static constexpr int TX = 128, TY = 1, MINB = 2, SEG = 256; };
-template <> struct Cfg<3, PREC_FP32> { static constexpr int TX = 32, TY = 16, MINB = 1, SEG = 128; };
-template <> struct Cfg<3, PREC_FP32_P64> { static constexpr int TX = 32, TY = 16, MINB = 1, SEG = 128; };
-template <> struct Cfg<3, PREC_FP32_PC> { static constexpr int TX = 32, TY = 16, MINB = 1, SEG = 128; };
-template <> struct Cfg<3, PREC_FP32_PS> { static constexpr int TX = 32, TY = 16, MINB = 1, SEG = 128; };
+template <> struct Cfg<3, PREC_FP32> { static constexpr int TX = 34, TY = 15, MINB = 1, SEG = 128; };
+template <> struct Cfg<3, PREC_FP32_P64> { static constexpr int TX = 34, TY = 15, MINB = 1, SEG = 128; };
+template <> struct Cfg<3, PREC_FP32_PC> { static constexpr int TX = 34, TY = 15, MINB = 1, SEG = 128; };
+template <> struct Cfg<3, PREC_FP32_PS> { static constexpr int TX = 34, TY = 15, MINB = 1, SEG = 128; };
 template <> struct Cfg<3, PREC_FP64> { static constexpr int TX = 32, TY = 8, MINB = 1, SEG = 128; };
 
 // With `n` null only the kernel's shared-memory attribute is set (done once per
