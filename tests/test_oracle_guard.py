@@ -166,3 +166,55 @@ def test_guard_cases_mirror(orc, case):
     A_, _ = O.step(P, U, (N,), h, dt)
     B_, _ = O.step(P, (U * mir)[:, ::-1].copy(), (N,), h, dt)
     assert np.array_equal((B_ * mir)[:, ::-1], A_)
+
+
+def embed_nd(case, reps, dim, axis, other):
+    """The case's six cells tiled reps times along axis (0 = x) of a dim-D
+    grid, uniform over the other axes (sizes `other`, in axis order) with zero
+    transverse momentum.  Returns (U of shape (dim + 3, ncell), x fastest; the
+    grid size tuple n)."""
+    line = np.tile(_array(case["cells"]), (1, reps))        # rho, m, E, E_nu
+    m = line.shape[1]
+    rest = iter(other)
+    n = tuple(m if a == axis else next(rest) for a in range(dim))
+    shape = tuple(reversed(n))                              # numpy order: x last
+    bshape = [1] * dim
+    bshape[dim - 1 - axis] = m
+    U = np.zeros((dim + 3,) + shape)
+    U[0] = line[0].reshape(bshape)
+    U[1 + axis] = line[1].reshape(bshape)
+    U[dim + 1] = line[2].reshape(bshape)
+    U[dim + 2] = line[3].reshape(bshape)
+    return U.reshape(dim + 3, -1).copy(), n
+
+
+@pytest.mark.parametrize("dim,axis", [(2, 0), (2, 1), (3, 0), (3, 1), (3, 2)])
+@pytest.mark.parametrize("name", ["a", "b"])
+def test_guard_cases_embedded_nd(orc, name, dim, axis):
+    """The 2D / 3D oracle on the case laid along one axis of the grid: the
+    transverse fluxes are uniform and cancel, so every line along that axis
+    takes the 1D result, and the guarded cells take the exact upwind value."""
+    case = CASE_A if name == "a" else CASE_B
+    reps = 2
+    U, n = embed_nd(case, reps, dim, axis, (3, 2)[: dim - 1])
+    h = 1.0 / n[axis]
+    dt = float(case["r"]) * h
+    Un, rc = O.step(O.Params(**FROZEN), U, n, h, dt)
+    U1, rc1 = O.step(O.Params(**FROZEN), np.tile(_array(case["cells"]), (1, reps)),
+                     (6 * reps,), h, dt)
+    assert (rc != 0) == (rc1 != 0)
+    want, _ = embed_nd(dict(cells=[tuple(U1[:, i]) for i in range(6)]), reps, dim, axis,
+                       (3, 2)[: dim - 1])
+    # the 1D result of both copies is the same (periodic tiling)
+    assert np.array_equal(U1[:, :6], U1[:, 6:])
+    assert np.max(np.abs(Un - want)) <= 1e-14 * np.max(np.abs(want))
+    j = case["j"]
+    expect = np.array([float(x) for x in upwind(case["cells"][j], case["cells"][j - 1],
+                                                case["r"])])
+    shape = (dim + 3,) + tuple(reversed(n))
+    sel = [slice(None)] * (dim + 1)
+    sel[dim - axis] = j
+    got = Un.reshape(shape)[tuple(sel)].reshape(dim + 3, -1)
+    exp_nd = np.zeros(dim + 3)
+    exp_nd[0], exp_nd[1 + axis], exp_nd[dim + 1], exp_nd[dim + 2] = expect
+    assert np.max(np.abs(got - exp_nd[:, None])) <= 1e-15 * np.max(np.abs(expect))
