@@ -463,9 +463,7 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
 template <int DIM, int PREC> struct Cfg;
 template <> struct Cfg<2, PREC_FP32_P64> { static constexpr int TX = 256, TY = 1, MINB = 2, SEG = 256; };
 template <> struct Cfg<2, PREC_FP64> { static constexpr int TX = 128, TY = 1, MINB = 2, SEG = 256; };
-template <> struct Cfg<3, PREC_FP32> { static constexpr int TX = 34, TY = 15, MINB = 1, SEG = 128; };
 template <> struct Cfg<3, PREC_FP32_P64> { static constexpr int TX = 34, TY = 15, MINB = 1, SEG = 128; };
-template <> struct Cfg<3, PREC_FP32_PC> { static constexpr int TX = 34, TY = 15, MINB = 1, SEG = 128; };
 template <> struct Cfg<3, PREC_FP32_PS> { static constexpr int TX = 34, TY = 15, MINB = 1, SEG = 128; };
 template <> struct Cfg<3, PREC_FP64> { static constexpr int TX = 32, TY = 8, MINB = 1, SEG = 128; };
 
@@ -513,15 +511,15 @@ static cudaError_t by_prec(int precision, const KParams& kp, void* a, void* b, C
     case PREC_FP64: return launch_nd<double, 0, LIM, SRC, DIM, PREC_FP64>(kp, a, b, ctl, n, seg, st);
     case PREC_FP32_P64: return launch_nd<float, 1, LIM, SRC, DIM, PREC_FP32_P64>(kp, a, b, ctl, n, seg, st);
     default:
-      // float and compensated-float pressure: in 2D packed plane pairs; 3D
-      // keeps one cell per thread (the pair kernel needs 242 registers there,
-      // one block per SM, and runs 17% slower)
+      // the other float policies: in 2D packed plane pairs
+      // (sv_stepnd_pair.cu); in 3D float and compensated-float pressure with
+      // each cell's fields in packed pairs (sv_stepnd3f.cu: plane pairs need
+      // 242 registers there, one block per SM, and ran 17% slower than one
+      // cell per thread), the perturbation layout one cell per thread
       if constexpr (DIM == 2) return stepnd_pair_launch(DIM, precision, kp, a, b, ctl, n, seg, st);
-      else if (precision == PREC_FP32_PC)
-        return launch_nd<float, 2, LIM, SRC, DIM, PREC_FP32_PC>(kp, a, b, ctl, n, seg, st);
       else if (precision == PREC_FP32_PS)
         return launch_nd<float, 3, LIM, SRC, DIM, PREC_FP32_PS>(kp, a, b, ctl, n, seg, st);
-      else return launch_nd<float, 0, LIM, SRC, DIM, PREC_FP32>(kp, a, b, ctl, n, seg, st);
+      else return stepnd3f_launch(precision, kp, a, b, ctl, n, seg, st);
   }
 }
 
@@ -549,9 +547,9 @@ int stepnd_default_seg(int dim, int precision) {
       dim == 2)
     return stepnd_pair_default_seg(dim);
   if (dim == 2) return precision == PREC_FP64 ? Cfg<2, PREC_FP64>::SEG : Cfg<2, PREC_FP32_P64>::SEG;
-  if (precision == PREC_FP32_PC) return Cfg<3, PREC_FP32_PC>::SEG;
   if (precision == PREC_FP32_PS) return Cfg<3, PREC_FP32_PS>::SEG;
-  return precision == PREC_FP64 ? Cfg<3, PREC_FP64>::SEG : Cfg<3, PREC_FP32>::SEG;
+  if (precision == PREC_FP32_P64) return Cfg<3, PREC_FP32_P64>::SEG;
+  return precision == PREC_FP64 ? Cfg<3, PREC_FP64>::SEG : stepnd3f_default_seg();
 }
 
 int stepnd_grid(int dim, int precision, const KParams& kp) {

@@ -198,7 +198,7 @@ def random_field_3d(gamma: float, n: int, L: float, base, amp: float, seed: int,
 
     def field():
         z = (rng.standard_normal(kk.shape) + 1j * rng.standard_normal(kk.shape)) * amp_k
-        f = np.fft.irfftn(z, s=(n, n, n))
+        f = np.fft.irfftn(z, s=(n, n, n), axes=(0, 1, 2))
         return amp * f / max(np.sqrt(np.mean(f * f)), 1e-300)
 
     drho = field()
