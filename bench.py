@@ -53,12 +53,23 @@ TRAFFIC_1D_FP32_N22 = {
 # lines and finds ~5 MB of its input still in L2, 129.2 MB per launch against the algorithmic
 # 134.2 MB.
 TRAFFIC_B2B_1D_FP32_N22 = 129.2e6
+# The 3D FP32 step at 512^3 (the field-pair kernel, segments of 128 planes), one-pass capture of
+# the benchmark command itself: 4360.4 MB read + 3196.1 MB written against the algorithmic
+# 6442.5 MB (the tiles' halo columns and rows are read by two blocks, each segment reads two
+# extra planes).
+TRAFFIC_3D_FP32_512 = {"segments of 128 planes": 7556.6e6}
 
 
 def traffic_of(workload: str, ncell: int, precision: str, config: str):
-    if workload != "1d" or ncell != 1 << 22 or precision != "fp32":
+    if precision != "fp32":
         return None
-    return next((v for k, v in TRAFFIC_1D_FP32_N22.items() if k in config), None)
+    if workload == "1d" and ncell == 1 << 22:
+        table = TRAFFIC_1D_FP32_N22
+    elif workload == "3d" and ncell == 512 ** 3:
+        table = TRAFFIC_3D_FP32_512
+    else:
+        return None
+    return next((v for k, v in table.items() if k in config), None)
 
 # FP64 flops one updated cell costs in the FP64 step kernels (2 DFMA + DMUL + DADD, ncu
 # warp-instruction counts x 32 lanes): step1d_kernel at N = 2^20, stepnd_kernel at 1024^2 and

@@ -1,5 +1,5 @@
 """Host logic of the benchmark's roofline objects (no GPU): the DRAM traffic
-reported for each 1D launch configuration, and the ALU roofline of the FP64
+reported for each 1D launch configuration and the 3D line, and the ALU roofline of the FP64
 lines against the FP64 rate the library's probe measures."""
 import os
 import sys
@@ -30,6 +30,20 @@ def test_traffic_per_configuration():
     assert bench.traffic_of("1d", n // 2, "fp32", TILE3) is None
     assert bench.traffic_of("1d", n, "fp32_ps", TILE3) is None
     assert bench.traffic_of("2d", n, "fp32", TILE3) is None
+
+
+def test_traffic_3d():
+    """The 3D FP32 line at 512^3 reports the capture of its 128-plane
+    segments: more than the algorithmic 48 B per cell (halo columns and rows
+    read by two tiles), less than half again as much; other segment lengths,
+    sizes and precisions report null."""
+    n = 512 ** 3
+    seg128 = "2D/3D: marching segments of 128 planes per block"
+    v = bench.traffic_of("3d", n, "fp32", seg128)
+    assert v == 7556.6e6 and 1.0 < v / (2 * 6 * 4 * n) < 1.5
+    assert bench.traffic_of("3d", n, "fp32", "2D/3D: marching segments of 256 planes per block") is None
+    assert bench.traffic_of("3d", 256 ** 3, "fp32", seg128) is None
+    assert bench.traffic_of("3d", n, "fp32_pc", seg128) is None
 
 
 def test_fp64_roofline():
