@@ -86,16 +86,20 @@ __device__ __forceinline__ void source(const P<float>& k, const f2 (&u)[DIM + 3]
 }
 
 // eq. 13 along axis A at two faces with left states L and right states R; a
-// face with a non-physical state uses the cell values (fl, fr).  Weights as in
-// pk::hll (all non-negative).
-template <int DIM, int PP, int A>
+// face with a non-physical state uses the cell values, which `cells(fl, fr)`
+// supplies (called on that rare path only, so a caller whose cell values sit
+// in shared memory loads them only then).  Weights as in pk::hll (all
+// non-negative).
+template <int DIM, int PP, int A, typename CV>
 __device__ __forceinline__ void hll(const P<float>& k, f2 (&L)[DIM + 3], f2 (&R)[DIM + 3],
-                                    const f2 (&fl)[DIM + 3], const f2 (&fr)[DIM + 3], f2 (&F)[DIM + 3]) {
+                                    CV&& cells, f2 (&F)[DIM + 3]) {
   constexpr int NF = DIM + 3;
   Prim<DIM> pl = prim<DIM, PP>(k, L), pr = prim<DIM, PP>(k, R);
   const bool g0 = fminf(fminf(L[0].x, pl.p.x), fminf(R[0].x, pr.p.x)) > 0.0f;
   const bool g1 = fminf(fminf(L[0].y, pl.p.y), fminf(R[0].y, pr.p.y)) > 0.0f;
   if (!(g0 && g1)) {
+    f2 fl[NF], fr[NF];
+    cells(fl, fr);
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       if (!g0) { L[f].x = fl[f].x; R[f].x = fr[f].x; }

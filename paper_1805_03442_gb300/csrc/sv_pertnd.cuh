@@ -176,15 +176,16 @@ __device__ __forceinline__ void source(const P<float>& k, const f2 (&u)[DIM + 3]
                                           pkps::em1(fma(splat(k.I_rho), lr, mul(splat(k.I_T), lT)))));
 }
 
-template <int DIM, int A>
+template <int DIM, int A, typename CV>
 __device__ __forceinline__ void hll(const P<float>& k, f2 (&L)[DIM + 3], f2 (&R)[DIM + 3],
-                                    const f2 (&fl)[DIM + 3], const f2 (&fr)[DIM + 3],
-                                    f2 (&F)[DIM + 3]) {
+                                    CV&& cells, f2 (&F)[DIM + 3]) {
   constexpr int NF = DIM + 3;
   Prim<DIM> pl = prim<DIM>(k, L), pr = prim<DIM>(k, R);
   const bool g0 = fminf(fminf(pl.rho.x, pl.p.x), fminf(pr.rho.x, pr.p.x)) > 0.0f;
   const bool g1 = fminf(fminf(pl.rho.y, pl.p.y), fminf(pr.rho.y, pr.p.y)) > 0.0f;
   if (!(g0 && g1)) {
+    f2 fl[NF], fr[NF];
+    cells(fl, fr);
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       if (!g0) { L[f].x = fl[f].x; R[f].x = fr[f].x; }
@@ -263,12 +264,11 @@ __device__ __forceinline__ void source(const P<float>& k, const pk::f2 (&u)[DIM 
   else pkn::source<DIM, PP, SRC>(k, u, yE, yEv);
 }
 
-template <int DIM, int PP, int A>
+template <int DIM, int PP, int A, typename CV>
 __device__ __forceinline__ void hll(const P<float>& k, pk::f2 (&L)[DIM + 3], pk::f2 (&R)[DIM + 3],
-                                    const pk::f2 (&fl)[DIM + 3], const pk::f2 (&fr)[DIM + 3],
-                                    pk::f2 (&F)[DIM + 3]) {
-  if constexpr (PP == 3) pknps::hll<DIM, A>(k, L, R, fl, fr, F);
-  else pkn::hll<DIM, PP, A>(k, L, R, fl, fr, F);
+                                    CV&& cells, pk::f2 (&F)[DIM + 3]) {
+  if constexpr (PP == 3) pknps::hll<DIM, A>(k, L, R, cells, F);
+  else pkn::hll<DIM, PP, A>(k, L, R, cells, F);
 }
 
 template <int DIM, int PP, int SRC>

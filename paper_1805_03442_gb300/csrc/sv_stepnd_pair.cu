@@ -9,11 +9,12 @@
 // planes along the outermost axis, each thread one column.  Here each
 // iteration takes the planes (q, q+1) of the column as one pair of cells and
 // runs their arithmetic in packed f32x2 operations (sv_pairnd.cuh):
-//   a. the column's planes q-1 .. q+2 come from a per-thread cp.async ring;
-//      planes q and q+1 (with the halo's second ring) are published in shared
-//      memory;
+//   a. the column's planes q-1 .. q+2 come from a per-thread cp.async ring
+//      that stores the planes as pairs (q, q+1); planes q and q+1 (with the
+//      halo's second ring) are published in shared memory, also as pairs, so
+//      that every shared-memory access of the step moves both cells;
 //   b. slopes on every axis, guard, half-step predictor of both cells; the
-//      + states of the transverse axes are published as 8-byte pairs;
+//      + states of the transverse axes are published;
 //   c. transverse faces (left neighbour's + states of both planes against the
 //      own - states), one packed HLL per transverse axis;
 //   d. transverse flux divergence of both cells;
@@ -36,21 +37,27 @@ namespace {
 
 using pk::f2;
 
-constexpr int kPairRing = 8;   // planes per thread ring
+constexpr int kPairRing = 8;   // planes per thread ring (four plane pairs)
 
 template <int DIM, int TX, int TY> struct PairHalo {
   static constexpr int N = 2 * TY + (DIM == 3 ? 2 * TX : 0);
 };
 
-// Shared memory: sU[2][NF][SY][TX+2] floats (planes q, q+1), sW and sF
-// [DIM-1][NF][NT] pairs, sR[D][NF][NT] floats (own-column ring), sH[D][NF][NH]
-// floats (the halo's second ring).
+// Shared memory, all in pairs of planes (q, q+1) -- a thread's two cells --
+// so that each access moves both: sU[NF][SY][TX+2] (the tile row with its
+// halo), sW and sF [DIM-1][NF][NT] (+ states, fluxes), sR[D/2][NF][NT]
+// (own-column ring), sH[D/2][NF][NH] (the halo's second ring).
 template <int DIM, int TX, int TY>
 constexpr size_t pair_smem() {
   constexpr size_t NF = DIM + 3, SY = DIM == 3 ? TY + 2 : 1, NT = (size_t)TX * TY;
-  return sizeof(float) * (2 * NF * SY * (TX + 2) + 2 * 2 * (DIM - 1) * NF * NT +
-                          (size_t)kPairRing * NF * NT +
-                          (size_t)kPairRing * NF * PairHalo<DIM, TX, TY>::N);
+  return sizeof(pk::f2) * (NF * SY * (TX + 2) + 2 * (DIM - 1) * NF * NT +
+                           (size_t)(kPairRing / 2) * NF * NT +
+                           (size_t)(kPairRing / 2) * NF * PairHalo<DIM, TX, TY>::N);
+}
+
+// component h of pair slot s as a float address (cp.async destination)
+__device__ __forceinline__ float* half_of(pk::f2* s, int h) {
+  return reinterpret_cast<float*>(s) + h;
 }
 
 template <int PP, int LIM, int SRC, int DIM, int TX, int TY, int MINB, bool BND>
@@ -60,17 +67,17 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
                    int tiles_y, int nseg) {
   static_assert(!BND || DIM == 2, "boundaries and media are 2D only");
   constexpr int NF = DIM + 3, NT = TX * TY, SY = DIM == 3 ? TY + 2 : 1, AM = DIM - 1;
-  constexpr int D = kPairRing, NH = PairHalo<DIM, TX, TY>::N;
+  constexpr int DP = kPairRing / 2, NH = PairHalo<DIM, TX, TY>::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float (*sU)[NF][SY][TX + 2] = reinterpret_cast<float (*)[NF][SY][TX + 2]>(smem_raw);
-  size_t off = sizeof(float) * 2 * NF * SY * (TX + 2);
+  f2 (*sU)[SY][TX + 2] = reinterpret_cast<f2 (*)[SY][TX + 2]>(smem_raw);
+  size_t off = sizeof(f2) * NF * SY * (TX + 2);
   f2 (*sW)[NF][NT] = reinterpret_cast<f2 (*)[NF][NT]>(smem_raw + off);
   off += sizeof(f2) * (DIM - 1) * NF * NT;
   f2 (*sF)[NF][NT] = reinterpret_cast<f2 (*)[NF][NT]>(smem_raw + off);
   off += sizeof(f2) * (DIM - 1) * NF * NT;
-  float (*sR)[NF][NT] = reinterpret_cast<float (*)[NF][NT]>(smem_raw + off);
-  off += sizeof(float) * D * NF * NT;
-  float (*sH)[NF][NH] = reinterpret_cast<float (*)[NF][NH]>(smem_raw + off);
+  f2 (*sR)[NF][NT] = reinterpret_cast<f2 (*)[NF][NT]>(smem_raw + off);
+  off += sizeof(f2) * DP * NF * NT;
+  f2 (*sH)[NF][NH] = reinterpret_cast<f2 (*)[NF][NH]>(smem_raw + off);
 
   const StepCtl sc = block_step_ctl(ctl);
   if (!(sc.dt > 0.0)) return;
@@ -129,37 +136,29 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
   const int tid = threadIdx.x;
   const int hx = ty * 2 + (tx == 0 ? 0 : 1);
   const int hy = 2 * TY + tx * 2 + (ty == 0 ? 0 : 1);
-  // copy plane p of the own column (p <= q1 + 3) and of the second ring
-  // (p <= q1 + 2) into ring slot p mod D; always commit a group
+  // The iterations take the planes in pairs (q, q+1) with q - q0 even, so
+  // plane p lives in component (p - q0) & 1 of ring pair (p - q0 + 4) / 2
+  // mod D/2.  Copy plane p of the own column (p <= q1 + 3) and of the second
+  // ring (p <= q1 + 2) into its place; always commit a group.
   auto issue = [&](I p) {
-    const int sl = (int)(p & (D - 1));
+    const int r = (int)(p - q0 + 4), ps = (r >> 1) & (DP - 1), h = r & 1;
     if (p <= q1 + 3) {
       bool fy;
       const I o = plane_of(p, fy) * plane;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) cp_async<4>(&sR[sl][f][tid], Uin + f * ncell + o + col);
+      for (int f = 0; f < NF; ++f) cp_async<4>(half_of(&sR[ps][f][tid], h), Uin + f * ncell + o + col);
       if (p <= q1 + 2) {
         if (ringx)
 #pragma unroll
-          for (int f = 0; f < NF; ++f) cp_async<4>(&sH[sl][f][hx], Uin + f * ncell + o + col_rx);
+          for (int f = 0; f < NF; ++f)
+            cp_async<4>(half_of(&sH[ps][f][hx], h), Uin + f * ncell + o + col_rx);
         if (ringy)
 #pragma unroll
-          for (int f = 0; f < NF; ++f) cp_async<4>(&sH[sl][f][hy], Uin + f * ncell + o + col_ry);
+          for (int f = 0; f < NF; ++f)
+            cp_async<4>(half_of(&sH[ps][f][hy], h), Uin + f * ncell + o + col_ry);
       }
     }
     cp_async_commit();
-  };
-  // the column's state at position p, wall ghosts with their momenta reversed
-  auto column = [&](I p, float (&u)[NF]) {
-    bool fy;
-    plane_of(p, fy);
-    const int sl = (int)(p & (D - 1));
-#pragma unroll
-    for (int f = 0; f < NF; ++f) u[f] = sR[sl][f][tid];
-    if (BND) {
-      if (fx_own) u[1] = -u[1];
-      if (fy) u[2] = -u[2];
-    }
   };
 
   // carried from pair to pair: the upper plane's + state on the marching
@@ -179,58 +178,69 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
     // a. planes q-1 .. q+2 of the own column and q, q+1 of the second ring
     //    have landed; publish planes q and q+1
     cp_async_wait<1>();
-    float um[NF], u0[NF], u1[NF], u2[NF];
-    column(q - 1, um);
-    column(q, u0);
-    column(q + 1, u1);
-    column(q + 2, u2);
-    bool fy0, fy1;
+    // ring pairs (q-2, q-1), (q, q+1) and (q+2, q+3)
+    const int pq = (int)(((q - q0 + 4) >> 1) & (DP - 1));
+    const int pm = (pq + DP - 1) & (DP - 1), pn = (pq + 1) & (DP - 1);
+    bool fym, fy0, fy1, fy2;
+    plane_of(q - 1, fym);
     const I j0 = plane_of(q, fy0), j1 = plane_of(q + 1, fy1);
-    const int s0 = (int)(q & (D - 1)), s1 = (int)((q + 1) & (D - 1));
+    plane_of(q + 2, fy2);
+    // the column's planes q-1 .. q+2 (X = planes q, q+1), wall ghosts with
+    // their momenta reversed
+    f2 X[NF];
+    float um[NF], u2[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      sU[0][f][oy][tx + 1] = u0[f];
-      sU[1][f][oy][tx + 1] = u1[f];
-      if (ringx) {
-        float a = sH[s0][f][hx], b = sH[s1][f][hx];
-        if (BND) {
-          if (f == 1 && fx_rx) {
-            a = -a;
-            b = -b;
-          }
-          if (f == 2 && fy0) a = -a;
-          if (f == 2 && fy1) b = -b;
-        }
-        sU[0][f][oy][tx == 0 ? 0 : TX + 1] = a;
-        sU[1][f][oy][tx == 0 ? 0 : TX + 1] = b;
-      }
-      if (DIM == 3 && ringy) {
-        sU[0][f][ty == 0 ? 0 : SY - 1][tx + 1] = sH[s0][f][hy];
-        sU[1][f][ty == 0 ? 0 : SY - 1][tx + 1] = sH[s1][f][hy];
-      }
+      X[f] = sR[pq][f][tid];
+      um[f] = sR[pm][f][tid].y;
+      u2[f] = sR[pn][f][tid].x;
     }
-    issue(q + 4);        // slots of planes q-4, q-3: no longer read
+    if (BND) {
+      if (fx_own) {
+        X[1] = pk::mul(X[1], pk::splat(-1.0f));
+        um[1] = -um[1];
+        u2[1] = -u2[1];
+      }
+      if (fym) um[2] = -um[2];
+      if (fy0) X[2].x = -X[2].x;
+      if (fy1) X[2].y = -X[2].y;
+      if (fy2) u2[2] = -u2[2];
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      sU[f][oy][tx + 1] = X[f];
+      if (ringx) {
+        f2 a = sH[pq][f][hx];
+        if (BND) {
+          if (f == 1 && fx_rx) a = pk::mul(a, pk::splat(-1.0f));
+          if (f == 2 && fy0) a.x = -a.x;
+          if (f == 2 && fy1) a.y = -a.y;
+        }
+        sU[f][oy][tx == 0 ? 0 : TX + 1] = a;
+      }
+      if (DIM == 3 && ringy) sU[f][ty == 0 ? 0 : SY - 1][tx + 1] = sH[pq][f][hy];
+    }
+    issue(q + 4);        // the pair of planes q-4, q-3: no longer read
     issue(q + 5);
     __syncthreads();
 
     // b. slopes on every axis, guard, predictor of the pair
-    f2 X[NF], d[DIM][NF];
+    f2 d[DIM][NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      X[f] = pk::pair(u0[f], u1[f]);
       {
-        const f2 A = pk::sub(X[f], pk::pair(sU[0][f][oy][tx], sU[1][f][oy][tx]));
-        const f2 B = pk::sub(pk::pair(sU[0][f][oy][tx + 2], sU[1][f][oy][tx + 2]), X[f]);
+        const f2 A = pk::sub(X[f], sU[f][oy][tx]);
+        const f2 B = pk::sub(sU[f][oy][tx + 2], X[f]);
         d[0][f] = pk::pair(pk::slope<LIM>(A.x, B.x), pk::slope<LIM>(A.y, B.y));
       }
       if (DIM == 3) {
-        const f2 A = pk::sub(X[f], pk::pair(sU[0][f][oy - 1][tx + 1], sU[1][f][oy - 1][tx + 1]));
-        const f2 B = pk::sub(pk::pair(sU[0][f][oy + 1][tx + 1], sU[1][f][oy + 1][tx + 1]), X[f]);
+        const f2 A = pk::sub(X[f], sU[f][oy - 1][tx + 1]);
+        const f2 B = pk::sub(sU[f][oy + 1][tx + 1], X[f]);
         d[1][f] = pk::pair(pk::slope<LIM>(A.x, B.x), pk::slope<LIM>(A.y, B.y));
       }
       {
-        const f2 A = pk::sub(X[f], pk::pair(um[f], u0[f]));
-        const f2 B = pk::sub(pk::pair(u1[f], u2[f]), X[f]);
+        const f2 A = pk::sub(X[f], pk::pair(um[f], X[f].x));
+        const f2 B = pk::sub(pk::pair(X[f].y, u2[f]), X[f]);
         d[AM][f] = pk::pair(pk::slope<LIM>(A.x, B.x), pk::slope<LIM>(A.y, B.y));
       }
     }
@@ -287,22 +297,37 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
     // c. transverse faces of both planes
     f2 Fx[NF], Fy[NF];
     {
-      f2 L[NF], Rr[NF], fl[NF];
+      f2 L[NF], Rr[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         L[f] = sW[0][f][tx > 0 ? tid - 1 : tid];
         Rr[f] = pk::fma(nhalf, d[0][f], uh[f]);
-        fl[f] = pk::pair(sU[0][f][oy][tx], sU[1][f][oy][tx]);
       }
-      pknx::hll<DIM, PP, 0>(k, L, Rr, fl, X, Fx);
+      // a face with a non-physical state: the cells left and right of it
+      pknx::hll<DIM, PP, 0>(k, L, Rr,
+                            [&](f2 (&cl)[NF], f2 (&cr)[NF]) {
+#pragma unroll
+                              for (int f = 0; f < NF; ++f) {
+                                cl[f] = sU[f][oy][tx];
+                                cr[f] = X[f];
+                              }
+                            },
+                            Fx);
       if (DIM == 3) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
           L[f] = sW[DIM == 3 ? 1 : 0][f][ty > 0 ? tid - TX : tid];
           Rr[f] = pk::fma(nhalf, d[1][f], uh[f]);
-          fl[f] = pk::pair(sU[0][f][oy > 0 ? oy - 1 : oy][tx + 1], sU[1][f][oy > 0 ? oy - 1 : oy][tx + 1]);
         }
-        pknx::hll<DIM, PP, DIM == 3 ? 1 : 0>(k, L, Rr, fl, X, Fy);
+        pknx::hll<DIM, PP, DIM == 3 ? 1 : 0>(k, L, Rr,
+                                             [&](f2 (&cl)[NF], f2 (&cr)[NF]) {
+#pragma unroll
+                                               for (int f = 0; f < NF; ++f) {
+                                                 cl[f] = sU[f][oy > 0 ? oy - 1 : oy][tx + 1];
+                                                 cr[f] = X[f];
+                                               }
+                                             },
+                                             Fy);
       }
     }
 #pragma unroll
@@ -325,26 +350,32 @@ stepnd_pair_kernel(const KParams kp, float* __restrict__ bufA, float* __restrict
     f2 Hq[NF];
     float wpm_next[NF];
     {
-      f2 L[NF], Rr[NF], fl[NF];
+      f2 L[NF], Rr[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         const f2 wp = pk::fma(half, d[AM][f], uh[f]);
         Rr[f] = pk::fma(nhalf, d[AM][f], uh[f]);
         L[f] = pk::pair(wpm_prev[f], wp.x);
-        fl[f] = pk::pair(um[f], u0[f]);
         wpm_next[f] = wp.y;
       }
-      pknx::hll<DIM, PP, AM>(k, L, Rr, fl, X, Hq);
+      pknx::hll<DIM, PP, AM>(k, L, Rr,
+                             [&](f2 (&cl)[NF], f2 (&cr)[NF]) {
+#pragma unroll
+                               for (int f = 0; f < NF; ++f) {
+                                 cl[f] = pk::pair(um[f], X[f].x);
+                                 cr[f] = X[f];
+                               }
+                             },
+                             Hq);
     }
 
     // f. update of planes q-2 and q-1 (interior planes: no ghosts)
     if (q - 2 >= q0 && interior) {
       const bool two = q - 1 < q1;
-      const int sq = (int)((q - 2) & (D - 1));
       f2 Nw[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        const f2 Q = pk::pair(sR[sq][f][tid], um[f]);
+        const f2 Q = sR[pm][f][tid];           // planes q-2, q-1 (never ghosts here)
         const f2 FR = pk::pair(H_prev[f].y, Hq[f].x);
         Nw[f] = pk::fma(ndtdx2, pk::add(D_prev[f], pk::sub(FR, H_prev[f])), Q);
       }
