@@ -2,8 +2,9 @@
 // periodic runs of uneven sizes and parameters advanced to their own t_end by
 // ONE persistent launch.
 //
-// Each CTA takes a run from a device work queue (runs ordered by decreasing
-// estimated cost, n^2 t_end / L, so the longest runs start first), steps it
+// Each CTA takes a run from a device work queue (the runs of >= 8192 cells
+// first, largest first, then the others by decreasing estimated cost,
+// n^2 t_end / L, so that the longest runs start first), steps it
 // to completion with the same per-warp MUSCL-Hancock body as the single-grid
 // kernel (sv_step1d.cuh), and only then takes the next run.  A run's dt
 // reduction is CTA-local (shared memory + __syncthreads): there is no grid
@@ -64,6 +65,9 @@ size_t alb(size_t x) { return (x + kAlignB - 1) / kAlignB * kAlignB; }
 struct BLayout {
   size_t state, runs, order, queue, logs, total;
 };
+
+// Runs of at least this many cells lead the queue (sv_batch_init).
+constexpr int64_t kBigRun = 8192;
 
 int64_t stride_of(int64_t n) { return (n + 31) / 32 * 32; }
 
@@ -285,13 +289,22 @@ int sv_batch_init(const sv_params* p, const sv_run* runs, int64_t nruns,
   b->queue = (int*)(m + 2 * L.state + L.runs + L.order);
   b->logs = (double*)(m + 2 * L.state + L.runs + L.order + L.queue);
 
-  // longest runs first: cost ~ n * steps ~ n^2 t_end / L
+  // Queue order.  The runs of >= kBigRun cells first, largest first: a run's
+  // worst case is the step cap, whose cost grows with n alone, and the few
+  // large runs that reach it (their dt collapses long after the start, which
+  // no estimate from the initial state foresees) set the sweep's end unless
+  // they start early.  Then the others, longest first by the estimated cost
+  // n * steps ~ n^2 t_end / L.
   std::vector<int> order((size_t)nruns);
   std::iota(order.begin(), order.end(), 0);
   std::vector<double> cost((size_t)nruns);
   for (int64_t i = 0; i < nruns; ++i)
     cost[(size_t)i] = (double)runs[i].n * (double)runs[i].n * runs[i].t_end / runs[i].L;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+  auto big = [&](int i) { return runs[i].n >= kBigRun; };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    if (big(a) != big(c)) return big(a);
+    return big(a) ? runs[a].n > runs[c].n : cost[a] > cost[c];
+  });
 
   rc = SV_OK;
   if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
