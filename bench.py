@@ -434,7 +434,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": W["desc"].format(cells=ncell, side=dims[0]), "cells": ncell},
+            "config": {"workload": W["desc"].format(cells=ncell, side=dims[0]), "cells": ncell,
+                       "precision": args.precision},
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": O.threads(), "kind": "oracle",
                              "sample": f"{args.steps} whole-grid FP64 oracle steps of the "
                                        f"workload on {'x'.join(map(str, dims))} cells"},
