@@ -67,11 +67,13 @@ cudaError_t stepnd_pair_launch(int dim, int precision, const KParams& kp, void* 
                                const int64_t* n, int seg, cudaStream_t st);
 
 // The float 3D step with the fields in packed pairs (sv_stepnd3f.cu),
-// precision PREC_FP32 or PREC_FP32_PC; n == nullptr sets the kernels'
-// shared-memory limits
+// precision PREC_FP32, PREC_FP32_PC or PREC_FP32_PS (the last compiled in
+// sv_stepnd3f_ps.cu); n == nullptr sets the kernels' shared-memory limits
 int stepnd3f_default_seg();
 cudaError_t stepnd3f_launch(int precision, const KParams& kp, void* a, void* b, Ctl* ctl,
                             const int64_t* n, int seg, cudaStream_t st);
+cudaError_t stepnd3f_launch_ps(const KParams& kp, void* a, void* b, Ctl* ctl, const int64_t* n,
+                               int seg, cudaStream_t st);
 
 // Batched sweep kernels of 256 (sv_batch.cu) and 128 (sv_batch128.cu) threads
 void* batch_pick256(int limiter, int precision);

@@ -26,7 +26,6 @@
 // computed; copies are coalesced along x.
 #include "sv_internal.h"
 #include "sv_ndbnd.cuh"
-#include "sv_pertnd.cuh"
 #include "sv_step1d.cuh"      // cp.async helpers
 
 namespace sv {
@@ -59,21 +58,6 @@ struct Nd {
   // F(u + d/2) - F(u - d/2) along axis A; returns false if a state is non-physical
   template <int A>
   static __device__ __forceinline__ bool dflux(const P<R>& k, const V& u, const V& d, V& dF) {
-    if constexpr (PP == 3) {           // perturbation layout (sv_pertnd.cuh)
-      V a, b;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        a[f] = u[f] + 0.5f * d[f];
-        b[f] = u[f] - 0.5f * d[f];
-      }
-      const psn::Prim<DIM> qa = psn::prim<DIM>(k, a), qb = psn::prim<DIM>(k, b);
-      V Fa, Fb;
-      psn::flux<DIM, A>(k, a, qa, Fa);
-      psn::flux<DIM, A>(k, b, qb, Fb);
-#pragma unroll
-      for (int f = 0; f < NF; ++f) dF[f] = Fa[f] - Fb[f];
-      return fminf(fminf(qa.rho, qa.p), fminf(qb.rho, qb.p)) > 0.0f;
-    }
     V a, b;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -96,10 +80,6 @@ struct Nd {
                                                 bool active = true) {
     yE = yEv = (R)0;
     if (SRC == 0 || !active) return;
-    if constexpr (PP == 3) {
-      psn::source<DIM, SRC>(k, u, psn::prim<DIM>(k, u), yE, yEv);
-      return;
-    }
     R ir, p, v[DIM];
     prim(k, u, ir, v, p);
     Src<R, SRC>::eval(k, u[0], p * ir, u[2 + DIM], yE, yEv);
@@ -109,30 +89,6 @@ struct Nd {
   template <int A>
   static __device__ __forceinline__ void hll(const P<R>& k, const V& l, const V& r, const V& fl,
                                              const V& fr, V& F) {
-    if constexpr (PP == 3) {
-      V L, Rr;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) { L[f] = l[f]; Rr[f] = r[f]; }
-      psn::Prim<DIM> qL = psn::prim<DIM>(k, L), qR = psn::prim<DIM>(k, Rr);
-      if (!(fminf(fminf(qL.rho, qL.p), fminf(qR.rho, qR.p)) > 0.0f)) {
-#pragma unroll
-        for (int f = 0; f < NF; ++f) { L[f] = fl[f]; Rr[f] = fr[f]; }
-        qL = psn::prim<DIM>(k, L);
-        qR = psn::prim<DIM>(k, Rr);
-      }
-      const float cL = Ar<float>::sqrt_pos(k.gamma * qL.p * qL.ir);
-      const float cR = Ar<float>::sqrt_pos(k.gamma * qR.p * qR.ir);
-      const float sl = fminf(fminf(qL.v[A] - cL, qR.v[A] - cR), 0.0f);
-      const float sr = fmaxf(fmaxf(qL.v[A] + cL, qR.v[A] + cR), 0.0f);
-      V FL, FR;
-      psn::flux<DIM, A>(k, L, qL, FL);
-      psn::flux<DIM, A>(k, Rr, qR, FR);
-      const float inv = Ar<float>::rcp(sr - sl);
-      const float wl = sr * inv, wr = -sl * inv, wd = sl * sr * inv;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) F[f] = wl * FL[f] + wr * FR[f] + wd * (Rr[f] - L[f]);
-      return;
-    }
     V L, Rr;
 #pragma unroll
     for (int f = 0; f < NF; ++f) { L[f] = l[f]; Rr[f] = r[f]; }
@@ -421,27 +377,21 @@ stepnd_kernel(const KParams kp, R* __restrict__ bufA, R* __restrict__ bufB, Ctl*
       un[1 + DIM] += dt * yE_prev;
       un[2 + DIM] += dt * yEv_prev;
       // a driven cell holds the pulsating source at the new time level
-      if (pulses && gx >= __ldg(kp.pul_lo + (q - 1)) && gx < __ldg(kp.pul_hi + (q - 1))) {
-        if constexpr (PP == 3) pulse_state_ps<NF>(kp, sc.t + sc.dt, un);
-        else pulse_state<R, NF>(kp, sc.t + sc.dt, un);
-      }
+      if (pulses && gx >= __ldg(kp.pul_lo + (q - 1)) && gx < __ldg(kp.pul_hi + (q - 1)))
+        pulse_state<R, NF>(kp, sc.t + sc.dt, un);
       const I o = pidx(q - 1) + col;
 #pragma unroll
       for (int f = 0; f < NF; ++f) Uout[f * ncell + o] = un[f];
-      if constexpr (PP == 3) {
-        psn::bound<DIM, SRC>(k, un, smax, akey, flags);
-      } else {
-        R ir, p, v[DIM];
-        C::prim(k, un, ir, v, p);
-        R v2 = 0;
+      R ir, p, v[DIM];
+      C::prim(k, un, ir, v, p);
+      R v2 = 0;
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) v2 += v[a] * v[a];
-        const R vmag = speed_of<R>(v2);
-        R kin2 = 0;
+      for (int a = 0; a < DIM; ++a) v2 += v[a] * v[a];
+      const R vmag = speed_of<R>(v2);
+      R kin2 = 0;
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) kin2 += un[1 + a] * v[a];
-        cfl_cell<R, PP, SRC>(k, un[0], kin2, vmag, un[1 + DIM], un[2 + DIM], smax, akey, flags);
-      }
+      for (int a = 0; a < DIM; ++a) kin2 += un[1 + a] * v[a];
+      cfl_cell<R, PP, SRC>(k, un[0], kin2, vmag, un[1 + DIM], un[2 + DIM], smax, akey, flags);
     }
 
     // rotate the plane window
@@ -464,7 +414,6 @@ template <int DIM, int PREC> struct Cfg;
 template <> struct Cfg<2, PREC_FP32_P64> { static constexpr int TX = 256, TY = 1, MINB = 2, SEG = 256; };
 template <> struct Cfg<2, PREC_FP64> { static constexpr int TX = 128, TY = 1, MINB = 2, SEG = 256; };
 template <> struct Cfg<3, PREC_FP32_P64> { static constexpr int TX = 34, TY = 15, MINB = 1, SEG = 128; };
-template <> struct Cfg<3, PREC_FP32_PS> { static constexpr int TX = 34, TY = 15, MINB = 1, SEG = 128; };
 template <> struct Cfg<3, PREC_FP64> { static constexpr int TX = 32, TY = 8, MINB = 1, SEG = 128; };
 
 // With `n` null only the kernel's shared-memory attribute is set (done once per
@@ -512,13 +461,10 @@ static cudaError_t by_prec(int precision, const KParams& kp, void* a, void* b, C
     case PREC_FP32_P64: return launch_nd<float, 1, LIM, SRC, DIM, PREC_FP32_P64>(kp, a, b, ctl, n, seg, st);
     default:
       // the other float policies: in 2D packed plane pairs
-      // (sv_stepnd_pair.cu); in 3D float and compensated-float pressure with
-      // each cell's fields in packed pairs (sv_stepnd3f.cu: plane pairs need
-      // 242 registers there, one block per SM, and ran 17% slower than one
-      // cell per thread), the perturbation layout one cell per thread
+      // (sv_stepnd_pair.cu); in 3D each cell's fields in packed pairs
+      // (sv_stepnd3f.cu: plane pairs need 242 registers there, one block per
+      // SM, and ran 17% slower than one cell per thread)
       if constexpr (DIM == 2) return stepnd_pair_launch(DIM, precision, kp, a, b, ctl, n, seg, st);
-      else if (precision == PREC_FP32_PS)
-        return launch_nd<float, 3, LIM, SRC, DIM, PREC_FP32_PS>(kp, a, b, ctl, n, seg, st);
       else return stepnd3f_launch(precision, kp, a, b, ctl, n, seg, st);
   }
 }
@@ -547,7 +493,6 @@ int stepnd_default_seg(int dim, int precision) {
       dim == 2)
     return stepnd_pair_default_seg(dim);
   if (dim == 2) return precision == PREC_FP64 ? Cfg<2, PREC_FP64>::SEG : Cfg<2, PREC_FP32_P64>::SEG;
-  if (precision == PREC_FP32_PS) return Cfg<3, PREC_FP32_PS>::SEG;
   if (precision == PREC_FP32_P64) return Cfg<3, PREC_FP32_P64>::SEG;
   return precision == PREC_FP64 ? Cfg<3, PREC_FP64>::SEG : stepnd3f_default_seg();
 }
