@@ -1,7 +1,9 @@
 // sv_pertnd.cuh -- the perturbation layout (SV_FP32_PS) of the 2D / 3D
 // unsplit steps: the arithmetic of sv_pert1d.cuh with DIM velocity
-// components, for one cell (psn::, the 3D kernel) and for a thread's two
-// cells in packed f32x2 (pknps::, the 2D plane-pair kernel).
+// components, for one cell (psn::, the source and the eq. 16 bound of the 3D
+// field-pair kernel and of the dt of an uploaded state) and for a thread's
+// two cells in packed f32x2 (pknps::, the 2D plane-pair kernel).  The 3D
+// kernel forms its fluxes in field pairs itself (sv_stepnd3f.cuh).
 //
 // u = U - U_ref, U_ref = (1, 0 .. 0, E0, E_nu0); fields (rho, rho v_1 ..
 // rho v_DIM, E, E_nu), NF = DIM + 3.  Along axis A the flux less F(U_ref)
@@ -50,16 +52,6 @@ __device__ __forceinline__ Prim<DIM> prim(const P<float>& k, const float (&u)[DI
   q.dp = k.g1 * fmaf(q.kin2, -0.5f, u[1 + DIM] - u[2 + DIM]);
   q.p = 1.0f + q.dp;
   return q;
-}
-
-template <int DIM, int A>
-__device__ __forceinline__ void flux(const P<float>& k, const float (&u)[DIM + 3],
-                                     const Prim<DIM>& q, float (&F)[DIM + 3]) {
-  F[0] = u[1 + A];
-#pragma unroll
-  for (int b = 0; b < DIM; ++b) F[1 + b] = u[1 + b] * q.v[A] + (b == A ? q.dp : 0.0f);
-  F[1 + DIM] = q.v[A] * (k.h0 + (u[1 + DIM] + q.dp));
-  F[2 + DIM] = q.v[A] * (k.ev0 + u[2 + DIM]);
 }
 
 template <int DIM, int SRC>
