@@ -71,12 +71,17 @@ def traffic_of(workload: str, ncell: int, precision: str, config: str):
         return None
     return next((v for k, v in table.items() if k in config), None)
 
-# FP64 flops one updated cell costs in the FP64 step kernels (2 DFMA + DMUL + DADD, ncu
-# warp-instruction counts x 32 lanes): step1d_kernel at N = 2^20, stepnd_kernel at 1024^2 and
-# 128^3 (the 3D figure includes the tile halo's redundant work), with the paper's closure
-# exponents (tau_rho = -1, tau_T = -1.5: the power laws of eq. 6 as products).  These kernels are bound
-# by GB300's FP64 pipe (ncu: 86-87 % of its peak busy), so FP64 lines report an "alu" roofline.
-FP64_FLOPS_PER_CELL = {1: 455.7, 2: 855.9, 3: 1938.3}
+# FP64 flops one updated cell costs in the FP64 step kernels of the benchmark grids (2 DFMA +
+# DMUL + DADD, ncu warp-instruction counts x 32 lanes, the tiles' halo work included): step1d_kernel
+# at N = 2^22 itself; stepnd_kernel on 4224^2 (2D) and 180^3 (3D), whose x-y tiles cover the grid
+# with the same redundancy as 8192^2 and 512^3 do (a capture of the full FP64 grids would hold
+# 5-6 GB), both scaled to the marching segments the benchmark grids run (two warm-up planes per
+# segment: 2D 793.5 counted with 64-row segments, x (258/256) / (66/64) for the 256-row segments
+# of 8192^2; 3D 1575.8 counted with 60-plane segments, x (520/512) / (186/180) for the 128-plane
+# segments of 512^3).  With the paper's closure exponents (tau_rho = -1,
+# tau_T = -1.5: the power laws of eq. 6 as products).  These kernels are bound by GB300's FP64 pipe
+# (ncu: 86 % of its peak busy), so FP64 lines report an "alu" roofline.
+FP64_FLOPS_PER_CELL = {1: 422.9, 2: 775.5, 3: 1548.8}
 
 # --precision names -> sv_params.precision (SV_FP32, SV_FP64, SV_FP32_P64,
 # SV_FP32_PC, SV_FP32_PS of include/sv.h) and the arithmetic type reported as "dtype"

@@ -414,7 +414,7 @@ template <int DIM, int PREC> struct Cfg;
 template <> struct Cfg<2, PREC_FP32_P64> { static constexpr int TX = 256, TY = 1, MINB = 2, SEG = 256; };
 template <> struct Cfg<2, PREC_FP64> { static constexpr int TX = 128, TY = 1, MINB = 2, SEG = 256; };
 template <> struct Cfg<3, PREC_FP32_P64> { static constexpr int TX = 34, TY = 15, MINB = 1, SEG = 128; };
-template <> struct Cfg<3, PREC_FP64> { static constexpr int TX = 32, TY = 8, MINB = 1, SEG = 128; };
+template <> struct Cfg<3, PREC_FP64> { static constexpr int TX = 16, TY = 16, MINB = 1, SEG = 128; };
 
 // With `n` null only the kernel's shared-memory attribute is set (done once per
 // solver at init, outside any stream capture).  `seg` = planes per block along

@@ -51,8 +51,8 @@ def test_fp64_roofline():
     r = bench.fp64_roofline(1, 1 << 22, 2.31e-3, 0.017, peak)
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["traffic"] is None
     assert r["peak"] == peak and "measured" in r["peak_src"]
-    assert r["flops_per_launch"] == pytest.approx(455.7 * (1 << 22))
-    assert r["achieved"] == pytest.approx(455.7 * (1 << 22) / 2.31e-3 / 1e12)
+    assert r["flops_per_launch"] == pytest.approx(422.9 * (1 << 22))
+    assert r["achieved"] == pytest.approx(422.9 * (1 << 22) / 2.31e-3 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"]) and 0 < r["frac"] < 1
     # flops per cell grow with the dimension (more fluxes, more fields)
     f = bench.FP64_FLOPS_PER_CELL
